@@ -1,0 +1,147 @@
+/*
+ * pa_gb300.h -- C ABI of the GB300 (sm_103a) MMH-MH privacy-amplification hash
+ * of "An efficient hybrid hash based privacy amplification algorithm for QKD"
+ * (arXiv 2105.13678).
+ *
+ * The library compresses an n-bit partially secure key to r output bits:
+ *   Algorithm 1 (Sec. 3.1):  x = <x_1..x_k>, a = <a_1..a_k> (gamma-bit slices),
+ *   MMH, Eq. 2:              y = sum_i a_i x_i  mod p,  p = 2^gamma - 1,
+ *   MH,  Eq. 4:              z = ((b y + c) mod 2^gamma) >> (gamma - r),
+ * with gamma a Mersenne prime exponent and n <= k * gamma (step 0, Sec. 4).
+ *
+ * Conventions shared by every entry point
+ *   - Bit strings are arrays of uint64_t; bit t lives in word t/64 at bit t%64.
+ *   - key:  ceil(n/64) words.  Bits at or past n in the last word are ignored.
+ *   - seed: ceil((k+2)*gamma/64) words: a_1..a_k, then b, then c, each a
+ *           gamma-bit slice in that order.  a_i is taken mod p (the all-ones
+ *           slice is p == 0); bit 0 of b is forced to 1 (gcd(b, 2) = 1).
+ *   - out:  ceil(r/64) words; bits at or past r are written as 0.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - Device pointers are owned by the caller and never freed by the library.
+ *     A plan owns the device workspace and tables it allocates.
+ *   - Calls are asynchronous on `stream` unless stated otherwise; a plan's
+ *     workspace is reused by every call on that plan, so calls that share a
+ *     plan must be ordered (same stream, or event-ordered).
+ *
+ * Return codes: PA_OK (0); PA_RELOAD (1): some key slice x_i equals
+ * 2^gamma - 1, Alg. 1 lines 3-4 -- the output is zero-filled and the caller
+ * must draw a new key; negative values are errors.
+ */
+#ifndef PA_GB300_H
+#define PA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PA_OK 0
+#define PA_RELOAD 1
+#define PA_ERR_INVALID (-1)     /* bad argument: n = 0, r = 0, null pointer, no gamma fits */
+#define PA_ERR_NOMEM (-2)       /* device or host allocation failed */
+#define PA_ERR_CUDA (-3)        /* a CUDA runtime call failed */
+#define PA_ERR_TIMEOUT (-4)     /* a bounded wait expired */
+#define PA_ERR_BUDGET (-5)      /* job larger than the server's whole HBM budget */
+#define PA_ERR_CANCELLED (-6)   /* job cancelled by pa_serve_destroy */
+#define PA_ERR_UNSUPPORTED (-7) /* sizes beyond what the kernels implement */
+#define PA_ERR_BUSY (-8)        /* server queue full / ticket unknown */
+
+/* Step-0 parameters (Sec. 4).  Pass NULL for the defaults. */
+typedef struct pa_params {
+    uint32_t gamma;        /* 0: smallest Mersenne exponent >= r + gamma_margin;
+                              otherwise a Mersenne exponent > r to use as is   */
+    uint32_t gamma_margin; /* default 128: gamma - r >= margin keeps the
+                              2^(r - gamma) term of the Sec. 3.2 bounds tiny   */
+    uint32_t reserved[6];  /* must be zero */
+} pa_params;
+
+typedef struct pa_plan_info {
+    uint64_t n_bits, r_bits;
+    uint32_t gamma;           /* Mersenne exponent, p = 2^gamma - 1           */
+    uint32_t reserved0;
+    uint64_t k;               /* segments, ceil(n / gamma)                      */
+    uint64_t key_words, seed_words, out_words;
+    uint64_t mmh_len;         /* cyclic transform length for Eq. 2 (mod 2^gamma - 1) */
+    uint64_t mh_len;          /* cyclic transform length for Eq. 4 (mod 2^(2 gamma) - 1) */
+    uint64_t workspace_bytes; /* device bytes owned by the plan                 */
+} pa_plan_info;
+
+typedef struct pa_plan_s pa_plan_t;
+
+/* Step 0 (Sec. 4, Table 3): choose gamma and k for (n, r) and allocate the
+ * plan's device workspace and twiddle/weight tables on the current device.
+ * Blocking.  Returns PA_ERR_INVALID if no tabulated exponent fits and
+ * PA_ERR_UNSUPPORTED beyond the largest transform the kernels implement. */
+int pa_plan(uint64_t n_bits, uint64_t r_bits, const pa_params *params, pa_plan_t **out);
+int pa_plan_info_get(const pa_plan_t *plan, pa_plan_info *info);
+int pa_plan_destroy(pa_plan_t *plan);
+
+/* Algorithm 1 on device buffers (key, seed, out as above; `status` is an
+ * optional device int that receives PA_OK or PA_RELOAD when the work runs).
+ * Asynchronous: returns PA_OK once enqueued. */
+int pa_hash(pa_plan_t *plan, const uint64_t *key, const uint64_t *seed, uint64_t *out,
+            int *status, void *stream);
+
+/* Algorithm 1 on HOST buffers: copies key and seed in, runs, copies out and
+ * synchronises `stream`.  Returns PA_OK, PA_RELOAD or an error. */
+int pa_hash_host(pa_plan_t *plan, const uint64_t *key, const uint64_t *seed, uint64_t *out,
+                 void *stream);
+
+/* The MMH value y = sum a_i x_i mod p of Eq. 2 (ceil(gamma/64) device words,
+ * canonical in [0, p)), for checking the intermediate.  Asynchronous. */
+int pa_debug_mmh(pa_plan_t *plan, const uint64_t *key, const uint64_t *seed, uint64_t *y,
+                 int *status, void *stream);
+
+/* Batched Algorithm 1 over `count` independent blocks, each with its own plan
+ * (plans must be distinct objects).  keys/seeds/outs are HOST arrays of device
+ * pointers; statuses is a device int[count] (may be NULL).  The first call for
+ * a given list of plans and buffers captures one CUDA graph whose branches run
+ * the blocks concurrently; later calls with the same arguments replay it.
+ * Asynchronous. */
+int pa_hash_batch(pa_plan_t *const *plans, const uint64_t *const *keys,
+                  const uint64_t *const *seeds, uint64_t *const *outs, int *statuses,
+                  int count, void *stream);
+/* Drop the graphs cached by pa_hash_batch (they are also dropped when one of
+ * their plans is destroyed). */
+int pa_batch_cache_clear(void);
+
+/* ---- serving: a continuous-batching request loop on one GPU ---------------
+ * Jobs are admitted while their device bytes (plan workspace) fit in the HBM
+ * budget; admitted jobs run concurrently on `slots` streams; others wait in a
+ * FIFO.  key/seed/out are DEVICE pointers owned by the caller and must stay
+ * valid until the job completes. */
+typedef struct pa_server_s pa_server_t;
+typedef struct pa_serve_config {
+    uint64_t hbm_budget_bytes; /* admission budget for plan workspaces         */
+    uint32_t slots;            /* concurrent jobs on the device (streams)      */
+    uint32_t max_queue;        /* pending jobs before submit returns PA_ERR_BUSY */
+    pa_params params;          /* step-0 parameters for every job               */
+} pa_serve_config;
+typedef struct pa_serve_stats {
+    uint64_t submitted, completed, failed, cancelled, queued, running;
+    uint64_t bits_completed;          /* sum of n over completed jobs          */
+    double p50_latency_ms, p99_latency_ms, max_latency_ms; /* submit -> done  */
+    double busy_seconds;              /* first submit -> last completion       */
+    uint64_t peak_budget_bytes;       /* highest admitted workspace in use     */
+} pa_serve_stats;
+
+int pa_serve_create(const pa_serve_config *cfg, pa_server_t **out);
+int pa_serve_submit(pa_server_t *srv, uint64_t n_bits, uint64_t r_bits, const uint64_t *key,
+                    const uint64_t *seed, uint64_t *out, uint64_t *ticket);
+int pa_serve_poll(pa_server_t *srv, uint64_t ticket, int *status);  /* PA_OK if done, PA_ERR_BUSY if not */
+int pa_serve_wait(pa_server_t *srv, uint64_t ticket, uint64_t timeout_ns, int *status);
+int pa_serve_stats_get(pa_server_t *srv, pa_serve_stats *stats);
+int pa_serve_destroy(pa_server_t *srv); /* cancels queued jobs, waits for running ones */
+
+/* Human-readable name of a return code (static string). */
+const char *pa_status_string(int code);
+/* Library version string. */
+const char *pa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PA_GB300_H */

@@ -1,0 +1,448 @@
+// pa_api.cu -- plans and the C ABI entry points (pa_plan, pa_hash, ...).
+//
+// Step 0 of Algorithm 1 (Sec. 4, Table 3) is the parameter rule implemented
+// in choose_gamma(): gamma is the smallest Mersenne prime exponent >= r +
+// margin (or the caller's exponent), k = ceil(n / gamma).  The rest of this
+// file sizes the two weighted cyclic transforms (Eq. 2 modulo 2^gamma - 1 and
+// the exact product of Eq. 4), builds their root-of-unity and weight tables
+// on the host, and enqueues the kernels of pa_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/pa_gb300.h"
+#include "pa_internal.h"
+
+using namespace pa;
+
+// Exponents of the known Mersenne primes (the public list cited in Sec. 3.1).
+static const uint32_t kMersenneExponents[] = {
+    2,        3,        5,        7,        13,       17,       19,       31,       61,        89,       107,
+    127,      521,      607,      1279,     2203,     2281,     3217,     4253,     4423,      9689,     9941,
+    11213,    19937,    21701,    23209,    44497,    86243,    110503,   132049,   216091,    756839,   859433,
+    1257787,  1398269,  2976221,  3021377,  6972593,  13466917, 20996011, 24036583, 25964951,  30402457, 32582657,
+    37156667, 42643801, 43112609, 57885161, 74207281, 77232917, 82589933, 136279841};
+
+static int choose_gamma(uint64_t r, const pa_params *p, uint32_t *gamma) {
+    const uint32_t margin = p ? p->gamma_margin : 128u;
+    const uint32_t want = p ? p->gamma : 0u;
+    for (uint32_t g : kMersenneExponents) {
+        if (want) {
+            if (g == want) {
+                if ((uint64_t)g <= r) return PA_ERR_INVALID;
+                *gamma = g;
+                return PA_OK;
+            }
+        } else if ((uint64_t)g >= r + (margin ? margin : 1u)) {
+            *gamma = g;
+            return PA_OK;
+        }
+    }
+    return PA_ERR_INVALID;
+}
+
+// Smallest N = 2^l whose digits keep every convolution coefficient below q:
+// digits are < 2^b with b = ceil(G / N); a coefficient of the weighted cyclic
+// convolution is a sum of N products per operand pair, each doubled at most
+// once by the weight ratio, so it is < 2 K N (2^b - 1)^2, plus one digit of c.
+static int choose_len(uint64_t G, uint64_t K, uint32_t *logN) {
+    for (uint32_t l = 0; l <= PA_MAX_LOGN; l++) {
+        const uint64_t N = 1ULL << l;
+        const uint64_t b = (G + N - 1) >> l;
+        if (b > 31) continue;
+        const unsigned __int128 m = ((unsigned __int128)1 << b) - 1;
+        const unsigned __int128 bound = (unsigned __int128)2 * K * N * m * m + m;
+        if (bound < GL_Q) {
+            *logN = l;
+            return PA_OK;
+        }
+    }
+    return PA_ERR_UNSUPPORTED;
+}
+
+namespace {
+
+struct DevTables {
+    std::vector<void *> allocs;
+    ~DevTables() {
+        for (void *p : allocs) cudaFree(p);
+    }
+    const u64 *upload(const std::vector<u64> &h, int *err) {
+        void *d = nullptr;
+        if (cudaMalloc(&d, h.size() * sizeof(u64)) != cudaSuccess) {
+            *err = PA_ERR_NOMEM;
+            return nullptr;
+        }
+        allocs.push_back(d);
+        if (cudaMemcpy(d, h.data(), h.size() * sizeof(u64), cudaMemcpyHostToDevice) != cudaSuccess) *err = PA_ERR_CUDA;
+        return (const u64 *)d;
+    }
+};
+
+// F_q has generator 7; omega_N = 7^((q-1)/N).  2 has order 192, so
+// 2 = rho^u with rho = 7^((q-1)/192); theta_N = 7^(u (q-1)/(192 N)) then
+// satisfies theta_N^N = 2 for every N dividing 2^26.
+static const u64 kGen = 7;
+
+u64 root_of_unity(uint32_t logN) { return gl_pow(kGen, (GL_Q - 1) >> logN); }
+
+u64 root_of_two(uint32_t logN) {
+    const u64 rho = gl_pow(kGen, (GL_Q - 1) / 192);
+    u64 acc = 1;
+    uint32_t u = 0;
+    for (uint32_t i = 1; i < 192; i++) {
+        acc = gl_mul(acc, rho);
+        if (acc == 2) {
+            u = i;
+            break;
+        }
+    }
+    const unsigned __int128 e = (unsigned __int128)u * (((GL_Q - 1) / 192) >> logN);
+    return gl_pow(kGen, (u64)(e % (GL_Q - 1)));
+}
+
+std::vector<u64> powers(u64 base, size_t count, u64 scale = 1) {
+    std::vector<u64> v(count ? count : 1);
+    u64 x = scale;
+    for (size_t i = 0; i < v.size(); i++) {
+        v[i] = x;
+        x = gl_mul(x, base);
+    }
+    return v;
+}
+
+}  // namespace
+
+struct pa_plan_s {
+    uint64_t n, r, k;
+    uint32_t gamma;
+    Xform mmh, mh;
+    DevTables tables;
+    // workspace
+    u64 *Y = nullptr;       // operand spectra (and the un-weighted coefficients)
+    u64 *S = nullptr;       // accumulated spectra
+    u64 *ybuf = nullptr;    // MMH value, gamma bits
+    u64 *tbuf = nullptr;    // b*y + c, 2 gamma bits
+    u64 *H = nullptr;
+    unsigned char *cstate = nullptr, *cta_state = nullptr, *cta_cin = nullptr;
+    int *flags = nullptr;   // [0] reload, [1] y all-ones, [2] t all-ones, [3] -, [4..4+k) slice counters
+    size_t flags_bytes = 0;
+    uint64_t ws_bytes = 0;
+    // device staging for pa_hash_host: key | seed | out | status
+    u64 *dkey = nullptr, *dseed = nullptr, *dout = nullptr;
+    int *dstatus = nullptr;
+    std::vector<void *> ws_allocs;
+    ~pa_plan_s() {
+        for (void *p : ws_allocs) cudaFree(p);
+    }
+    void *alloc(size_t bytes, int *err) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes ? bytes : 8) != cudaSuccess) {
+            *err = PA_ERR_NOMEM;
+            return nullptr;
+        }
+        ws_allocs.push_back(p);
+        ws_bytes += bytes;
+        return p;
+    }
+};
+
+static int build_xform(pa_plan_t *pl, Xform &X, uint64_t G, uint64_t K) {
+    uint32_t l;
+    int rc = choose_len(G, K, &l);
+    if (rc) return rc;
+    X.N = 1ULL << l;
+    X.G = G;
+    X.K = (u32)K;
+    X.logN = l;
+    X.logR = std::min(l / 2, PA_MAX_LOGR);
+    X.logC = l - X.logR;
+    X.R = 1u << X.logR;
+    X.C = 1u << X.logC;
+    X.hb = (l + 1) / 2;
+    u32 tc = 8;
+    while (tc > 1 && (uint64_t)X.R * tc > 8192) tc >>= 1;
+    while (tc > X.C) tc >>= 1;
+    X.tc = tc;
+    const u64 w = root_of_unity(l), wi = gl_inv(w);
+    const u64 th = root_of_two(l), thi = gl_inv(th);
+    const u64 ninv = gl_inv(X.N % GL_Q);
+    const u64 wR = gl_pow(w, X.C), wC = gl_pow(w, X.R);
+    int err = PA_OK;
+    auto up = [&](const std::vector<u64> &v) { return pl->tables.upload(v, &err); };
+    X.twR = up(powers(wR, X.R / 2));
+    X.itwR = up(powers(gl_inv(wR), X.R / 2));
+    X.twC = up(powers(wC, X.C / 2));
+    X.itwC = up(powers(gl_inv(wC), X.C / 2));
+    const size_t nlo = (size_t)1 << X.hb, nhi = (size_t)(X.N >> X.hb);
+    X.ipw_lo = up(powers(w, nlo));
+    X.ipw_hi = up(powers(gl_pow(w, nlo), nhi));
+    X.iipw_lo = up(powers(wi, nlo));
+    X.iipw_hi = up(powers(gl_pow(wi, nlo), nhi));
+    X.wt_lo = up(powers(th, nlo));
+    X.wt_hi = up(powers(gl_pow(th, nlo), nhi));
+    X.iwt_lo = up(powers(thi, nlo));
+    X.iwt_hi = up(powers(gl_pow(thi, nlo), nhi, ninv));
+    return err;
+}
+
+// Device bytes of a plan's workspace (shared by pa_plan and the server's admission).
+struct WsSizes {
+    uint64_t Y, S, ybuf, tbuf, H, cstate, cta, flags;
+    uint64_t total() const { return Y + S + ybuf + tbuf + H + cstate + 2 * cta + flags; }
+};
+static WsSizes ws_sizes(uint32_t gamma, uint64_t k, uint64_t N1, uint64_t N2) {
+    WsSizes z;
+    const uint64_t Nmax = std::max(N1, N2);
+    z.Y = std::max<uint64_t>(2 * k * N1, 2 * N2) * 8;
+    z.S = Nmax * 8;
+    z.ybuf = ((gamma + 63) / 64 + 2) * 8;
+    z.tbuf = ((2ULL * gamma + 63) / 64 + 2) * 8;
+    const uint64_t nch = std::max<uint64_t>(Nmax / PA_CARRY_D, 1);
+    z.H = nch * 8;
+    z.cstate = nch;
+    z.cta = nch / PA_CARRY_T + 1;
+    z.flags = (4 + k) * sizeof(int);
+    return z;
+}
+
+extern "C" {
+
+int pa_plan(uint64_t n_bits, uint64_t r_bits, const pa_params *params, pa_plan_t **out) {
+    if (!out || n_bits == 0 || r_bits == 0) return PA_ERR_INVALID;
+    *out = nullptr;
+    if (params) {
+        for (uint32_t v : params->reserved)
+            if (v) return PA_ERR_INVALID;
+    }
+    uint32_t gamma;
+    int rc = choose_gamma(r_bits, params, &gamma);
+    if (rc) return rc;
+    if (prepare_kernels()) return PA_ERR_CUDA;
+    pa_plan_t *pl = new (std::nothrow) pa_plan_s();
+    if (!pl) return PA_ERR_NOMEM;
+    pl->n = n_bits;
+    pl->r = r_bits;
+    pl->gamma = gamma;
+    pl->k = (n_bits + gamma - 1) / gamma;
+    if (2 * pl->k > 65535) {  // operands index gridDim.y of the column pass
+        delete pl;
+        return PA_ERR_UNSUPPORTED;
+    }
+    rc = build_xform(pl, pl->mmh, gamma, pl->k);
+    if (!rc) rc = build_xform(pl, pl->mh, 2ULL * gamma, 1);
+    if (rc) {
+        delete pl;
+        return rc;
+    }
+    const WsSizes z = ws_sizes(gamma, pl->k, pl->mmh.N, pl->mh.N);
+    int err = PA_OK;
+    pl->Y = (u64 *)pl->alloc(z.Y, &err);
+    pl->S = (u64 *)pl->alloc(z.S, &err);
+    pl->ybuf = (u64 *)pl->alloc(z.ybuf, &err);
+    pl->tbuf = (u64 *)pl->alloc(z.tbuf, &err);
+    pl->H = (u64 *)pl->alloc(z.H, &err);
+    pl->cstate = (unsigned char *)pl->alloc(z.cstate, &err);
+    pl->cta_state = (unsigned char *)pl->alloc(z.cta, &err);
+    pl->cta_cin = (unsigned char *)pl->alloc(z.cta, &err);
+    pl->flags_bytes = z.flags;
+    pl->flags = (int *)pl->alloc(z.flags, &err);
+    if (err) {
+        delete pl;
+        return err;
+    }
+    *out = pl;
+    return PA_OK;
+}
+
+int pa_plan_info_get(const pa_plan_t *pl, pa_plan_info *info) {
+    if (!pl || !info) return PA_ERR_INVALID;
+    memset(info, 0, sizeof(*info));
+    info->n_bits = pl->n;
+    info->r_bits = pl->r;
+    info->gamma = pl->gamma;
+    info->k = pl->k;
+    info->key_words = (pl->n + 63) / 64;
+    info->seed_words = ((pl->k + 2) * pl->gamma + 63) / 64;
+    info->out_words = (pl->r + 63) / 64;
+    info->mmh_len = pl->mmh.N;
+    info->mh_len = pl->mh.N;
+    info->workspace_bytes = pl->ws_bytes;
+    return PA_OK;
+}
+
+int pa_batch_drop_plan(pa_plan_t *pl);
+
+int pa_plan_destroy(pa_plan_t *pl) {
+    if (!pl) return PA_ERR_INVALID;
+    pa_batch_drop_plan(pl);
+    cudaDeviceSynchronize();
+    delete pl;
+    return PA_OK;
+}
+
+}  // extern "C"
+
+// Eq. 2 (MMH): y = sum_i a_i x_i mod 2^gamma - 1, written to y (canonical after
+// the optional zero fix-up when `canonical` is set).
+static int enqueue_mmh(pa_plan_t *pl, const u64 *key, const u64 *seed, u64 *y, bool canonical, void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    int e;
+    if ((e = cudaMemsetAsync(pl->flags, 0, pl->flags_bytes, s))) return e;
+    Operands ops;
+    ops.key = key;
+    ops.seed = seed;
+    ops.y = nullptr;
+    ops.y_zero = nullptr;
+    ops.reload = pl->flags;
+    ops.n = pl->n;
+    ops.gamma = pl->gamma;
+    ops.k = pl->k;
+    ops.mode = 0;
+    const Xform &X = pl->mmh;
+    if ((e = launch_fwd_col(X, ops, (int)(2 * pl->k), pl->Y, stream))) return e;
+    if ((e = launch_row_mac(X, pl->Y, pl->S, stream))) return e;
+    if ((e = launch_inv_col(X, pl->S, pl->Y, nullptr, 0, 0, stream))) return e;
+    CarryDev cd;
+    cd.N = X.N;
+    cd.G = X.G;
+    cd.logN = X.logN;
+    cd.nchunks = X.N / PA_CARRY_D;
+    cd.H = pl->H;
+    cd.state = pl->cstate;
+    cd.cta_state = pl->cta_state;
+    cd.cta_cin = pl->cta_cin;
+    cd.allones = pl->flags + 1;
+    const u64 ywords = (pl->gamma + 63) / 64;
+    if ((e = launch_carry(X, cd, pl->Y, y, ywords, stream))) return e;
+    if (canonical && (e = launch_canonical_zero(pl->flags + 1, y, ywords, stream))) return e;
+    return 0;
+}
+
+// Eq. 4 (MH): out = ((b y + c) mod 2^gamma) >> (gamma - r).
+static int enqueue_mh(pa_plan_t *pl, const u64 *seed, u64 *out, int *status, void *stream) {
+    int e;
+    Operands ops;
+    ops.key = nullptr;
+    ops.seed = seed;
+    ops.y = pl->ybuf;
+    ops.y_zero = pl->flags + 1;
+    ops.reload = pl->flags;
+    ops.n = pl->n;
+    ops.gamma = pl->gamma;
+    ops.k = pl->k;
+    ops.mode = 1;
+    const Xform &X = pl->mh;
+    if ((e = launch_fwd_col(X, ops, 2, pl->Y, stream))) return e;
+    if ((e = launch_row_mac(X, pl->Y, pl->S, stream))) return e;
+    if ((e = launch_inv_col(X, pl->S, pl->Y, seed, (pl->k + 1) * (u64)pl->gamma, pl->gamma, stream))) return e;
+    CarryDev cd;
+    cd.N = X.N;
+    cd.G = X.G;
+    cd.logN = X.logN;
+    cd.nchunks = X.N / PA_CARRY_D;
+    cd.H = pl->H;
+    cd.state = pl->cstate;
+    cd.cta_state = pl->cta_state;
+    cd.cta_cin = pl->cta_cin;
+    cd.allones = pl->flags + 2;
+    if ((e = launch_carry(X, cd, pl->Y, pl->tbuf, (2ULL * pl->gamma + 63) / 64, stream))) return e;
+    if ((e = launch_extract(pl->tbuf, pl->gamma, pl->r, pl->flags, pl->k, out, status, stream))) return e;
+    return 0;
+}
+
+static int cuda_rc(int e) { return e ? PA_ERR_CUDA : PA_OK; }
+
+extern "C" {
+
+int pa_hash(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint64_t *out, int *status, void *stream) {
+    if (!pl || !key || !seed || !out) return PA_ERR_INVALID;
+    int e = enqueue_mmh(pl, (const u64 *)key, (const u64 *)seed, pl->ybuf, false, stream);
+    if (!e) e = enqueue_mh(pl, (const u64 *)seed, (u64 *)out, status, stream);
+    return cuda_rc(e);
+}
+
+int pa_debug_mmh(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint64_t *y, int *status, void *stream) {
+    if (!pl || !key || !seed || !y) return PA_ERR_INVALID;
+    int e = enqueue_mmh(pl, (const u64 *)key, (const u64 *)seed, (u64 *)y, true, stream);
+    if (!e && status) e = cudaMemcpyAsync(status, pl->flags, sizeof(int), cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+    return cuda_rc(e);
+}
+
+int pa_hash_host(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint64_t *out, void *stream) {
+    if (!pl || !key || !seed || !out) return PA_ERR_INVALID;
+    const size_t kw = (pl->n + 63) / 64, sw = ((pl->k + 2) * pl->gamma + 63) / 64, ow = (pl->r + 63) / 64;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!pl->dkey) {
+        void *d = nullptr;
+        if (cudaMalloc(&d, (kw + sw + ow + 1) * 8) != cudaSuccess) return PA_ERR_NOMEM;
+        pl->ws_allocs.push_back(d);
+        pl->dkey = (u64 *)d;
+        pl->dseed = pl->dkey + kw;
+        pl->dout = pl->dseed + sw;
+        pl->dstatus = (int *)(pl->dout + ow);
+    }
+    int e;
+    if ((e = cudaMemcpyAsync(pl->dkey, key, kw * 8, cudaMemcpyHostToDevice, s))) return PA_ERR_CUDA;
+    if ((e = cudaMemcpyAsync(pl->dseed, seed, sw * 8, cudaMemcpyHostToDevice, s))) return PA_ERR_CUDA;
+    int rc = pa_hash(pl, (const uint64_t *)pl->dkey, (const uint64_t *)pl->dseed, (uint64_t *)pl->dout, pl->dstatus, stream);
+    if (rc) return rc;
+    if ((e = cudaMemcpyAsync(out, pl->dout, ow * 8, cudaMemcpyDeviceToHost, s))) return PA_ERR_CUDA;
+    int st = 0;
+    if ((e = cudaMemcpyAsync(&st, pl->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s))) return PA_ERR_CUDA;
+    if ((e = cudaStreamSynchronize(s))) return PA_ERR_CUDA;
+    return st ? PA_RELOAD : PA_OK;
+}
+
+const char *pa_status_string(int code) {
+    switch (code) {
+        case PA_OK: return "ok";
+        case PA_RELOAD: return "reload: a key slice equals 2^gamma - 1";
+        case PA_ERR_INVALID: return "invalid argument";
+        case PA_ERR_NOMEM: return "out of memory";
+        case PA_ERR_CUDA: return "CUDA error";
+        case PA_ERR_TIMEOUT: return "timeout";
+        case PA_ERR_BUDGET: return "job exceeds the HBM budget";
+        case PA_ERR_CANCELLED: return "cancelled";
+        case PA_ERR_UNSUPPORTED: return "unsupported size";
+        case PA_ERR_BUSY: return "busy / not ready";
+        default: return "unknown";
+    }
+}
+
+const char *pa_version(void) { return "pa_gb300 0.1 (sm_103a)"; }
+
+// Workspace bytes pa_plan would allocate for (n, r), without allocating.
+int pa_plan_estimate_bytes(uint64_t n_bits, uint64_t r_bits, const pa_params *params, uint64_t *bytes) {
+    if (!bytes || n_bits == 0 || r_bits == 0) return PA_ERR_INVALID;
+    uint32_t gamma, l1, l2;
+    int rc = choose_gamma(r_bits, params, &gamma);
+    if (rc) return rc;
+    const uint64_t k = (n_bits + gamma - 1) / gamma;
+    if ((rc = choose_len(gamma, k, &l1)) || (rc = choose_len(2ULL * gamma, 1, &l2))) return rc;
+    *bytes = ws_sizes(gamma, k, 1ULL << l1, 1ULL << l2).total();
+    return PA_OK;
+}
+
+// Field constants for host-side checks: omega_N (order N) and theta_N (theta^N = 2).
+int pa_field_constants(uint32_t log_n, uint64_t *omega, uint64_t *theta) {
+    if (log_n > 26 || !omega || !theta) return PA_ERR_INVALID;
+    *omega = root_of_unity(log_n);
+    *theta = root_of_two(log_n);
+    return PA_OK;
+}
+
+// Digit split chosen for a modulus of G bits and K operand pairs.
+int pa_transform_len(uint64_t G, uint64_t K, uint32_t *log_n) {
+    if (!log_n || G == 0 || K == 0) return PA_ERR_INVALID;
+    return choose_len(G, K, log_n);
+}
+
+}  // extern "C"

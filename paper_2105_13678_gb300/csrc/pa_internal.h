@@ -1,0 +1,138 @@
+// pa_internal.h -- shared definitions of the GB300 MMH-MH library (not part of the ABI).
+//
+// Arithmetic model.  Every large product of Algorithm 1 is an exact cyclic
+// convolution computed with a number-theoretic transform over the prime
+//   q = 2^64 - 2^32 + 1  ("Goldilocks"),
+// using the irrational-base discrete weighted transform (Crandall and Fagin,
+// Math. Comp. 62 (1994)): a G-bit operand is cut into N digits, digit j
+// holding bits [s_j, s_{j+1}) with s_j = ceil(G j / N), and digit j is
+// multiplied by the weight theta^((-G j) mod N) where theta^N = 2 in F_q.  The
+// cyclic convolution of the weighted digits, un-weighted, then equals the
+// product modulo 2^G - 1.  With G = gamma this is exactly the reduction mod
+// the Mersenne prime p of Eq. 2; with G = 2 gamma it is the exact product b*y
+// needed by Eq. 4 (b*y + c < 2^(2 gamma) - 1).  theta exists for N <= 2^26
+// because 2 has multiplicative order 192 in F_q.
+#pragma once
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define PA_HD __host__ __device__ __forceinline__
+#else
+#define PA_HD inline
+#endif
+
+namespace pa {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+constexpr u64 GL_Q = 0xFFFFFFFF00000001ULL;  // 2^64 - 2^32 + 1
+constexpr u64 GL_EPS = 0xFFFFFFFFULL;        // 2^64 mod q
+
+// a, b canonical (< q) -> canonical sum.
+PA_HD u64 gl_add(u64 a, u64 b) {
+    u64 s = a + b;
+    if (s < a) s += GL_EPS;  // wrapped: add 2^64 mod q (result is then < q)
+    if (s >= GL_Q) s -= GL_Q;
+    return s;
+}
+
+PA_HD u64 gl_sub(u64 a, u64 b) {
+    u64 d = a - b;
+    if (a < b) d -= GL_EPS;  // wrapped: subtract 2^64 mod q, i.e. add q
+    return d;
+}
+
+// (hi * 2^64 + lo) mod q, canonical.  2^64 = 2^32 - 1 and 2^96 = -1 (mod q).
+PA_HD u64 gl_reduce128(u64 lo, u64 hi) {
+    u64 hh = hi >> 32, hl = hi & 0xFFFFFFFFULL;
+    u64 t = lo - hh;
+    if (lo < hh) t -= GL_EPS;
+    u64 u = (hl << 32) - hl;
+    u64 r = t + u;
+    if (r < u) r += GL_EPS;
+    if (r >= GL_Q) r -= GL_Q;
+    return r;
+}
+
+PA_HD u64 gl_mul(u64 a, u64 b) {
+#if defined(__CUDA_ARCH__)
+    return gl_reduce128(a * b, __umul64hi(a, b));
+#else
+    unsigned __int128 p = (unsigned __int128)a * b;
+    return gl_reduce128((u64)p, (u64)(p >> 64));
+#endif
+}
+
+inline u64 gl_pow(u64 b, u64 e) {
+    u64 r = 1;
+    while (e) {
+        if (e & 1) r = gl_mul(r, b);
+        b = gl_mul(b, b);
+        e >>= 1;
+    }
+    return r;
+}
+
+inline u64 gl_inv(u64 a) { return gl_pow(a, GL_Q - 2); }
+
+// ------------------------------------------------------------------ plans --
+
+// One weighted cyclic transform of length N = R * C over F_q.  All tables are
+// device pointers owned by the plan.
+struct Xform {
+    u64 N;       // transform length (power of two)
+    u64 G;       // the modulus is 2^G - 1; digit j holds bits [s_j, s_{j+1})
+    u32 logN, logR, logC, R, C;
+    u32 hb;      // split of the two-level tables: e = hi * 2^hb + lo
+    u32 tc;      // columns per CTA tile in the column passes
+    u32 K;       // operand pairs accumulated in the transform domain
+    const u64 *twR, *itwR;           // omega_R^e, omega_R^-e, e < R/2
+    const u64 *twC, *itwC;           // omega_C^e, omega_C^-e, e < C/2
+    const u64 *ipw_lo, *ipw_hi;      // omega_N^e (two-level), e < N
+    const u64 *iipw_lo, *iipw_hi;    // omega_N^-e
+    const u64 *wt_lo, *wt_hi;        // theta^e
+    const u64 *iwt_lo, *iwt_hi;      // theta^-e / N
+};
+
+// Where the digits of operand o come from.
+struct Operands {
+    const u64 *key;     // Eq. 2 key, n bits
+    const u64 *seed;    // (k+2) gamma bits: a_1..a_k, b, c
+    const u64 *y;       // Eq. 4 input (MMH value), gamma bits
+    const int *y_zero;  // if *y_zero != 0, y is p itself and reads as 0
+    int *reload;        // per-slice all-ones flags (Alg. 1 lines 3-4)
+    u64 n, gamma, k;
+    int mode;           // 0: MMH (x_1..x_k then a_1..a_k), 1: MH (y, b)
+};
+
+// Carry resolution of N digits (value mod 2^G - 1, end-around carry).
+struct CarryDev {
+    u64 N, G;
+    u32 logN;
+    u64 nchunks;          // N / PA_CARRY_D
+    u64 *H;               // chunk carry-outs (multi-bit), nchunks
+    unsigned char *state; // chunk G/P state, nchunks
+    unsigned char *cta_state, *cta_cin;
+    int *allones;         // set when the resolved value is 2^G - 1 (== 0)
+};
+
+constexpr u32 PA_CARRY_D = 16;     // digits per thread chunk
+constexpr u32 PA_CARRY_T = 256;    // threads per CTA in the carry kernels
+constexpr u32 PA_COL_T = 256;      // threads per CTA in the column passes
+constexpr u32 PA_MAX_LOGN = 24;    // largest transform the kernels implement
+constexpr u32 PA_MAX_LOGR = 11;    // column length cap (smem tile R x tc)
+
+// Kernel launch wrappers (pa_kernels.cu).  All return a cudaError_t as int.
+int prepare_kernels();
+int launch_fwd_col(const Xform &X, const Operands &S, int num_operands, u64 *Y, void *stream);
+int launch_row_mac(const Xform &X, const u64 *Y, u64 *S, void *stream);
+int launch_inv_col(const Xform &X, const u64 *S, u64 *Z, const u64 *add_src, u64 add_base,
+                   u64 add_len, void *stream);
+int launch_carry(const Xform &X, const CarryDev &cd, u64 *z, u64 *out_bits, u64 out_words,
+                 void *stream);
+int launch_extract(const u64 *t, u64 gamma, u64 r, const int *reload, u64 k, u64 *out,
+                   int *status, void *stream);
+int launch_canonical_zero(const int *flag, u64 *y, u64 words, void *stream);
+
+}  // namespace pa

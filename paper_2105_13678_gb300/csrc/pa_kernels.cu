@@ -1,0 +1,695 @@
+// pa_kernels.cu -- sm_103a kernels of the MMH-MH privacy-amplification hash.
+//
+// Data path of one block (Algorithm 1, Sec. 3.1), all integer arithmetic:
+//   k_fwd_col   unpack gamma-bit slices into weighted digits, column NTTs of
+//               the four-step transform, inter-pass twiddles       (Eq. 2/4 inputs)
+//   k_row_mac   row NTTs of each operand pair, transform-domain
+//               multiply-accumulate sum_i A_i * X_i, inverse row NTTs (Eq. 2)
+//   k_inv_col   inverse column NTTs, un-weighting, 1/N, (+ c for Eq. 4)
+//   k_carry_*   exact carry resolution of the digit vector modulo 2^G - 1
+//               (the Mersenne reduction of Sec. 3.1 happens here as an
+//               end-around carry)
+//   k_extract   z = bits [gamma - r, gamma) of b*y + c              (Eq. 4)
+#include <cuda_runtime.h>
+
+#include "pa_internal.h"
+
+namespace pa {
+
+// ------------------------------------------------------------- helpers --
+
+__device__ __forceinline__ u32 pidx(u32 i) { return i + (i >> 4); }  // 1 pad word per 16
+
+__device__ __forceinline__ u32 bitrev(u32 x, u32 bits) { return bits ? (__brev(x) >> (32 - bits)) : 0u; }
+
+__device__ __forceinline__ u64 tbl2(const u64 *__restrict__ lo, const u64 *__restrict__ hi, u64 e, u32 hb) {
+    return gl_mul(__ldg(lo + (e & ((1ULL << hb) - 1))), __ldg(hi + (e >> hb)));
+}
+
+__device__ __forceinline__ u64 digit_start(u64 G, u64 j, u64 N, u32 logN) { return (G * j + N - 1) >> logN; }
+
+// nb in [1, 63] bits starting at absolute bit position pos.
+__device__ __forceinline__ u64 read_bits(const u64 *__restrict__ src, u64 pos, u32 nb) {
+    const u64 wi = pos >> 6;
+    const u32 sh = (u32)(pos & 63);
+    u64 v = __ldg(src + wi) >> sh;
+    if (sh + nb > 64) v |= __ldg(src + wi + 1) << (64 - sh);
+    return v & ((1ULL << nb) - 1);
+}
+
+// Radix-2 decimation-in-frequency stages s0 .. s0+NS-1 of a length-L
+// transform on the 2^NS elements base + m*stride held in v (lo = base mod
+// stride).  Stage s pairs (i, i + L/2^(s+1)) with twiddle
+// omega_L^((i mod L/2^(s+1)) * 2^s) (Gentleman-Sande).
+template <int NS>
+__device__ __forceinline__ void dif_regs(u64 (&v)[8], u32 s0, u32 lo, u32 stride, const u64 *__restrict__ tw) {
+#pragma unroll
+    for (int sg = 0; sg < NS; sg++) {
+        const int half = 1 << (NS - 1 - sg);
+#pragma unroll
+        for (int m = 0; m < (1 << NS); m++) {
+            if (m & half) continue;
+            const u32 e = (lo + (u32)(m & (half - 1)) * stride) << (s0 + sg);
+            const u64 a = v[m], b = v[m + half];
+            v[m] = gl_add(a, b);
+            v[m + half] = gl_mul(gl_sub(a, b), __ldg(tw + e));
+        }
+    }
+}
+
+// Inverse of dif_regs up to a factor 2 per stage (decimation in time,
+// stages in reverse order, inverse twiddles).
+template <int NS>
+__device__ __forceinline__ void dit_regs(u64 (&v)[8], u32 s0, u32 lo, u32 stride, const u64 *__restrict__ itw) {
+#pragma unroll
+    for (int sg = NS - 1; sg >= 0; sg--) {
+        const int half = 1 << (NS - 1 - sg);
+#pragma unroll
+        for (int m = 0; m < (1 << NS); m++) {
+            if (m & half) continue;
+            const u32 e = (lo + (u32)(m & (half - 1)) * stride) << (s0 + sg);
+            const u64 a = v[m], b = gl_mul(v[m + half], __ldg(itw + e));
+            v[m] = gl_add(a, b);
+            v[m + half] = gl_sub(a, b);
+        }
+    }
+}
+
+// ------------------------------------------------------------- operands --
+
+struct OpDesc {
+    const u64 *src;
+    u64 base, len;  // operand = bits [base, base + len) of src, zero above len
+    int force_odd, check_ones, zero;
+};
+
+// Alg. 1 lines 1-2 and the seed layout: MMH operand o < k is key slice x_{o+1},
+// o >= k is seed slice a_{o-k+1}; MH operand 0 is y, operand 1 is b (odd).
+__device__ __forceinline__ OpDesc op_desc(const Operands &S, u32 o) {
+    OpDesc d;
+    d.force_odd = 0;
+    d.check_ones = 0;
+    d.zero = 0;
+    if (S.mode == 0) {
+        if (o < S.k) {
+            d.src = S.key;
+            d.base = (u64)o * S.gamma;
+            const u64 rem = S.n - d.base;
+            d.len = rem < S.gamma ? rem : S.gamma;
+            d.check_ones = 1;
+        } else {
+            d.src = S.seed;
+            d.base = (u64)(o - S.k) * S.gamma;
+            d.len = S.gamma;
+        }
+    } else {
+        if (o == 0) {
+            d.src = S.y;
+            d.base = 0;
+            d.len = S.gamma;
+            d.zero = (*S.y_zero != 0);
+        } else {
+            d.src = S.seed;
+            d.base = S.k * S.gamma;
+            d.len = S.gamma;
+            d.force_odd = 1;
+        }
+    }
+    return d;
+}
+
+// Weighted digit j of an operand: digit * theta^((-G j) mod N).
+__device__ __forceinline__ u64 weighted_digit(const Xform &X, const OpDesc &d, u64 j, bool &ones) {
+    const u64 slo = digit_start(X.G, j, X.N, X.logN);
+    const u64 shi = digit_start(X.G, j + 1, X.N, X.logN);
+    const u64 hi = shi < d.len ? shi : d.len;
+    u64 dig = 0;
+    if (slo < hi) dig = read_bits(d.src, d.base + slo, (u32)(hi - slo));
+    const u32 width = (u32)(shi - slo);
+    ones = ones && (shi <= d.len) && (dig == ((1ULL << width) - 1));
+    if (d.force_odd && j == 0) dig |= 1;
+    if (d.zero) dig = 0;
+    if (dig == 0) return 0;
+    const u64 e = (0ULL - X.G * j) & (X.N - 1);
+    return gl_mul(dig, tbl2(X.wt_lo, X.wt_hi, e, X.hb));
+}
+
+// ------------------------------------------------------ forward columns --
+
+template <int NS>
+__device__ __forceinline__ void fwd_col_round(const Xform &X, const OpDesc &d, u64 *__restrict__ sm,
+                                              u64 *__restrict__ Yo, u32 c0, u32 s0, bool first, bool last,
+                                              bool &ones) {
+    const u32 l = X.logR, tc = X.tc;
+    const u32 sh = l - s0 - NS, stride = 1u << sh;
+    const u32 ntask = (X.R >> NS) * tc;
+    const u32 logtc = __ffs(tc) - 1;
+    for (u32 task = threadIdx.x; task < ntask; task += blockDim.x) {
+        const u32 c = task & (tc - 1), g = task >> logtc;
+        const u32 lo = g & (stride - 1), base = ((g >> sh) << (l - s0)) + lo;
+        u64 v[8];
+#pragma unroll
+        for (int m = 0; m < (1 << NS); m++) {
+            const u32 r = base + m * stride;
+            v[m] = first ? weighted_digit(X, d, (u64)r * X.C + c0 + c, ones) : sm[pidx(r * tc + c)];
+        }
+        dif_regs<NS>(v, s0, lo, stride, X.twR);
+#pragma unroll
+        for (int m = 0; m < (1 << NS); m++) {
+            const u32 r = base + m * stride;
+            if (last) {
+                // position r holds column frequency bitrev(r): twiddle omega_N^(c * k_r)
+                const u64 e = (u64)(c0 + c) * bitrev(r, l);
+                Yo[(u64)r * X.C + c0 + c] = gl_mul(v[m], tbl2(X.ipw_lo, X.ipw_hi, e, X.hb));
+            } else {
+                sm[pidx(r * tc + c)] = v[m];
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(PA_COL_T) k_fwd_col(Xform X, Operands S, u64 *__restrict__ Y) {
+    extern __shared__ u64 sm[];
+    const u32 tc = X.tc, c0 = blockIdx.x * tc, o = blockIdx.y;
+    const OpDesc d = op_desc(S, o);
+    u64 *Yo = Y + (u64)o * X.N;
+    bool ones = true;
+    const u32 l = X.logR;
+    if (l == 0) {
+        for (u32 c = threadIdx.x; c < tc; c += blockDim.x) Yo[c0 + c] = weighted_digit(X, d, c0 + c, ones);
+    } else {
+        const u32 nr = (l + 2) / 3;
+        for (u32 rd = 0; rd < nr; rd++) {
+            const u32 s0 = 3 * rd, ns = min(3u, l - s0);
+            const bool first = rd == 0, last = rd == nr - 1;
+            if (ns == 3)
+                fwd_col_round<3>(X, d, sm, Yo, c0, s0, first, last, ones);
+            else if (ns == 2)
+                fwd_col_round<2>(X, d, sm, Yo, c0, s0, first, last, ones);
+            else
+                fwd_col_round<1>(X, d, sm, Yo, c0, s0, first, last, ones);
+            __syncthreads();
+        }
+    }
+    if (d.check_ones) {
+        // Alg. 1 lines 3-4: slice o is all ones iff every CTA of the slice saw only ones.
+        const int all = __syncthreads_and(ones ? 1 : 0);
+        if (threadIdx.x == 0 && all) {
+            int *cnt = S.reload + 4 + o;
+            if (atomicAdd(cnt, 1) + 1 == (int)gridDim.x) atomicExch(S.reload, 1);
+        }
+    }
+}
+
+// --------------------------------------------------- rows + MAC (Eq. 2) --
+
+template <int NS, int ACC>
+__device__ __forceinline__ void row_fwd_round(const Xform &X, const u64 *__restrict__ xrow,
+                                              const u64 *__restrict__ arow, u64 *__restrict__ smx,
+                                              u64 *__restrict__ sma, u32 s0, bool first, bool last, u64 (&acc)[ACC]) {
+    const u32 l = X.logC, sh = l - s0 - NS, stride = 1u << sh, ngroups = X.C >> NS;
+#pragma unroll
+    for (int t = 0; t < (ACC >> NS); t++) {
+        const u32 g = threadIdx.x + t * blockDim.x;
+        if (g < ngroups) {
+            const u32 lo = g & (stride - 1), base = ((g >> sh) << (l - s0)) + lo;
+            u64 vx[8], va[8];
+#pragma unroll
+            for (int m = 0; m < (1 << NS); m++) {
+                const u32 idx = base + m * stride;
+                vx[m] = first ? __ldg(xrow + idx) : smx[pidx(idx)];
+                va[m] = first ? __ldg(arow + idx) : sma[pidx(idx)];
+            }
+            dif_regs<NS>(vx, s0, lo, stride, X.twC);
+            dif_regs<NS>(va, s0, lo, stride, X.twC);
+#pragma unroll
+            for (int m = 0; m < (1 << NS); m++) {
+                const u32 idx = base + m * stride;
+                if (last) {
+                    acc[t * (1 << NS) + m] = gl_add(acc[t * (1 << NS) + m], gl_mul(vx[m], va[m]));
+                } else {
+                    smx[pidx(idx)] = vx[m];
+                    sma[pidx(idx)] = va[m];
+                }
+            }
+        }
+    }
+}
+
+template <int NS, int ACC>
+__device__ __forceinline__ void row_inv_round(const Xform &X, u64 *__restrict__ sm, u64 *__restrict__ Srow, u32 row,
+                                              u32 s0, bool from_acc, bool to_global, const u64 (&acc)[ACC]) {
+    const u32 l = X.logC, sh = l - s0 - NS, stride = 1u << sh, ngroups = X.C >> NS;
+    const u32 kr = bitrev(row, X.logR);
+#pragma unroll
+    for (int t = 0; t < (ACC >> NS); t++) {
+        const u32 g = threadIdx.x + t * blockDim.x;
+        if (g < ngroups) {
+            const u32 lo = g & (stride - 1), base = ((g >> sh) << (l - s0)) + lo;
+            u64 v[8];
+#pragma unroll
+            for (int m = 0; m < (1 << NS); m++)
+                v[m] = from_acc ? acc[t * (1 << NS) + m] : sm[pidx(base + m * stride)];
+            dit_regs<NS>(v, s0, lo, stride, X.itwC);
+#pragma unroll
+            for (int m = 0; m < (1 << NS); m++) {
+                const u32 idx = base + m * stride;
+                if (to_global) {
+                    const u64 e = (u64)idx * kr;  // omega_N^(-c * k_r)
+                    Srow[idx] = gl_mul(v[m], tbl2(X.iipw_lo, X.iipw_hi, e, X.hb));
+                } else {
+                    sm[pidx(idx)] = v[m];
+                }
+            }
+        }
+    }
+}
+
+#define PA_DISPATCH_NS(ns, call_tmpl)  \
+    do {                               \
+        if ((ns) == 3) {               \
+            call_tmpl(3);              \
+        } else if ((ns) == 2) {        \
+            call_tmpl(2);              \
+        } else {                       \
+            call_tmpl(1);              \
+        }                              \
+    } while (0)
+
+// One CTA per row; blockDim = C / ACC threads, each owning ACC accumulators.
+template <int ACC>
+__global__ void __launch_bounds__(512) k_row_mac(Xform X, const u64 *__restrict__ Y, u64 *__restrict__ S) {
+    extern __shared__ u64 sm[];
+    const u32 C = X.C, row = blockIdx.x, l = X.logC;
+    const u64 N = X.N;
+    u64 *smx = sm, *sma = sm + pidx(C);
+    if (l == 0) {
+        if (threadIdx.x == 0) {
+            u64 s = 0;
+            for (u32 i = 0; i < X.K; i++)
+                s = gl_add(s, gl_mul(Y[(u64)i * N + row], Y[(u64)(X.K + i) * N + row]));
+            S[row] = s;
+        }
+        return;
+    }
+    u64 acc[ACC];
+#pragma unroll
+    for (int m = 0; m < ACC; m++) acc[m] = 0;
+    const u32 nr = (l + 2) / 3;
+    for (u32 i = 0; i < X.K; i++) {
+        const u64 *xrow = Y + (u64)i * N + (u64)row * C;
+        const u64 *arow = Y + (u64)(X.K + i) * N + (u64)row * C;
+        for (u32 rd = 0; rd < nr; rd++) {
+            const u32 s0 = 3 * rd, ns = min(3u, l - s0);
+            const bool first = rd == 0, last = rd == nr - 1;
+#define PA_ROW_FWD(NSV) row_fwd_round<NSV, ACC>(X, xrow, arow, smx, sma, s0, first, last, acc)
+            PA_DISPATCH_NS(ns, PA_ROW_FWD);
+#undef PA_ROW_FWD
+            __syncthreads();
+        }
+    }
+    u64 *Srow = S + (u64)row * C;
+    for (int rd = (int)nr - 1; rd >= 0; rd--) {
+        const u32 s0 = 3 * rd, ns = min(3u, l - s0);
+        const bool from_acc = rd == (int)nr - 1, to_global = rd == 0;
+#define PA_ROW_INV(NSV) row_inv_round<NSV, ACC>(X, smx, Srow, row, s0, from_acc, to_global, acc)
+        PA_DISPATCH_NS(ns, PA_ROW_INV);
+#undef PA_ROW_INV
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------ inverse columns --
+
+template <int NS>
+__device__ __forceinline__ void inv_col_round(const Xform &X, const u64 *__restrict__ Sg, u64 *__restrict__ sm,
+                                              u64 *__restrict__ Z, u32 c0, u32 s0, bool first, bool last,
+                                              const u64 *__restrict__ add_src, u64 add_base, u64 add_len) {
+    const u32 l = X.logR, tc = X.tc;
+    const u32 sh = l - s0 - NS, stride = 1u << sh;
+    const u32 ntask = (X.R >> NS) * tc;
+    const u32 logtc = __ffs(tc) - 1;
+    for (u32 task = threadIdx.x; task < ntask; task += blockDim.x) {
+        const u32 c = task & (tc - 1), g = task >> logtc;
+        const u32 lo = g & (stride - 1), base = ((g >> sh) << (l - s0)) + lo;
+        u64 v[8];
+#pragma unroll
+        for (int m = 0; m < (1 << NS); m++) {
+            const u32 r = base + m * stride;
+            v[m] = first ? __ldg(Sg + (u64)r * X.C + c0 + c) : sm[pidx(r * tc + c)];
+        }
+        dit_regs<NS>(v, s0, lo, stride, X.itwR);
+#pragma unroll
+        for (int m = 0; m < (1 << NS); m++) {
+            const u32 r = base + m * stride;
+            if (last) {
+                const u64 j = (u64)r * X.C + c0 + c;
+                const u64 e = (0ULL - X.G * j) & (X.N - 1);
+                u64 z = gl_mul(v[m], tbl2(X.iwt_lo, X.iwt_hi, e, X.hb));
+                if (add_src) {
+                    const u64 slo = digit_start(X.G, j, X.N, X.logN);
+                    u64 shi = digit_start(X.G, j + 1, X.N, X.logN);
+                    if (shi > add_len) shi = add_len;
+                    if (slo < shi) z += read_bits(add_src, add_base + slo, (u32)(shi - slo));
+                }
+                Z[j] = z;
+            } else {
+                sm[pidx(r * tc + c)] = v[m];
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(PA_COL_T) k_inv_col(Xform X, const u64 *__restrict__ Sg, u64 *__restrict__ Z,
+                                                      const u64 *__restrict__ add_src, u64 add_base, u64 add_len) {
+    extern __shared__ u64 sm[];
+    const u32 tc = X.tc, c0 = blockIdx.x * tc;
+    const u32 l = X.logR;
+    if (l == 0) {
+        for (u32 c = threadIdx.x; c < tc; c += blockDim.x) {
+            const u64 j = c0 + c;
+            const u64 e = (0ULL - X.G * j) & (X.N - 1);
+            u64 z = gl_mul(Sg[j], tbl2(X.iwt_lo, X.iwt_hi, e, X.hb));
+            if (add_src) {
+                const u64 slo = digit_start(X.G, j, X.N, X.logN);
+                u64 shi = digit_start(X.G, j + 1, X.N, X.logN);
+                if (shi > add_len) shi = add_len;
+                if (slo < shi) z += read_bits(add_src, add_base + slo, (u32)(shi - slo));
+            }
+            Z[j] = z;
+        }
+        return;
+    }
+    const u32 nr = (l + 2) / 3;
+    for (int rd = (int)nr - 1; rd >= 0; rd--) {
+        const u32 s0 = 3 * rd, ns = min(3u, l - s0);
+        const bool first = rd == (int)nr - 1, last = rd == 0;
+#define PA_INV_COL(NSV) inv_col_round<NSV>(X, Sg, sm, Z, c0, s0, first, last, add_src, add_base, add_len)
+        PA_DISPATCH_NS(ns, PA_INV_COL);
+#undef PA_INV_COL
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- carry --
+//
+// Digits z_j (< 2^64) at bit offsets s_j = ceil(G j / N) represent
+// V = sum_j z_j 2^(s_j); the result is V mod (2^G - 1) as G packed bits, with
+// the carry out of bit G-1 wrapping to bit 0 (2^G == 1).  Thread t owns the
+// 16-digit chunk t.  Phase A: chunk carry-outs H_t with zero carry-in, then
+// the chunk's bits with carry-in H_{t-1}; the 1-bit carry that adding H_{t-1}
+// may still produce is summarised as generate / propagate.  Phase B: one warp
+// resolves the CTA-level generate/propagate chain around the ring.  Phase C:
+// every chunk receiving a carry increments its bit range.
+
+__device__ __forceinline__ u32 digit_bits(const CarryDev &cd, u64 j) {
+    return (u32)(digit_start(cd.G, j + 1, cd.N, cd.logN) - digit_start(cd.G, j, cd.N, cd.logN));
+}
+
+__device__ __forceinline__ u64 chunk_carry_out(const CarryDev &cd, const u64 *__restrict__ z, u64 t) {
+    const u64 j0 = t * PA_CARRY_D;
+    unsigned __int128 acc = 0;
+#pragma unroll
+    for (u32 d = 0; d < PA_CARRY_D; d++) {
+        acc += __ldg(z + j0 + d);
+        acc >>= digit_bits(cd, j0 + d);
+    }
+    return (u64)acc;
+}
+
+__global__ void __launch_bounds__(PA_CARRY_T) k_carry_a(CarryDev cd, const u64 *__restrict__ z, u64 *__restrict__ y) {
+    __shared__ u64 Hs[PA_CARRY_T];
+    __shared__ u64 Hprev;
+    __shared__ unsigned wg[PA_CARRY_T / 32], wp[PA_CARRY_T / 32];
+    const u64 t = (u64)blockIdx.x * PA_CARRY_T + threadIdx.x;
+    const u64 j0 = t * PA_CARRY_D;
+    u64 zz[PA_CARRY_D];
+    u32 bd[PA_CARRY_D];
+    const ulonglong2 *z2 = reinterpret_cast<const ulonglong2 *>(z + j0);
+#pragma unroll
+    for (u32 d = 0; d < PA_CARRY_D / 2; d++) {
+        const ulonglong2 w = __ldg(z2 + d);
+        zz[2 * d] = w.x;
+        zz[2 * d + 1] = w.y;
+    }
+    u64 s = digit_start(cd.G, j0, cd.N, cd.logN);
+    const u64 s_begin = s;
+#pragma unroll
+    for (u32 d = 0; d < PA_CARRY_D; d++) {
+        const u64 s1 = digit_start(cd.G, j0 + d + 1, cd.N, cd.logN);
+        bd[d] = (u32)(s1 - s);
+        s = s1;
+    }
+    unsigned __int128 acc = 0;
+#pragma unroll
+    for (u32 d = 0; d < PA_CARRY_D; d++) {
+        acc += zz[d];
+        acc >>= bd[d];
+    }
+    const u64 Ht = (u64)acc;
+    Hs[threadIdx.x] = Ht;
+    cd.H[t] = Ht;
+    if (threadIdx.x == 0) Hprev = chunk_carry_out(cd, z, t == 0 ? cd.nchunks - 1 : t - 1);
+    __syncthreads();
+    const u64 Hin = threadIdx.x ? Hs[threadIdx.x - 1] : Hprev;
+
+    acc = Hin;
+    bool ones = true;
+    u64 wi = s_begin >> 6, wv = 0;
+    u32 bo = (u32)(s_begin & 63);
+#pragma unroll
+    for (u32 d = 0; d < PA_CARRY_D; d++) {
+        acc += zz[d];
+        const u64 mask = (1ULL << bd[d]) - 1;
+        const u64 bits = (u64)acc & mask;
+        ones = ones && (bits == mask);
+        acc >>= bd[d];
+        wv |= bits << bo;
+        const u32 nb = bo + bd[d];
+        if (nb >= 64) {
+            atomicOr(y + wi, wv);
+            wi++;
+            wv = (nb > 64) ? (bits >> (64 - bo)) : 0;
+            bo = nb - 64;
+        } else {
+            bo = nb;
+        }
+    }
+    if (bo) atomicOr(y + wi, wv);
+    const bool g = (u64)acc != Ht;  // acc == H_t + (carry from adding H_{t-1})
+    const bool p = !g && ones;
+    cd.state[t] = (unsigned char)((g ? 1 : 0) | (p ? 2 : 0));
+
+    const unsigned gm = __ballot_sync(0xFFFFFFFFu, g), pm = __ballot_sync(0xFFFFFFFFu, p);
+    if ((threadIdx.x & 31) == 0) {
+        wg[threadIdx.x >> 5] = (unsigned)((((u64)(gm | pm)) + gm) >> 32);
+        wp[threadIdx.x >> 5] = (pm == 0xFFFFFFFFu);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned G = 0, P = 1;
+        for (u32 w = 0; w < PA_CARRY_T / 32; w++) {
+            G = wg[w] | (wp[w] & G);
+            P = wp[w] & P;
+        }
+        cd.cta_state[blockIdx.x] = (unsigned char)(G | (P << 1));
+    }
+}
+
+// One warp: carry into every CTA range, closed around the ring.
+__global__ void k_carry_b(CarryDev cd, u32 nctas) {
+    const u32 lane = threadIdx.x;
+    unsigned cin = 0;
+    for (u32 base = 0; base < nctas; base += 32) {
+        const unsigned st = (base + lane < nctas) ? cd.cta_state[base + lane] : 2u;
+        const unsigned gm = __ballot_sync(0xFFFFFFFFu, st & 1), pm = __ballot_sync(0xFFFFFFFFu, (st >> 1) & 1);
+        cin = (unsigned)((((u64)(gm | pm)) + gm + cin) >> 32);
+    }
+    // cin is now the carry out of the top with carry-in 0: it wraps to bit 0
+    // (if every range propagates, the value is all ones and no carry is taken).
+    unsigned c = cin;
+    for (u32 base = 0; base < nctas; base += 32) {
+        const unsigned st = (base + lane < nctas) ? cd.cta_state[base + lane] : 2u;
+        const unsigned gm = __ballot_sync(0xFFFFFFFFu, st & 1), pm = __ballot_sync(0xFFFFFFFFu, (st >> 1) & 1);
+        const u64 a = gm | pm, sum = a + gm + c;
+        const u64 into = sum ^ a ^ gm;
+        if (base + lane < nctas) cd.cta_cin[base + lane] = (unsigned char)((into >> lane) & 1);
+        c = (unsigned)(sum >> 32);
+    }
+    if (lane == 0) *cd.allones = 1;
+}
+
+__global__ void __launch_bounds__(PA_CARRY_T) k_carry_c(CarryDev cd, u64 *__restrict__ y) {
+    __shared__ unsigned wg[PA_CARRY_T / 32], wp[PA_CARRY_T / 32];
+    const u64 t = (u64)blockIdx.x * PA_CARRY_T + threadIdx.x;
+    const unsigned st = cd.state[t];
+    const unsigned gm = __ballot_sync(0xFFFFFFFFu, st & 1), pm = __ballot_sync(0xFFFFFFFFu, (st >> 1) & 1);
+    const u32 lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        wg[warp] = (unsigned)((((u64)(gm | pm)) + gm) >> 32);
+        wp[warp] = (pm == 0xFFFFFFFFu);
+    }
+    __syncthreads();
+    unsigned cw = cd.cta_cin[blockIdx.x];
+    for (u32 w = 0; w < warp; w++) cw = wg[w] | (wp[w] & cw);
+    const u64 a = gm | pm, sum = a + gm + cw;
+    const bool e = ((sum ^ a ^ gm) >> lane) & 1;
+
+    const u64 j0 = t * PA_CARRY_D;
+    const u64 s_lo = digit_start(cd.G, j0, cd.N, cd.logN);
+    const u64 s_hi = digit_start(cd.G, j0 + PA_CARRY_D, cd.N, cd.logN);
+    bool fin_ones = true, flipping = e;
+    for (u64 wi = s_lo >> 6; (wi << 6) < s_hi; wi++) {
+        const u64 wb = wi << 6;
+        u64 m = ~0ULL;
+        if (s_lo > wb) m &= ~0ULL << (s_lo - wb);
+        if (s_hi < wb + 64) m &= (1ULL << (s_hi - wb)) - 1;
+        const u64 orig = y[wi] & m;
+        u64 flip = 0;
+        if (flipping) {
+            const u64 zeros = ~orig & m;
+            if (zeros) {
+                const u32 pos = __ffsll((long long)zeros) - 1;
+                flip = m & ((2ULL << pos) - 1);
+                flipping = false;
+            } else {
+                flip = m;
+            }
+            atomicXor(y + wi, flip);
+        }
+        fin_ones = fin_ones && (((orig ^ flip) & m) == m);
+    }
+    const int all = __syncthreads_and(fin_ones ? 1 : 0);
+    if (threadIdx.x == 0 && !all) *cd.allones = 0;
+}
+
+// Small transforms: one thread resolves the whole ring sequentially.
+__global__ void k_carry_seq(CarryDev cd, u64 *__restrict__ z, u64 *__restrict__ y) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned __int128 c = 0;
+    for (int pass = 0; pass < 8; pass++) {
+        for (u64 j = 0; j < cd.N; j++) {
+            const u32 b = digit_bits(cd, j);
+            const unsigned __int128 v = (unsigned __int128)z[j] + c;
+            z[j] = (u64)v & ((1ULL << b) - 1);
+            c = v >> b;
+        }
+        if (c == 0) break;
+    }
+    bool ones = true;
+    for (u64 j = 0; j < cd.N; j++) {
+        const u32 b = digit_bits(cd, j);
+        const u64 s = digit_start(cd.G, j, cd.N, cd.logN);
+        ones = ones && z[j] == ((1ULL << b) - 1);
+        if (b) {
+            y[s >> 6] |= z[j] << (s & 63);
+            if ((s & 63) + b > 64) y[(s >> 6) + 1] |= z[j] >> (64 - (s & 63));
+        }
+    }
+    *cd.allones = ones ? 1 : 0;
+}
+
+// -------------------------------------------------------------- extract --
+
+// Eq. 4: out = bits [gamma - r, gamma) of t = b*y + c; zero on reload.
+__global__ void k_extract(const u64 *__restrict__ t, u64 gamma, u64 r, const int *__restrict__ reload,
+                          u64 *__restrict__ out, int *status) {
+    const u64 w = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 nw = (r + 63) >> 6;
+    const bool rl = *reload != 0;
+    if (w < nw) {
+        u64 v = 0;
+        if (!rl) {
+            const u64 lo = gamma - r + (w << 6);
+            const u64 hi = (lo + 64 < gamma) ? lo + 64 : gamma;
+            const u32 nb = (u32)(hi - lo);  // 1..64
+            const u64 wi = lo >> 6;
+            const u32 sh = (u32)(lo & 63);
+            v = __ldg(t + wi) >> sh;
+            if (sh != 0 && sh + nb > 64) v |= __ldg(t + wi + 1) << (64 - sh);
+            if (nb < 64) v &= (1ULL << nb) - 1;
+        }
+        out[w] = v;
+    }
+    if (w == 0 && status) *status = rl ? 1 : 0;
+}
+
+__global__ void k_canonical_zero(const int *__restrict__ flag, u64 *__restrict__ y, u64 words) {
+    if (*flag == 0) return;
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (u64)gridDim.x * blockDim.x) y[i] = 0;
+}
+
+// -------------------------------------------------------------- launchers --
+
+static size_t col_smem(const Xform &X) { return (size_t)((X.R * X.tc) + ((X.R * X.tc) >> 4) + 1) * sizeof(u64); }
+static size_t row_smem(const Xform &X) { return (size_t)2 * (X.C + (X.C >> 4) + 1) * sizeof(u64); }
+
+int prepare_kernels() {
+    static bool done = false;
+    if (done) return 0;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_fwd_col, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024))) return e;
+    if ((e = cudaFuncSetAttribute(k_inv_col, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024))) return e;
+    if ((e = cudaFuncSetAttribute(k_row_mac<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024))) return e;
+    if ((e = cudaFuncSetAttribute(k_row_mac<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024))) return e;
+    done = true;
+    return 0;
+}
+
+int launch_fwd_col(const Xform &X, const Operands &S, int num_operands, u64 *Y, void *stream) {
+    if (int e = prepare_kernels()) return e;
+    dim3 grid(X.C / X.tc, num_operands);
+    k_fwd_col<<<grid, PA_COL_T, col_smem(X), (cudaStream_t)stream>>>(X, S, Y);
+    return (int)cudaGetLastError();
+}
+
+int launch_row_mac(const Xform &X, const u64 *Y, u64 *S, void *stream) {
+    if (int e = prepare_kernels()) return e;
+    if (X.C > 4096) {
+        k_row_mac<16><<<X.R, X.C / 16, row_smem(X), (cudaStream_t)stream>>>(X, Y, S);
+    } else {
+        u32 threads = X.C / 8;
+        if (threads < 32) threads = 32;
+        k_row_mac<8><<<X.R, threads, row_smem(X), (cudaStream_t)stream>>>(X, Y, S);
+    }
+    return (int)cudaGetLastError();
+}
+
+int launch_inv_col(const Xform &X, const u64 *S, u64 *Z, const u64 *add_src, u64 add_base, u64 add_len,
+                   void *stream) {
+    if (int e = prepare_kernels()) return e;
+    k_inv_col<<<X.C / X.tc, PA_COL_T, col_smem(X), (cudaStream_t)stream>>>(X, S, Z, add_src, add_base, add_len);
+    return (int)cudaGetLastError();
+}
+
+int launch_carry(const Xform &X, const CarryDev &cd, u64 *z, u64 *out_bits, u64 out_words, void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(out_bits, 0, out_words * sizeof(u64), s);
+    if (e) return e;
+    const bool parallel = cd.nchunks >= PA_CARRY_T && (X.G >> X.logN) >= 4;
+    if (!parallel) {
+        k_carry_seq<<<1, 32, 0, s>>>(cd, z, out_bits);
+        return (int)cudaGetLastError();
+    }
+    const u32 nctas = (u32)(cd.nchunks / PA_CARRY_T);
+    k_carry_a<<<nctas, PA_CARRY_T, 0, s>>>(cd, z, out_bits);
+    k_carry_b<<<1, 32, 0, s>>>(cd, nctas);
+    k_carry_c<<<nctas, PA_CARRY_T, 0, s>>>(cd, out_bits);
+    return (int)cudaGetLastError();
+}
+
+int launch_extract(const u64 *t, u64 gamma, u64 r, const int *reload, u64 k, u64 *out, int *status, void *stream) {
+    (void)k;
+    const u64 nw = (r + 63) >> 6;
+    const u32 threads = 256;
+    const u64 blocks = (nw + threads - 1) / threads;
+    k_extract<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(t, gamma, r, reload, out, status);
+    return (int)cudaGetLastError();
+}
+
+int launch_canonical_zero(const int *flag, u64 *y, u64 words, void *stream) {
+    k_canonical_zero<<<64, 256, 0, (cudaStream_t)stream>>>(flag, y, words);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace pa

@@ -1,0 +1,151 @@
+"""Bit-exact parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerance: zero differing bits (the hash is an exact integer function)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2105_13678_gb300 import synthetic
+
+from helpers import gpu_hash, oracle_hash_parallel
+
+pytestmark = pytest.mark.gpu
+
+
+def _plan(n, r, gamma=0, margin=128):
+    from paper_2105_13678_gb300 import _lib
+    return _lib.Plan(n, r, gamma=gamma, margin=margin)
+
+
+def _check(n, r, seed_id, gamma=0, margin=128, parallel=False, key=None, hseed=None):
+    plan = _plan(n, r, gamma, margin)
+    g, k = plan.gamma, plan.k
+    assert (g, k) == oracle.plan(n, r, margin=margin, gamma=gamma)
+    if key is None:
+        key, hseed = synthetic.block_inputs(seed_id, n, (k + 2) * g)
+    if parallel:
+        rc, out, y = oracle_hash_parallel(key, n, hseed, r, g, k)
+    else:
+        rc, out, y = oracle.pa_hash(key, n, hseed, r, g, k)
+    st, gout, gy, st2 = gpu_hash(plan, key, hseed)
+    assert st == rc and st2 == rc
+    assert np.array_equal(gout, out), f"output mismatch n={n} r={r} gamma={g} k={k}"
+    if rc == oracle.ORA_OK:
+        assert np.array_equal(gy, y[: gy.size]), f"MMH value mismatch n={n} r={r} gamma={g} k={k}"
+    plan.close()
+    return plan
+
+
+def test_config1_plain_block_2p20():
+    """n = 2^20 uniform bits (splitmix64 seed 1), r = ceil(0.1 n) = 104858."""
+    p = _check(1 << 20, 104858, 1)
+    assert (p.gamma, p.k) == (110503, 10)
+
+
+@pytest.mark.parametrize("gamma", [2, 3, 5, 7, 13, 17, 19, 31, 61, 89, 107, 127, 521, 607, 1279, 2203, 4423])
+def test_small_gammas(gamma):
+    rng = np.random.default_rng(gamma)
+    for n in (gamma, 3 * gamma, 7 * gamma + 1, 40 * gamma - 3):
+        for r in sorted({1, max(1, gamma // 2), gamma - 1}):
+            if r >= gamma:
+                continue
+            _check(n, r, int(rng.integers(1 << 30)), gamma=gamma)
+
+
+@pytest.mark.parametrize("n,r", [(64, 1), (65, 7), (1000, 100), (4096, 1000), (12345, 3000), (100000, 10000),
+                                 (300000, 29000), (2**20 + 17, 50000), (3 * 110503, 100000), (5 * 756839, 300000)])
+def test_ragged_sizes(n, r):
+    _check(n, r, n ^ r)
+
+
+@pytest.mark.parametrize("n,r,gamma", [(10 * 9689, 500, 9689), (5 * 44497, 20000, 44497), (86243, 2000, 86243),
+                                       (1000, 10, 1279)])
+def test_no_padding_and_k1(n, r, gamma):
+    _check(n, r, 77, gamma=gamma)
+
+
+def test_reload_on_all_ones_slice():
+    n, r, gamma = 4 * 4423, 100, 4423
+    plan = _plan(n, r, gamma)
+    k = plan.k
+    key, hseed = synthetic.block_inputs(5, n, (k + 2) * gamma)
+    kv = oracle.words_to_int(key) | (((1 << gamma) - 1) << (2 * gamma))  # slice x_3 all ones
+    key = oracle.int_to_words(kv, key.size)
+    rc, out, _ = oracle.pa_hash(key, n, hseed, r, gamma, k)
+    assert rc == oracle.ORA_RELOAD
+    st, gout, _, _ = gpu_hash(plan, key, hseed)
+    assert st == oracle.ORA_RELOAD and not gout.any()
+
+
+def test_zero_mmh_value_and_all_ones_representation():
+    """Seeds that make y = 0: a = 0, and a pair with a_2 = -a_1, x_2 = x_1 (the
+    carry ring may land on the all-ones representation of 0)."""
+    gamma = 44497
+    n, r = 2 * gamma, 1000
+    plan = _plan(n, r, gamma)
+    k = plan.k
+    key, hseed = synthetic.block_inputs(9, n, (k + 2) * gamma)
+    p = (1 << gamma) - 1
+    sv = oracle.words_to_int(hseed)
+    mask = (1 << (2 * gamma)) - 1
+    for a1, a2, x_same in ((0, 0, False), (12345, p - 12345, True), (1, p - 1, True), (p, 0, False)):
+        s2 = (sv & ~mask) | a1 | (a2 << gamma)
+        seed2 = oracle.int_to_words(s2, hseed.size)
+        key2 = key
+        if x_same:
+            kv = oracle.words_to_int(key)
+            x1 = kv & ((1 << gamma) - 1)
+            key2 = oracle.int_to_words(x1 | (x1 << gamma), key.size)
+        _check(n, r, 0, gamma=gamma, key=key2, hseed=seed2)
+
+
+def test_bits_past_n_ignored():
+    n, r = 100003, 5000
+    plan = _plan(n, r)
+    k, g = plan.k, plan.gamma
+    key, hseed = synthetic.block_inputs(21, n, (k + 2) * g)
+    dirty = key.copy()
+    dirty[-1] |= ~np.uint64((1 << (n % 64)) - 1)
+    st, a, _, _ = gpu_hash(plan, key, hseed)
+    st2, b, _, _ = gpu_hash(plan, dirty, hseed)
+    assert st == st2 == 0 and np.array_equal(a, b)
+
+
+def test_host_entry_point_matches_device():
+    from paper_2105_13678_gb300 import _lib
+    n, r = 1 << 20, 104858
+    plan = _plan(n, r)
+    key, hseed = synthetic.block_inputs(1, n, (plan.k + 2) * plan.gamma)
+    st, out = _lib.pa_hash_host(plan, key, hseed)
+    st2, out2, _, _ = gpu_hash(plan, key, hseed)
+    assert st == st2 == 0 and np.array_equal(out, out2)
+
+
+def test_repeat_calls_identical():
+    n, r = 3_000_000, 300_000
+    plan = _plan(n, r)
+    key, hseed = synthetic.block_inputs(4, n, (plan.k + 2) * plan.gamma)
+    outs = [gpu_hash(plan, key, hseed)[1] for _ in range(3)]
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])
+
+
+@pytest.mark.parametrize("n,r,seed_id", [(10_000_000, 1_000_000, 3), (100_000_000, 10_000_000, 4)])
+def test_sweep_sizes(n, r, seed_id):
+    """Block-size sweep points n = 1e7 and 1e8 (r = 0.1 n, seeds 3, 4)."""
+    _check(n, r, seed_id, parallel=True)
+
+
+@pytest.mark.parametrize("ratio", [0.1, 0.05, 0.3])
+def test_paper_scale_2p6e8(ratio):
+    """Paper-scale block n = 2.6e8 (seed 2) at r/n = 0.1, 0.05, 0.3."""
+    n = 260_000_000
+    r = int(np.ceil(ratio * n))
+    _check(n, r, 2, parallel=True)
+
+
+def test_paper_points_cv_dv():
+    """The paper's unpadded points: CV n = 10 * 25964951, DV n = 3 * 74207281."""
+    for n, ratio in ((10 * 25964951, 0.0972), (3 * 74207281, 0.2957)):
+        r = int(np.floor(ratio * n))
+        p = _check(n, r, 11, parallel=True)
+        assert p.k * p.gamma == n
