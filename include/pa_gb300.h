@@ -135,6 +135,32 @@ int pa_serve_wait(pa_server_t *srv, uint64_t ticket, uint64_t timeout_ns, int *s
 int pa_serve_stats_get(pa_server_t *srv, pa_serve_stats *stats);
 int pa_serve_destroy(pa_server_t *srv); /* cancels queued jobs, waits for running ones */
 
+/* ---- tracing: per-kernel device time ---------------------------------------
+ * pa_trace_enable(1) clears earlier records and brackets every later kernel
+ * launch of the library with a CUDA event pair on its launching stream (not
+ * while the stream is being captured into a graph); pa_trace_enable(0) stops
+ * recording.  pa_trace_collect waits for the recorded events and fills up to
+ * max_entries aggregates, one per kernel and stage ("mmh.row_mac", ...);
+ * *count receives the number of distinct entries. */
+typedef struct pa_trace_entry {
+    char name[32];
+    uint64_t launches;
+    double total_ms;
+} pa_trace_entry;
+int pa_trace_enable(int on);
+int pa_trace_collect(pa_trace_entry *out, int max_entries, int *count);
+
+/* ---- diagnostics for host-side checks (no device work) --------------------
+ * pa_plan_estimate_bytes: device bytes pa_plan would allocate for (n, r).
+ * pa_field_constants: the primitive 2^log_n-th root of unity omega and the
+ *   element theta with theta^(2^log_n) = 2 in F_q, q = 2^64 - 2^32 + 1, that
+ *   the weighted transforms use (log_n <= 26).
+ * pa_transform_len: log2 of the transform length chosen for a modulus of
+ *   2^G - 1 with K accumulated products. */
+int pa_plan_estimate_bytes(uint64_t n_bits, uint64_t r_bits, const pa_params *params, uint64_t *bytes);
+int pa_field_constants(uint32_t log_n, uint64_t *omega, uint64_t *theta);
+int pa_transform_len(uint64_t G, uint64_t K, uint32_t *log_n);
+
 /* Human-readable name of a return code (static string). */
 const char *pa_status_string(int code);
 /* Library version string. */

@@ -55,6 +55,10 @@ class pa_serve_stats(ctypes.Structure):
                 ("peak_budget_bytes", _u64)]
 
 
+class pa_trace_entry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", _u64), ("total_ms", ctypes.c_double)]
+
+
 # name -> (restype, argtypes), in header order
 SIGNATURES = {
     "pa_plan": (ctypes.c_int, [_u64, _u64, ctypes.POINTER(pa_params), ctypes.POINTER(_vp)]),
@@ -72,6 +76,8 @@ SIGNATURES = {
     "pa_serve_wait": (ctypes.c_int, [_vp, _u64, _u64, ctypes.POINTER(ctypes.c_int)]),
     "pa_serve_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(pa_serve_stats)]),
     "pa_serve_destroy": (ctypes.c_int, [_vp]),
+    "pa_trace_enable": (ctypes.c_int, [ctypes.c_int]),
+    "pa_trace_collect": (ctypes.c_int, [ctypes.POINTER(pa_trace_entry), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "pa_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pa_version": (ctypes.c_char_p, []),
     "pa_plan_estimate_bytes": (ctypes.c_int, [_u64, _u64, ctypes.POINTER(pa_params), ctypes.POINTER(_u64)]),
@@ -176,6 +182,18 @@ def pa_hash_batch(plans, key_ptrs, seed_ptrs, out_ptrs, statuses_ptr: int = 0, s
     arr = lambda xs: (_vp * n)(*xs)  # noqa: E731
     return check(lib().pa_hash_batch(arr([p.handle.value for p in plans]), arr(key_ptrs), arr(seed_ptrs),
                                      arr(out_ptrs), statuses_ptr or None, n, stream or None), "pa_hash_batch")
+
+
+def trace_enable(on: bool) -> None:
+    check(lib().pa_trace_enable(1 if on else 0), "pa_trace_enable")
+
+
+def trace_collect() -> dict:
+    """{name: (launches, total_ms)} for the launches recorded since trace_enable(True)."""
+    ent = (pa_trace_entry * 128)()
+    cnt = ctypes.c_int()
+    check(lib().pa_trace_collect(ent, 128, ctypes.byref(cnt)), "pa_trace_collect")
+    return {ent[i].name.decode(): (int(ent[i].launches), float(ent[i].total_ms)) for i in range(min(cnt.value, 128))}
 
 
 def field_constants(log_n: int):

@@ -238,6 +238,8 @@ int pa_plan(uint64_t n_bits, uint64_t r_bits, const pa_params *params, pa_plan_t
     }
     rc = build_xform(pl, pl->mmh, gamma, pl->k);
     if (!rc) rc = build_xform(pl, pl->mh, 2ULL * gamma, 1);
+    pl->mmh.stage = 0;
+    pl->mh.stage = 1;
     if (rc) {
         delete pl;
         return rc;

@@ -87,6 +87,7 @@ struct Xform {
     u32 hb;      // split of the two-level tables: e = hi * 2^hb + lo
     u32 tc;      // columns per CTA tile in the column passes
     u32 K;       // operand pairs accumulated in the transform domain
+    u32 stage;   // 0: MMH (Eq. 2), 1: MH (Eq. 4); used for trace names
     const u64 *twR, *itwR;           // omega_R^e, omega_R^-e, e < R/2
     const u64 *twC, *itwC;           // omega_C^e, omega_C^-e, e < C/2
     const u64 *ipw_lo, *ipw_hi;      // omega_N^e (two-level), e < N
@@ -122,6 +123,10 @@ constexpr u32 PA_CARRY_T = 256;    // threads per CTA in the carry kernels
 constexpr u32 PA_COL_T = 256;      // threads per CTA in the column passes
 constexpr u32 PA_MAX_LOGN = 24;    // largest transform the kernels implement
 constexpr u32 PA_MAX_LOGR = 11;    // column length cap (smem tile R x tc)
+
+// Tracing (pa_trace.cu): event pair around a launch when enabled.
+void *trace_begin(const char *name, u32 stage, void *stream);
+void trace_end(void *token, void *stream);
 
 // Kernel launch wrappers (pa_kernels.cu).  All return a cudaError_t as int.
 int prepare_kernels();

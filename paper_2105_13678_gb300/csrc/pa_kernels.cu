@@ -620,6 +620,17 @@ __global__ void k_canonical_zero(const int *__restrict__ flag, u64 *__restrict__
 }
 
 // -------------------------------------------------------------- launchers --
+//
+// Every launch goes through TRACED(): when tracing is on (pa_trace_enable) and
+// the stream is not being captured, a CUDA event pair is recorded on the
+// launching stream around the kernel.
+
+#define TRACED(name, stage, stream, launch)                      \
+    do {                                                         \
+        void *tr_ = trace_begin((name), (stage), (stream));      \
+        launch;                                                  \
+        trace_end(tr_, (stream));                                \
+    } while (0)
 
 static size_t col_smem(const Xform &X) { return (size_t)((X.R * X.tc) + ((X.R * X.tc) >> 4) + 1) * sizeof(u64); }
 static size_t row_smem(const Xform &X) { return (size_t)2 * (X.C + (X.C >> 4) + 1) * sizeof(u64); }
@@ -639,18 +650,18 @@ int prepare_kernels() {
 int launch_fwd_col(const Xform &X, const Operands &S, int num_operands, u64 *Y, void *stream) {
     if (int e = prepare_kernels()) return e;
     dim3 grid(X.C / X.tc, num_operands);
-    k_fwd_col<<<grid, PA_COL_T, col_smem(X), (cudaStream_t)stream>>>(X, S, Y);
+    TRACED("fwd_col", X.stage, stream, (k_fwd_col<<<grid, PA_COL_T, col_smem(X), (cudaStream_t)stream>>>(X, S, Y)));
     return (int)cudaGetLastError();
 }
 
 int launch_row_mac(const Xform &X, const u64 *Y, u64 *S, void *stream) {
     if (int e = prepare_kernels()) return e;
     if (X.C > 4096) {
-        k_row_mac<16><<<X.R, X.C / 16, row_smem(X), (cudaStream_t)stream>>>(X, Y, S);
+        TRACED("row_mac", X.stage, stream, (k_row_mac<16><<<X.R, X.C / 16, row_smem(X), (cudaStream_t)stream>>>(X, Y, S)));
     } else {
         u32 threads = X.C / 8;
         if (threads < 32) threads = 32;
-        k_row_mac<8><<<X.R, threads, row_smem(X), (cudaStream_t)stream>>>(X, Y, S);
+        TRACED("row_mac", X.stage, stream, (k_row_mac<8><<<X.R, threads, row_smem(X), (cudaStream_t)stream>>>(X, Y, S)));
     }
     return (int)cudaGetLastError();
 }
@@ -658,7 +669,8 @@ int launch_row_mac(const Xform &X, const u64 *Y, u64 *S, void *stream) {
 int launch_inv_col(const Xform &X, const u64 *S, u64 *Z, const u64 *add_src, u64 add_base, u64 add_len,
                    void *stream) {
     if (int e = prepare_kernels()) return e;
-    k_inv_col<<<X.C / X.tc, PA_COL_T, col_smem(X), (cudaStream_t)stream>>>(X, S, Z, add_src, add_base, add_len);
+    TRACED("inv_col", X.stage, stream,
+           (k_inv_col<<<X.C / X.tc, PA_COL_T, col_smem(X), (cudaStream_t)stream>>>(X, S, Z, add_src, add_base, add_len)));
     return (int)cudaGetLastError();
 }
 
@@ -668,13 +680,13 @@ int launch_carry(const Xform &X, const CarryDev &cd, u64 *z, u64 *out_bits, u64 
     if (e) return e;
     const bool parallel = cd.nchunks >= PA_CARRY_T && (X.G >> X.logN) >= 4;
     if (!parallel) {
-        k_carry_seq<<<1, 32, 0, s>>>(cd, z, out_bits);
+        TRACED("carry_seq", X.stage, stream, (k_carry_seq<<<1, 32, 0, s>>>(cd, z, out_bits)));
         return (int)cudaGetLastError();
     }
     const u32 nctas = (u32)(cd.nchunks / PA_CARRY_T);
-    k_carry_a<<<nctas, PA_CARRY_T, 0, s>>>(cd, z, out_bits);
-    k_carry_b<<<1, 32, 0, s>>>(cd, nctas);
-    k_carry_c<<<nctas, PA_CARRY_T, 0, s>>>(cd, out_bits);
+    TRACED("carry_a", X.stage, stream, (k_carry_a<<<nctas, PA_CARRY_T, 0, s>>>(cd, z, out_bits)));
+    TRACED("carry_b", X.stage, stream, (k_carry_b<<<1, 32, 0, s>>>(cd, nctas)));
+    TRACED("carry_c", X.stage, stream, (k_carry_c<<<nctas, PA_CARRY_T, 0, s>>>(cd, out_bits)));
     return (int)cudaGetLastError();
 }
 
@@ -683,12 +695,12 @@ int launch_extract(const u64 *t, u64 gamma, u64 r, const int *reload, u64 k, u64
     const u64 nw = (r + 63) >> 6;
     const u32 threads = 256;
     const u64 blocks = (nw + threads - 1) / threads;
-    k_extract<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(t, gamma, r, reload, out, status);
+    TRACED("extract", 1, stream, (k_extract<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(t, gamma, r, reload, out, status)));
     return (int)cudaGetLastError();
 }
 
 int launch_canonical_zero(const int *flag, u64 *y, u64 words, void *stream) {
-    k_canonical_zero<<<64, 256, 0, (cudaStream_t)stream>>>(flag, y, words);
+    TRACED("canonical_zero", 0, stream, (k_canonical_zero<<<64, 256, 0, (cudaStream_t)stream>>>(flag, y, words)));
     return (int)cudaGetLastError();
 }
 

@@ -1,0 +1,76 @@
+"""Host-side checks of the C-ABI library (no device work): it loads, exports
+every symbol the headers declare, and its host-side plan logic and field
+constants are right."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2105_13678_gb300 import _lib, synthetic
+
+from helpers import oracle_hash_parallel
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+Q = 2**64 - 2**32 + 1
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"^\s*(?:const\s+)?\w[\w\s\*]*?\b(pa_\w+)\s*\(", txt, flags=re.M))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    L = _lib.lib()
+    declared = _declared()
+    assert {"pa_plan", "pa_hash", "pa_hash_batch", "pa_serve_create", "pa_hash_host"} <= declared
+    for name in declared:
+        assert hasattr(L, name), name
+    assert set(_lib.SIGNATURES) >= declared
+
+
+def test_field_constants():
+    for l in range(0, 27):
+        w, t = _lib.field_constants(l)
+        assert pow(t, 1 << l, Q) == 2
+        assert pow(w, 1 << l, Q) == 1
+        if l:
+            assert pow(w, 1 << (l - 1), Q) == Q - 1
+    with pytest.raises(_lib.PAError):
+        _lib.field_constants(27)
+
+
+@pytest.mark.parametrize("G,K", [(110503, 10), (30402457, 9), (60804914, 1), (136279841, 8), (272559682, 1),
+                                 (5, 1), (127, 3), (61, 1000)])
+def test_transform_len_is_smallest_exact(G, K):
+    """The chosen length keeps 2 K N (2^b - 1)^2 + 2^b below q and is minimal."""
+    l = _lib.transform_len(G, K)
+    N = 1 << l
+    b = -(-G // N)
+    assert b <= 31 and 2 * K * N * (2**b - 1) ** 2 + 2**b - 1 < Q
+    if l:
+        N2 = N // 2
+        b2 = -(-G // N2)
+        assert b2 > 31 or 2 * K * N2 * (2**b2 - 1) ** 2 + 2**b2 - 1 >= Q
+
+
+def test_plan_estimate_and_status_strings():
+    assert _lib.plan_estimate_bytes(260_000_000, 26_000_000) > 260_000_000 // 8
+    assert _lib.lib().pa_status_string(1).decode().startswith("reload")
+    with pytest.raises(_lib.PAError):
+        _lib.plan_estimate_bytes(10, 136279841)
+
+
+def test_parallel_oracle_driver_matches_serial():
+    n, r = 1_000_003, 90_000
+    g, k = oracle.plan(n, r)
+    key, seed = synthetic.block_inputs(31, n, (k + 2) * g)
+    rc, out, y = oracle.pa_hash(key, n, seed, r, g, k)
+    rc2, out2, y2 = oracle_hash_parallel(key, n, seed, r, g, k, workers=3)
+    assert rc == rc2 == 0 and np.array_equal(out, out2) and np.array_equal(y, y2)
