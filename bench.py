@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the CPU baseline, batched and served measurements")
     ap.add_argument("--served-jobs", type=int, default=2000)
+    ap.add_argument("--n-bits", type=int, default=N_BITS, help="block size (profiling runs use smaller blocks)")
+    ap.add_argument("--ratio", type=float, default=RATIO, help="r / n")
     return ap.parse_args()
 
 
@@ -151,8 +153,8 @@ def run_gb300(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    n = N_BITS
-    r = int(math.ceil(RATIO * n))
+    n = args.n_bits
+    r = int(math.ceil(args.ratio * n))
     plan = _lib.Plan(n, r)
     info = plan.info
     block_seed = 2 if rank == 0 else (2 << 32) + rank
@@ -244,7 +246,7 @@ def run_gb300(args):
         "vs_baseline": None,
         "dtype": "u64 (exact integer, F_q NTT)",
         "data": "synthetic uniform random key and seed bits (splitmix64 seed 2)",
-        "config": {"workload": "plain single block n=2.6e8 bits, r=0.1n=2.6e7 (seed 2)",
+        "config": {"workload": f"plain single block n={n:.3g} bits, r={args.ratio:g}n={r} (seed 2)",
                    "n_bits": n, "r_bits": r, "gamma": plan.gamma, "k": plan.k,
                    "mmh_transform_len": info.mmh_len, "mh_transform_len": info.mh_len,
                    "parallelism": f"replicas x{ws}", "l2": "flushed (256 MB write) between timed steps",
@@ -460,7 +462,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / len(times), 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64 limbs (exact integer)",
         "data": "synthetic uniform random bits (splitmix64 seed 2)",
-        "config": {"workload": "plain single block n=2.6e8 bits, r=0.1n=2.6e7 (seed 2)", "sample": sample},
+        "config": {"workload": f"plain single block n={n:.3g} bits, r={args.ratio:g}n={r} (seed 2)", "sample": sample},
         "cpu_baseline": {"value": round(value, 3), "unit": "Mbps", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 3), "unit": "Mbps", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
