@@ -160,6 +160,10 @@ int pa_trace_collect(pa_trace_entry *out, int max_entries, int *count);
 int pa_plan_estimate_bytes(uint64_t n_bits, uint64_t r_bits, const pa_params *params, uint64_t *bytes);
 int pa_field_constants(uint32_t log_n, uint64_t *omega, uint64_t *theta);
 int pa_transform_len(uint64_t G, uint64_t K, uint32_t *log_n);
+/* Device check of the F_q arithmetic used inside the transforms: for i < n,
+ * out[3i], out[3i+1], out[3i+2] = (a[i] + b[i], a[i] - b[i], a[i] * b[i]) mod q,
+ * canonical; a, b, out are device arrays (any 64-bit inputs).  Asynchronous. */
+int pa_selftest_field(const uint64_t *a, const uint64_t *b, uint64_t *out, uint64_t n, void *stream);
 
 /* Human-readable name of a return code (static string). */
 const char *pa_status_string(int code);

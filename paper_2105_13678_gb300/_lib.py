@@ -83,6 +83,7 @@ SIGNATURES = {
     "pa_plan_estimate_bytes": (ctypes.c_int, [_u64, _u64, ctypes.POINTER(pa_params), ctypes.POINTER(_u64)]),
     "pa_field_constants": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "pa_transform_len": (ctypes.c_int, [_u64, _u64, ctypes.POINTER(ctypes.c_uint32)]),
+    "pa_selftest_field": (ctypes.c_int, [_vp, _vp, _vp, _u64, _vp]),
 }
 
 _lib = None

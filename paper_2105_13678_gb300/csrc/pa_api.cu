@@ -168,7 +168,7 @@ static int build_xform(pa_plan_t *pl, Xform &X, uint64_t G, uint64_t K) {
     X.C = 1u << X.logC;
     X.hb = (l + 1) / 2;
     u32 tc = 8;
-    while (tc > 1 && (uint64_t)X.R * tc > 8192) tc >>= 1;
+    while (tc > 1 && (uint64_t)X.R * tc > 4096) tc >>= 1;
     while (tc > X.C) tc >>= 1;
     X.tc = tc;
     const u64 w = root_of_unity(l), wi = gl_inv(w);
@@ -232,7 +232,7 @@ int pa_plan(uint64_t n_bits, uint64_t r_bits, const pa_params *params, pa_plan_t
     pl->r = r_bits;
     pl->gamma = gamma;
     pl->k = (n_bits + gamma - 1) / gamma;
-    if (2 * pl->k > 65535) {  // operands index gridDim.y of the column pass
+    if (pl->k > 65535) {  // operand pairs index gridDim.y of the column pass
         delete pl;
         return PA_ERR_UNSUPPORTED;
     }
@@ -309,7 +309,7 @@ static int enqueue_mmh(pa_plan_t *pl, const u64 *key, const u64 *seed, u64 *y, b
     ops.k = pl->k;
     ops.mode = 0;
     const Xform &X = pl->mmh;
-    if ((e = launch_fwd_col(X, ops, (int)(2 * pl->k), pl->Y, stream))) return e;
+    if ((e = launch_fwd_col(X, ops, (int)pl->k, pl->Y, stream))) return e;
     if ((e = launch_row_mac(X, pl->Y, pl->S, stream))) return e;
     if ((e = launch_inv_col(X, pl->S, pl->Y, nullptr, 0, 0, stream))) return e;
     CarryDev cd;
@@ -342,7 +342,7 @@ static int enqueue_mh(pa_plan_t *pl, const u64 *seed, u64 *out, int *status, voi
     ops.k = pl->k;
     ops.mode = 1;
     const Xform &X = pl->mh;
-    if ((e = launch_fwd_col(X, ops, 2, pl->Y, stream))) return e;
+    if ((e = launch_fwd_col(X, ops, 1, pl->Y, stream))) return e;
     if ((e = launch_row_mac(X, pl->Y, pl->S, stream))) return e;
     if ((e = launch_inv_col(X, pl->S, pl->Y, seed, (pl->k + 1) * (u64)pl->gamma, pl->gamma, stream))) return e;
     CarryDev cd;
@@ -439,6 +439,12 @@ int pa_field_constants(uint32_t log_n, uint64_t *omega, uint64_t *theta) {
     *omega = root_of_unity(log_n);
     *theta = root_of_two(log_n);
     return PA_OK;
+}
+
+// Device F_q arithmetic check: out[3i..3i+2] = a+b, a-b, a*b (canonical).
+int pa_selftest_field(const uint64_t *a, const uint64_t *b, uint64_t *out, uint64_t n, void *stream) {
+    if (!a || !b || !out) return PA_ERR_INVALID;
+    return launch_selftest_field((const u64 *)a, (const u64 *)b, (u64 *)out, n, stream) ? PA_ERR_CUDA : PA_OK;
 }
 
 // Digit split chosen for a modulus of G bits and K operand pairs.

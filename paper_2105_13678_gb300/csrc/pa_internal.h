@@ -130,7 +130,7 @@ void trace_end(void *token, void *stream);
 
 // Kernel launch wrappers (pa_kernels.cu).  All return a cudaError_t as int.
 int prepare_kernels();
-int launch_fwd_col(const Xform &X, const Operands &S, int num_operands, u64 *Y, void *stream);
+int launch_fwd_col(const Xform &X, const Operands &S, int num_pairs, u64 *Y, void *stream);
 int launch_row_mac(const Xform &X, const u64 *Y, u64 *S, void *stream);
 int launch_inv_col(const Xform &X, const u64 *S, u64 *Z, const u64 *add_src, u64 add_base,
                    u64 add_len, void *stream);
@@ -139,5 +139,6 @@ int launch_carry(const Xform &X, const CarryDev &cd, u64 *z, u64 *out_bits, u64 
 int launch_extract(const u64 *t, u64 gamma, u64 r, const int *reload, u64 k, u64 *out,
                    int *status, void *stream);
 int launch_canonical_zero(const int *flag, u64 *y, u64 words, void *stream);
+int launch_selftest_field(const u64 *a, const u64 *b, u64 *out, u64 n, void *stream);
 
 }  // namespace pa

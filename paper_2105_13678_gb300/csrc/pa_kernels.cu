@@ -12,6 +12,7 @@
 //   k_extract   z = bits [gamma - r, gamma) of b*y + c              (Eq. 4)
 #include <cuda_runtime.h>
 
+#include "gl_device.cuh"
 #include "pa_internal.h"
 
 namespace pa {
@@ -23,7 +24,7 @@ __device__ __forceinline__ u32 pidx(u32 i) { return i + (i >> 4); }  // 1 pad wo
 __device__ __forceinline__ u32 bitrev(u32 x, u32 bits) { return bits ? (__brev(x) >> (32 - bits)) : 0u; }
 
 __device__ __forceinline__ u64 tbl2(const u64 *__restrict__ lo, const u64 *__restrict__ hi, u64 e, u32 hb) {
-    return gl_mul(__ldg(lo + (e & ((1ULL << hb) - 1))), __ldg(hi + (e >> hb)));
+    return gd_mul(__ldg(lo + (e & ((1ULL << hb) - 1))), __ldg(hi + (e >> hb)));
 }
 
 __device__ __forceinline__ u64 digit_start(u64 G, u64 j, u64 N, u32 logN) { return (G * j + N - 1) >> logN; }
@@ -40,8 +41,9 @@ __device__ __forceinline__ u64 read_bits(const u64 *__restrict__ src, u64 pos, u
 // Radix-2 decimation-in-frequency stages s0 .. s0+NS-1 of a length-L
 // transform on the 2^NS elements base + m*stride held in v (lo = base mod
 // stride).  Stage s pairs (i, i + L/2^(s+1)) with twiddle
-// omega_L^((i mod L/2^(s+1)) * 2^s) (Gentleman-Sande).
-template <int NS>
+// omega_L^((i mod L/2^(s+1)) * 2^s) (Gentleman-Sande).  When the group holds
+// the final stage (LAST), that stage's twiddles are all 1 and are skipped.
+template <int NS, bool LAST>
 __device__ __forceinline__ void dif_regs(u64 (&v)[8], u32 s0, u32 lo, u32 stride, const u64 *__restrict__ tw) {
 #pragma unroll
     for (int sg = 0; sg < NS; sg++) {
@@ -49,17 +51,21 @@ __device__ __forceinline__ void dif_regs(u64 (&v)[8], u32 s0, u32 lo, u32 stride
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
             if (m & half) continue;
-            const u32 e = (lo + (u32)(m & (half - 1)) * stride) << (s0 + sg);
             const u64 a = v[m], b = v[m + half];
-            v[m] = gl_add(a, b);
-            v[m + half] = gl_mul(gl_sub(a, b), __ldg(tw + e));
+            v[m] = gd_add(a, b);
+            if (LAST && sg == NS - 1) {
+                v[m + half] = gd_sub(a, b);
+            } else {
+                const u32 e = (lo + (u32)(m & (half - 1)) * stride) << (s0 + sg);
+                v[m + half] = gd_mul(gd_sub(a, b), __ldg(tw + e));
+            }
         }
     }
 }
 
 // Inverse of dif_regs up to a factor 2 per stage (decimation in time,
 // stages in reverse order, inverse twiddles).
-template <int NS>
+template <int NS, bool LAST>
 __device__ __forceinline__ void dit_regs(u64 (&v)[8], u32 s0, u32 lo, u32 stride, const u64 *__restrict__ itw) {
 #pragma unroll
     for (int sg = NS - 1; sg >= 0; sg--) {
@@ -67,10 +73,14 @@ __device__ __forceinline__ void dit_regs(u64 (&v)[8], u32 s0, u32 lo, u32 stride
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
             if (m & half) continue;
-            const u32 e = (lo + (u32)(m & (half - 1)) * stride) << (s0 + sg);
-            const u64 a = v[m], b = gl_mul(v[m + half], __ldg(itw + e));
-            v[m] = gl_add(a, b);
-            v[m + half] = gl_sub(a, b);
+            const u64 a = v[m];
+            u64 b = v[m + half];
+            if (!(LAST && sg == NS - 1)) {
+                const u32 e = (lo + (u32)(m & (half - 1)) * stride) << (s0 + sg);
+                b = gd_mul(b, __ldg(itw + e));
+            }
+            v[m] = gd_add(a, b);
+            v[m + half] = gd_sub(a, b);
         }
     }
 }
@@ -83,63 +93,76 @@ struct OpDesc {
     int force_odd, check_ones, zero;
 };
 
-// Alg. 1 lines 1-2 and the seed layout: MMH operand o < k is key slice x_{o+1},
-// o >= k is seed slice a_{o-k+1}; MH operand 0 is y, operand 1 is b (odd).
-__device__ __forceinline__ OpDesc op_desc(const Operands &S, u32 o) {
-    OpDesc d;
-    d.force_odd = 0;
-    d.check_ones = 0;
-    d.zero = 0;
+// Alg. 1 lines 1-2 and the seed layout.  Pair i of the MMH stage is
+// (x_{i+1}, a_{i+1}): key slice i and seed slice i.  The MH stage has the
+// single pair (y, b) with b forced odd.
+__device__ __forceinline__ void pair_desc(const Operands &S, u32 i, OpDesc &dx, OpDesc &da) {
+    dx.force_odd = da.force_odd = 0;
+    dx.check_ones = da.check_ones = 0;
+    dx.zero = da.zero = 0;
     if (S.mode == 0) {
-        if (o < S.k) {
-            d.src = S.key;
-            d.base = (u64)o * S.gamma;
-            const u64 rem = S.n - d.base;
-            d.len = rem < S.gamma ? rem : S.gamma;
-            d.check_ones = 1;
-        } else {
-            d.src = S.seed;
-            d.base = (u64)(o - S.k) * S.gamma;
-            d.len = S.gamma;
-        }
+        dx.src = S.key;
+        dx.base = (u64)i * S.gamma;
+        const u64 rem = S.n - dx.base;
+        dx.len = rem < S.gamma ? rem : S.gamma;
+        dx.check_ones = 1;
+        da.src = S.seed;
+        da.base = (u64)i * S.gamma;
+        da.len = S.gamma;
     } else {
-        if (o == 0) {
-            d.src = S.y;
-            d.base = 0;
-            d.len = S.gamma;
-            d.zero = (*S.y_zero != 0);
-        } else {
-            d.src = S.seed;
-            d.base = S.k * S.gamma;
-            d.len = S.gamma;
-            d.force_odd = 1;
-        }
+        dx.src = S.y;
+        dx.base = 0;
+        dx.len = S.gamma;
+        dx.zero = (*S.y_zero != 0);
+        da.src = S.seed;
+        da.base = S.k * S.gamma;
+        da.len = S.gamma;
+        da.force_odd = 1;
     }
-    return d;
 }
 
-// Weighted digit j of an operand: digit * theta^((-G j) mod N).
-__device__ __forceinline__ u64 weighted_digit(const Xform &X, const OpDesc &d, u64 j, bool &ones) {
-    const u64 slo = digit_start(X.G, j, X.N, X.logN);
-    const u64 shi = digit_start(X.G, j + 1, X.N, X.logN);
+__device__ __forceinline__ u64 op_digit(const OpDesc &d, u64 j, u64 slo, u64 shi, bool &ones) {
     const u64 hi = shi < d.len ? shi : d.len;
     u64 dig = 0;
     if (slo < hi) dig = read_bits(d.src, d.base + slo, (u32)(hi - slo));
-    const u32 width = (u32)(shi - slo);
-    ones = ones && (shi <= d.len) && (dig == ((1ULL << width) - 1));
+    ones = ones && (shi <= d.len) && (dig == ((1ULL << (u32)(shi - slo)) - 1));
     if (d.force_odd && j == 0) dig |= 1;
     if (d.zero) dig = 0;
-    if (dig == 0) return 0;
+    return dig;
+}
+
+// Weighted digits j of both operands of a pair: digit * theta^((-G j) mod N).
+__device__ __forceinline__ void weighted_pair(const Xform &X, const OpDesc &dx, const OpDesc &da, u64 j, u64 &wx,
+                                              u64 &wa, bool &ones) {
+    const u64 slo = digit_start(X.G, j, X.N, X.logN);
+    const u64 shi = digit_start(X.G, j + 1, X.N, X.logN);
+    bool dummy = true;
+    const u64 gx = op_digit(dx, j, slo, shi, ones);
+    const u64 ga = op_digit(da, j, slo, shi, dummy);
     const u64 e = (0ULL - X.G * j) & (X.N - 1);
-    return gl_mul(dig, tbl2(X.wt_lo, X.wt_hi, e, X.hb));
+    const u64 w = tbl2(X.wt_lo, X.wt_hi, e, X.hb);
+    wx = gx ? gd_mul(gx, w) : 0;
+    wa = ga ? gd_mul(ga, w) : 0;
 }
 
 // ------------------------------------------------------ forward columns --
 
-template <int NS>
-__device__ __forceinline__ void fwd_col_round(const Xform &X, const OpDesc &d, u64 *__restrict__ sm,
-                                              u64 *__restrict__ Yo, u32 c0, u32 s0, bool first, bool last,
-                                              bool &ones) {
+#define PA_DISPATCH_NS(ns, call_tmpl)  \
+    do {                               \
+        if ((ns) == 3) {               \
+            call_tmpl(3);              \
+        } else if ((ns) == 2) {        \
+            call_tmpl(2);              \
+        } else {                       \
+            call_tmpl(1);              \
+        }                              \
+    } while (0)
+
+
+template <int NS, bool LAST>
+__device__ __forceinline__ void fwd_col_round(const Xform &X, const OpDesc &dx, const OpDesc &da,
+                                              u64 *__restrict__ smx, u64 *__restrict__ sma, u64 *__restrict__ Yx,
+                                              u64 *__restrict__ Ya, u32 c0, u32 s0, bool first, bool &ones) {
     const u32 l = X.logR, tc = X.tc;
     const u32 sh = l - s0 - NS, stride = 1u << sh;
     const u32 ntask = (X.R >> NS) * tc;
@@ -147,55 +170,75 @@ __device__ __forceinline__ void fwd_col_round(const Xform &X, const OpDesc &d, u
     for (u32 task = threadIdx.x; task < ntask; task += blockDim.x) {
         const u32 c = task & (tc - 1), g = task >> logtc;
         const u32 lo = g & (stride - 1), base = ((g >> sh) << (l - s0)) + lo;
-        u64 v[8];
+        u64 vx[8], va[8];
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
             const u32 r = base + m * stride;
-            v[m] = first ? weighted_digit(X, d, (u64)r * X.C + c0 + c, ones) : sm[pidx(r * tc + c)];
+            if (first) {
+                weighted_pair(X, dx, da, (u64)r * X.C + c0 + c, vx[m], va[m], ones);
+            } else {
+                vx[m] = smx[pidx(r * tc + c)];
+                va[m] = sma[pidx(r * tc + c)];
+            }
         }
-        dif_regs<NS>(v, s0, lo, stride, X.twR);
+        dif_regs<NS, LAST>(vx, s0, lo, stride, X.twR);
+        dif_regs<NS, LAST>(va, s0, lo, stride, X.twR);
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
             const u32 r = base + m * stride;
-            if (last) {
+            if (LAST) {
                 // position r holds column frequency bitrev(r): twiddle omega_N^(c * k_r)
                 const u64 e = (u64)(c0 + c) * bitrev(r, l);
-                Yo[(u64)r * X.C + c0 + c] = gl_mul(v[m], tbl2(X.ipw_lo, X.ipw_hi, e, X.hb));
+                const u64 t = tbl2(X.ipw_lo, X.ipw_hi, e, X.hb);
+                Yx[(u64)r * X.C + c0 + c] = gd_mul(vx[m], t);
+                Ya[(u64)r * X.C + c0 + c] = gd_mul(va[m], t);
             } else {
-                sm[pidx(r * tc + c)] = v[m];
+                smx[pidx(r * tc + c)] = vx[m];
+                sma[pidx(r * tc + c)] = va[m];
             }
         }
     }
 }
 
+// One CTA: a tile of tc columns of both operands of pair blockIdx.y.
 __global__ void __launch_bounds__(PA_COL_T) k_fwd_col(Xform X, Operands S, u64 *__restrict__ Y) {
     extern __shared__ u64 sm[];
-    const u32 tc = X.tc, c0 = blockIdx.x * tc, o = blockIdx.y;
-    const OpDesc d = op_desc(S, o);
-    u64 *Yo = Y + (u64)o * X.N;
+    const u32 tc = X.tc, c0 = blockIdx.x * tc, i = blockIdx.y;
+    OpDesc dx, da;
+    pair_desc(S, i, dx, da);
+    u64 *Yx = Y + (u64)i * X.N, *Ya = Y + (u64)(X.K + i) * X.N;
+    u64 *smx = sm, *sma = sm + pidx(X.R * tc);
     bool ones = true;
     const u32 l = X.logR;
     if (l == 0) {
-        for (u32 c = threadIdx.x; c < tc; c += blockDim.x) Yo[c0 + c] = weighted_digit(X, d, c0 + c, ones);
+        for (u32 c = threadIdx.x; c < tc; c += blockDim.x) {
+            u64 wx, wa;
+            weighted_pair(X, dx, da, c0 + c, wx, wa, ones);
+            Yx[c0 + c] = wx;
+            Ya[c0 + c] = wa;
+        }
     } else {
         const u32 nr = (l + 2) / 3;
         for (u32 rd = 0; rd < nr; rd++) {
             const u32 s0 = 3 * rd, ns = min(3u, l - s0);
             const bool first = rd == 0, last = rd == nr - 1;
-            if (ns == 3)
-                fwd_col_round<3>(X, d, sm, Yo, c0, s0, first, last, ones);
-            else if (ns == 2)
-                fwd_col_round<2>(X, d, sm, Yo, c0, s0, first, last, ones);
-            else
-                fwd_col_round<1>(X, d, sm, Yo, c0, s0, first, last, ones);
+#define PA_FWD_COL(NSV)                                                                 \
+    do {                                                                                \
+        if (last)                                                                       \
+            fwd_col_round<NSV, true>(X, dx, da, smx, sma, Yx, Ya, c0, s0, first, ones);  \
+        else                                                                            \
+            fwd_col_round<NSV, false>(X, dx, da, smx, sma, Yx, Ya, c0, s0, first, ones); \
+    } while (0)
+            PA_DISPATCH_NS(ns, PA_FWD_COL);
+#undef PA_FWD_COL
             __syncthreads();
         }
     }
-    if (d.check_ones) {
-        // Alg. 1 lines 3-4: slice o is all ones iff every CTA of the slice saw only ones.
+    if (dx.check_ones) {
+        // Alg. 1 lines 3-4: slice i is all ones iff every CTA of the slice saw only ones.
         const int all = __syncthreads_and(ones ? 1 : 0);
         if (threadIdx.x == 0 && all) {
-            int *cnt = S.reload + 4 + o;
+            int *cnt = S.reload + 4 + i;
             if (atomicAdd(cnt, 1) + 1 == (int)gridDim.x) atomicExch(S.reload, 1);
         }
     }
@@ -203,10 +246,10 @@ __global__ void __launch_bounds__(PA_COL_T) k_fwd_col(Xform X, Operands S, u64 *
 
 // --------------------------------------------------- rows + MAC (Eq. 2) --
 
-template <int NS, int ACC>
+template <int NS, int ACC, bool LAST>
 __device__ __forceinline__ void row_fwd_round(const Xform &X, const u64 *__restrict__ xrow,
                                               const u64 *__restrict__ arow, u64 *__restrict__ smx,
-                                              u64 *__restrict__ sma, u32 s0, bool first, bool last, u64 (&acc)[ACC]) {
+                                              u64 *__restrict__ sma, u32 s0, bool first, u64 (&acc)[ACC]) {
     const u32 l = X.logC, sh = l - s0 - NS, stride = 1u << sh, ngroups = X.C >> NS;
 #pragma unroll
     for (int t = 0; t < (ACC >> NS); t++) {
@@ -220,13 +263,13 @@ __device__ __forceinline__ void row_fwd_round(const Xform &X, const u64 *__restr
                 vx[m] = first ? __ldg(xrow + idx) : smx[pidx(idx)];
                 va[m] = first ? __ldg(arow + idx) : sma[pidx(idx)];
             }
-            dif_regs<NS>(vx, s0, lo, stride, X.twC);
-            dif_regs<NS>(va, s0, lo, stride, X.twC);
+            dif_regs<NS, LAST>(vx, s0, lo, stride, X.twC);
+            dif_regs<NS, LAST>(va, s0, lo, stride, X.twC);
 #pragma unroll
             for (int m = 0; m < (1 << NS); m++) {
                 const u32 idx = base + m * stride;
-                if (last) {
-                    acc[t * (1 << NS) + m] = gl_add(acc[t * (1 << NS) + m], gl_mul(vx[m], va[m]));
+                if (LAST) {
+                    acc[t * (1 << NS) + m] = gd_add(acc[t * (1 << NS) + m], gd_mul(vx[m], va[m]));
                 } else {
                     smx[pidx(idx)] = vx[m];
                     sma[pidx(idx)] = va[m];
@@ -236,9 +279,9 @@ __device__ __forceinline__ void row_fwd_round(const Xform &X, const u64 *__restr
     }
 }
 
-template <int NS, int ACC>
+template <int NS, int ACC, bool LAST>
 __device__ __forceinline__ void row_inv_round(const Xform &X, u64 *__restrict__ sm, u64 *__restrict__ Srow, u32 row,
-                                              u32 s0, bool from_acc, bool to_global, const u64 (&acc)[ACC]) {
+                                              u32 s0, bool to_global, const u64 (&acc)[ACC]) {
     const u32 l = X.logC, sh = l - s0 - NS, stride = 1u << sh, ngroups = X.C >> NS;
     const u32 kr = bitrev(row, X.logR);
 #pragma unroll
@@ -249,14 +292,14 @@ __device__ __forceinline__ void row_inv_round(const Xform &X, u64 *__restrict__ 
             u64 v[8];
 #pragma unroll
             for (int m = 0; m < (1 << NS); m++)
-                v[m] = from_acc ? acc[t * (1 << NS) + m] : sm[pidx(base + m * stride)];
-            dit_regs<NS>(v, s0, lo, stride, X.itwC);
+                v[m] = LAST ? acc[t * (1 << NS) + m] : sm[pidx(base + m * stride)];
+            dit_regs<NS, LAST>(v, s0, lo, stride, X.itwC);
 #pragma unroll
             for (int m = 0; m < (1 << NS); m++) {
                 const u32 idx = base + m * stride;
                 if (to_global) {
                     const u64 e = (u64)idx * kr;  // omega_N^(-c * k_r)
-                    Srow[idx] = gl_mul(v[m], tbl2(X.iipw_lo, X.iipw_hi, e, X.hb));
+                    Srow[idx] = gd_mul(v[m], tbl2(X.iipw_lo, X.iipw_hi, e, X.hb));
                 } else {
                     sm[pidx(idx)] = v[m];
                 }
@@ -265,16 +308,6 @@ __device__ __forceinline__ void row_inv_round(const Xform &X, u64 *__restrict__ 
     }
 }
 
-#define PA_DISPATCH_NS(ns, call_tmpl)  \
-    do {                               \
-        if ((ns) == 3) {               \
-            call_tmpl(3);              \
-        } else if ((ns) == 2) {        \
-            call_tmpl(2);              \
-        } else {                       \
-            call_tmpl(1);              \
-        }                              \
-    } while (0)
 
 // One CTA per row; blockDim = C / ACC threads, each owning ACC accumulators.
 template <int ACC>
@@ -287,7 +320,7 @@ __global__ void __launch_bounds__(512) k_row_mac(Xform X, const u64 *__restrict_
         if (threadIdx.x == 0) {
             u64 s = 0;
             for (u32 i = 0; i < X.K; i++)
-                s = gl_add(s, gl_mul(Y[(u64)i * N + row], Y[(u64)(X.K + i) * N + row]));
+                s = gd_add(s, gd_mul(Y[(u64)i * N + row], Y[(u64)(X.K + i) * N + row]));
             S[row] = s;
         }
         return;
@@ -302,7 +335,13 @@ __global__ void __launch_bounds__(512) k_row_mac(Xform X, const u64 *__restrict_
         for (u32 rd = 0; rd < nr; rd++) {
             const u32 s0 = 3 * rd, ns = min(3u, l - s0);
             const bool first = rd == 0, last = rd == nr - 1;
-#define PA_ROW_FWD(NSV) row_fwd_round<NSV, ACC>(X, xrow, arow, smx, sma, s0, first, last, acc)
+#define PA_ROW_FWD(NSV)                                                           \
+    do {                                                                          \
+        if (last)                                                                 \
+            row_fwd_round<NSV, ACC, true>(X, xrow, arow, smx, sma, s0, first, acc);  \
+        else                                                                      \
+            row_fwd_round<NSV, ACC, false>(X, xrow, arow, smx, sma, s0, first, acc); \
+    } while (0)
             PA_DISPATCH_NS(ns, PA_ROW_FWD);
 #undef PA_ROW_FWD
             __syncthreads();
@@ -312,7 +351,13 @@ __global__ void __launch_bounds__(512) k_row_mac(Xform X, const u64 *__restrict_
     for (int rd = (int)nr - 1; rd >= 0; rd--) {
         const u32 s0 = 3 * rd, ns = min(3u, l - s0);
         const bool from_acc = rd == (int)nr - 1, to_global = rd == 0;
-#define PA_ROW_INV(NSV) row_inv_round<NSV, ACC>(X, smx, Srow, row, s0, from_acc, to_global, acc)
+#define PA_ROW_INV(NSV)                                                        \
+    do {                                                                       \
+        if (from_acc)                                                          \
+            row_inv_round<NSV, ACC, true>(X, smx, Srow, row, s0, to_global, acc);  \
+        else                                                                   \
+            row_inv_round<NSV, ACC, false>(X, smx, Srow, row, s0, to_global, acc); \
+    } while (0)
         PA_DISPATCH_NS(ns, PA_ROW_INV);
 #undef PA_ROW_INV
         __syncthreads();
@@ -321,7 +366,7 @@ __global__ void __launch_bounds__(512) k_row_mac(Xform X, const u64 *__restrict_
 
 // ------------------------------------------------------ inverse columns --
 
-template <int NS>
+template <int NS, bool LASTSTAGE>
 __device__ __forceinline__ void inv_col_round(const Xform &X, const u64 *__restrict__ Sg, u64 *__restrict__ sm,
                                               u64 *__restrict__ Z, u32 c0, u32 s0, bool first, bool last,
                                               const u64 *__restrict__ add_src, u64 add_base, u64 add_len) {
@@ -338,14 +383,14 @@ __device__ __forceinline__ void inv_col_round(const Xform &X, const u64 *__restr
             const u32 r = base + m * stride;
             v[m] = first ? __ldg(Sg + (u64)r * X.C + c0 + c) : sm[pidx(r * tc + c)];
         }
-        dit_regs<NS>(v, s0, lo, stride, X.itwR);
+        dit_regs<NS, LASTSTAGE>(v, s0, lo, stride, X.itwR);
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
             const u32 r = base + m * stride;
             if (last) {
                 const u64 j = (u64)r * X.C + c0 + c;
                 const u64 e = (0ULL - X.G * j) & (X.N - 1);
-                u64 z = gl_mul(v[m], tbl2(X.iwt_lo, X.iwt_hi, e, X.hb));
+                u64 z = gd_canon(gd_mul(v[m], tbl2(X.iwt_lo, X.iwt_hi, e, X.hb)));
                 if (add_src) {
                     const u64 slo = digit_start(X.G, j, X.N, X.logN);
                     u64 shi = digit_start(X.G, j + 1, X.N, X.logN);
@@ -369,7 +414,7 @@ __global__ void __launch_bounds__(PA_COL_T) k_inv_col(Xform X, const u64 *__rest
         for (u32 c = threadIdx.x; c < tc; c += blockDim.x) {
             const u64 j = c0 + c;
             const u64 e = (0ULL - X.G * j) & (X.N - 1);
-            u64 z = gl_mul(Sg[j], tbl2(X.iwt_lo, X.iwt_hi, e, X.hb));
+            u64 z = gd_canon(gd_mul(Sg[j], tbl2(X.iwt_lo, X.iwt_hi, e, X.hb)));
             if (add_src) {
                 const u64 slo = digit_start(X.G, j, X.N, X.logN);
                 u64 shi = digit_start(X.G, j + 1, X.N, X.logN);
@@ -384,7 +429,13 @@ __global__ void __launch_bounds__(PA_COL_T) k_inv_col(Xform X, const u64 *__rest
     for (int rd = (int)nr - 1; rd >= 0; rd--) {
         const u32 s0 = 3 * rd, ns = min(3u, l - s0);
         const bool first = rd == (int)nr - 1, last = rd == 0;
-#define PA_INV_COL(NSV) inv_col_round<NSV>(X, Sg, sm, Z, c0, s0, first, last, add_src, add_base, add_len)
+#define PA_INV_COL(NSV)                                                                              \
+    do {                                                                                             \
+        if (first)                                                                                   \
+            inv_col_round<NSV, true>(X, Sg, sm, Z, c0, s0, first, last, add_src, add_base, add_len);  \
+        else                                                                                         \
+            inv_col_round<NSV, false>(X, Sg, sm, Z, c0, s0, first, last, add_src, add_base, add_len); \
+    } while (0)
         PA_DISPATCH_NS(ns, PA_INV_COL);
 #undef PA_INV_COL
         __syncthreads();
@@ -619,7 +670,24 @@ __global__ void k_canonical_zero(const int *__restrict__ flag, u64 *__restrict__
     for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (u64)gridDim.x * blockDim.x) y[i] = 0;
 }
 
+// Element-wise F_q arithmetic of the transforms, for host-side checking:
+// out[3i] = a+b, out[3i+1] = a-b, out[3i+2] = a*b (canonical); any 64-bit inputs.
+__global__ void k_selftest_field(const u64 *__restrict__ a, const u64 *__restrict__ b, u64 *__restrict__ out, u64 n) {
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
+        out[3 * i] = gd_canon(gd_add(a[i], b[i]));
+        out[3 * i + 1] = gd_canon(gd_sub(a[i], b[i]));
+        out[3 * i + 2] = gd_canon(gd_mul(a[i], b[i]));
+    }
+}
+
+int launch_selftest_field(const u64 *a, const u64 *b, u64 *out, u64 n, void *stream) {
+    k_selftest_field<<<64, 256, 0, (cudaStream_t)stream>>>(a, b, out, n);
+    return (int)cudaGetLastError();
+}
+
 // -------------------------------------------------------------- launchers --
+
+static inline u32 pidx_host(u32 i) { return i + (i >> 4); }
 //
 // Every launch goes through TRACED(): when tracing is on (pa_trace_enable) and
 // the stream is not being captured, a CUDA event pair is recorded on the
@@ -632,8 +700,8 @@ __global__ void k_canonical_zero(const int *__restrict__ flag, u64 *__restrict__
         trace_end(tr_, (stream));                                \
     } while (0)
 
-static size_t col_smem(const Xform &X) { return (size_t)((X.R * X.tc) + ((X.R * X.tc) >> 4) + 1) * sizeof(u64); }
-static size_t row_smem(const Xform &X) { return (size_t)2 * (X.C + (X.C >> 4) + 1) * sizeof(u64); }
+static size_t col_smem(const Xform &X) { return (size_t)pidx_host(X.R * X.tc) * sizeof(u64); }
+static size_t row_smem(const Xform &X) { return (size_t)2 * pidx_host(X.C) * sizeof(u64); }
 
 int prepare_kernels() {
     static bool done = false;
@@ -647,10 +715,11 @@ int prepare_kernels() {
     return 0;
 }
 
-int launch_fwd_col(const Xform &X, const Operands &S, int num_operands, u64 *Y, void *stream) {
+int launch_fwd_col(const Xform &X, const Operands &S, int num_pairs, u64 *Y, void *stream) {
     if (int e = prepare_kernels()) return e;
-    dim3 grid(X.C / X.tc, num_operands);
-    TRACED("fwd_col", X.stage, stream, (k_fwd_col<<<grid, PA_COL_T, col_smem(X), (cudaStream_t)stream>>>(X, S, Y)));
+    dim3 grid(X.C / X.tc, num_pairs);
+    const size_t smem = 2 * col_smem(X);
+    TRACED("fwd_col", X.stage, stream, (k_fwd_col<<<grid, PA_COL_T, smem, (cudaStream_t)stream>>>(X, S, Y)));
     return (int)cudaGetLastError();
 }
 
