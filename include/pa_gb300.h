@@ -94,6 +94,24 @@ int pa_hash_host(pa_plan_t *plan, const uint64_t *key, const uint64_t *seed, uin
 int pa_debug_mmh(pa_plan_t *plan, const uint64_t *key, const uint64_t *seed, uint64_t *y,
                  int *status, void *stream);
 
+/* Algorithm 1 without any device allocation, for callers that cannot call
+ * cudaMalloc (device memory owned by another allocator or pool, code paths
+ * where an allocation and its possible device synchronisation are not
+ * allowed, or a device footprint fixed at start-up).  Same result as
+ * pa_plan(n, r, params) followed by pa_hash.  All intermediate buffers and
+ * tables live in one library-owned static device array of
+ * PA_NOALLOC_SCRATCH_BYTES, resident on every GPU that loads the library until
+ * the process exits.  Blocks whose workspace does not fit (about n <= 1e7 key
+ * bits at r = 0.1 n) return PA_ERR_UNSUPPORTED.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) and should be
+ * made before any stream capture on that device.  Every call shares the array:
+ * calls whose work overlaps on the GPU race, so order them (one stream, or
+ * events).  key, seed, out and status are device pointers as for pa_hash.
+ * Asynchronous.  This entry point has no counterpart in the paper. */
+#define PA_NOALLOC_SCRATCH_BYTES (16ULL << 20)
+int pa_hash_noalloc(uint64_t n_bits, uint64_t r_bits, const pa_params *params, const uint64_t *key,
+                    const uint64_t *seed, uint64_t *out, int *status, void *stream);
+
 /* Batched Algorithm 1 over `count` independent blocks, each with its own plan
  * (plans must be distinct objects).  keys/seeds/outs are HOST arrays of device
  * pointers; statuses is a device int[count] (may be NULL).  The first call for

@@ -67,6 +67,7 @@ SIGNATURES = {
     "pa_hash": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "pa_hash_host": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "pa_debug_mmh": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "pa_hash_noalloc": (ctypes.c_int, [_u64, _u64, ctypes.POINTER(pa_params), _vp, _vp, _vp, _vp, _vp]),
     "pa_hash_batch": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                      ctypes.POINTER(_vp), _vp, ctypes.c_int, _vp]),
     "pa_batch_cache_clear": (ctypes.c_int, []),

@@ -421,6 +421,21 @@ const char *pa_status_string(int code) {
 
 const char *pa_version(void) { return "pa_gb300 0.1 (sm_103a)"; }
 
+}  // extern "C"
+
+// Step-0 parameters and transform lengths for (n, r), host arithmetic only.
+int pa::choose_params(uint64_t n_bits, uint64_t r_bits, const pa_params *params, uint32_t *gamma, uint64_t *k,
+                      uint32_t *log_mmh, uint32_t *log_mh) {
+    if (n_bits == 0 || r_bits == 0) return PA_ERR_INVALID;
+    int rc = choose_gamma(r_bits, params, gamma);
+    if (rc) return rc;
+    *k = (n_bits + *gamma - 1) / *gamma;
+    if ((rc = choose_len(*gamma, *k, log_mmh))) return rc;
+    return choose_len(2ULL * *gamma, 1, log_mh);
+}
+
+extern "C" {
+
 // Workspace bytes pa_plan would allocate for (n, r), without allocating.
 int pa_plan_estimate_bytes(uint64_t n_bits, uint64_t r_bits, const pa_params *params, uint64_t *bytes) {
     if (!bytes || n_bits == 0 || r_bits == 0) return PA_ERR_INVALID;

@@ -15,6 +15,8 @@
 #pragma once
 #include <stdint.h>
 
+struct pa_params;
+
 #if defined(__CUDACC__)
 #define PA_HD __host__ __device__ __forceinline__
 #else
@@ -123,6 +125,10 @@ constexpr u32 PA_CARRY_T = 256;    // threads per CTA in the carry kernels
 constexpr u32 PA_COL_T = 256;      // threads per CTA in the column passes
 constexpr u32 PA_MAX_LOGN = 24;    // largest transform the kernels implement
 constexpr u32 PA_MAX_LOGR = 11;    // column length cap (smem tile R x tc)
+
+// Step-0 parameters (pa_api.cu): gamma, k and log2 of both transform lengths.
+int choose_params(uint64_t n_bits, uint64_t r_bits, const struct pa_params *params, uint32_t *gamma, uint64_t *k,
+                  uint32_t *log_mmh, uint32_t *log_mh);
 
 // Tracing (pa_trace.cu): event pair around a launch when enabled.
 void *trace_begin(const char *name, u32 stage, void *stream);
