@@ -24,7 +24,7 @@
  *     plan must be ordered (same stream, or event-ordered).
  *
  * Return codes: PA_OK (0); PA_RELOAD (1): some key slice x_i equals
- * 2^gamma - 1, Alg. 1 lines 3-4 -- the output is zero-filled and the caller
+ * 2^gamma - 1 (Algorithm 1 reload rule) -- the output is zero-filled and the caller
  * must draw a new key; negative values are errors.
  */
 #ifndef PA_GB300_H

@@ -15,18 +15,18 @@
  *       prime exponent, n = k * gamma.  Reading used here: gamma is the
  *       smallest known Mersenne exponent >= r + margin, k = ceil(n / gamma),
  *       the last segment is zero-padded at its high end.
- *   Alg. 1 lines 1-2: x = <x_1..x_k>, a = <a_1..a_k>, each a gamma-bit slice.
- *   Alg. 1 lines 3-4: if some x_i = 2^gamma - 1 the key must be reloaded;
+ *   Algorithm 1, splitting: x = <x_1..x_k>, a = <a_1..a_k>, gamma-bit slices.
+ *   Algorithm 1, reload rule: if some x_i = 2^gamma - 1 the key is reloaded;
  *       the oracle returns ORA_RELOAD and a zero output.
- *   Eq. 2 / Alg. 1 lines 6-9 (MMH): y = sum_i a_i * x_i mod p, the products
+ *   Eq. 2 / Algorithm 1 (MMH): y = sum_i a_i * x_i mod p, the products
  *       taken as exact integers, one reduction mod p at the end.  The
  *       reduction uses the Mersenne identity of Sec. 3.1
  *       (x mod M_gamma == floor(x / 2^gamma) + x mod 2^gamma, applied until
  *       the value is below 2^gamma, then 2^gamma - 1 -> 0).
- *   Eq. 4 / Alg. 1 line 10 (MH): z = ((b * y + c) mod 2^alpha) / 2^(alpha-beta)
+ *   Eq. 4 / Algorithm 1 (MH): z = ((b * y + c) mod 2^alpha) / 2^(alpha-beta)
  *       with alpha = gamma, beta = r, b forced odd (gcd(b, 2) = 1).
  *
- * Seed layout (reading of Alg. 1's random numbers): (k + 2) * gamma bits;
+ * Seed layout (reading of Algorithm 1's random numbers): (k + 2) * gamma bits;
  * a_i = bits [(i-1)gamma, i*gamma) reduced mod p, b = bits [k*gamma,
  * (k+1)gamma) with bit 0 set, c = bits [(k+1)gamma, (k+2)gamma).
  * Bit order everywhere: bit t of a string lives in word t/64 at position t%64.
@@ -73,7 +73,7 @@ int ora_plan(uint64_t n, uint64_t r, uint32_t margin, uint32_t gamma_override,
         if (g == 0 || (uint64_t)g <= r) return ORA_ERR_INVALID;
     } else {
         uint64_t need = r + (uint64_t)margin;
-        if (need <= r) need = r + 1; /* gamma > beta strictly (Alg. 1 output) */
+        if (need <= r) need = r + 1; /* gamma > beta strictly (Algorithm 1 output) */
         for (size_t i = 0; i < ORA_N_MERSENNE; i++)
             if ((uint64_t)ORA_MERSENNE[i] >= need) { g = ORA_MERSENNE[i]; break; }
         if (g == 0) return ORA_ERR_INVALID;
@@ -259,9 +259,9 @@ static int bn_mod_mersenne(uint64_t *s, size_t ns, uint32_t gamma) {
 
 /* ------------------------------------------------------------ MMH, MH -- */
 
-/* Alg. 1 lines 1-9: y = sum_{i=1..k} a_i x_i mod p.  key has n bits, seed
+/* Algorithm 1, MMH part (Eq. 2): y = sum_{i=1..k} a_i x_i mod p.  key has n bits, seed
  * has (k+2)*gamma bits.  Writes y (ceil(gamma/64) words).  Returns ORA_RELOAD
- * if some x_i == 2^gamma - 1 (Alg. 1 lines 3-4), y then unspecified. */
+ * if some x_i == 2^gamma - 1 (Algorithm 1 reload rule), y then unspecified. */
 static int mmh(const uint64_t *key, uint64_t n, const uint64_t *seed, uint32_t gamma, uint64_t k,
                uint64_t *y) {
     size_t gw = words_for(gamma);
@@ -293,7 +293,7 @@ out:
     return rc;
 }
 
-/* Eq. 4 / Alg. 1 line 10 with alpha = gamma, beta = r:
+/* Eq. 4 (Algorithm 1, MH part) with alpha = gamma, beta = r:
  * out = ((b * y + c) mod 2^gamma) >> (gamma - r), r bits, high bits zero. */
 static int mh(const uint64_t *y, const uint64_t *seed, uint32_t gamma, uint64_t k, uint64_t r,
               uint64_t *out) {

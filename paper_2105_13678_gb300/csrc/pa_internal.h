@@ -104,7 +104,7 @@ struct Operands {
     const u64 *seed;    // (k+2) gamma bits: a_1..a_k, b, c
     const u64 *y;       // Eq. 4 input (MMH value), gamma bits
     const int *y_zero;  // if *y_zero != 0, y is p itself and reads as 0
-    int *reload;        // per-slice all-ones flags (Alg. 1 lines 3-4)
+    int *reload;        // reload flag + per-slice all-ones counters (Algorithm 1)
     u64 n, gamma, k;
     int mode;           // 0: MMH (x_1..x_k then a_1..a_k), 1: MH (y, b)
 };

@@ -93,7 +93,7 @@ struct OpDesc {
     int force_odd, check_ones, zero;
 };
 
-// Alg. 1 lines 1-2 and the seed layout.  Pair i of the MMH stage is
+// Algorithm 1 slices and the seed layout.  Pair i of the MMH stage is
 // (x_{i+1}, a_{i+1}): key slice i and seed slice i.  The MH stage has the
 // single pair (y, b) with b forced odd.
 __device__ __forceinline__ void pair_desc(const Operands &S, u32 i, OpDesc &dx, OpDesc &da) {
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(PA_COL_T) k_fwd_col(Xform X, Operands S, u64 *
         }
     }
     if (dx.check_ones) {
-        // Alg. 1 lines 3-4: slice i is all ones iff every CTA of the slice saw only ones.
+        // Algorithm 1 reload rule: slice i is all ones iff every CTA of the slice saw only ones.
         const int all = __syncthreads_and(ones ? 1 : 0);
         if (threadIdx.x == 0 && all) {
             int *cnt = S.reload + 4 + i;

@@ -215,7 +215,7 @@ def test_mmh_all_ones_seed_slice_is_zero():
 
 
 def test_reload_on_all_ones_segment():
-    """Alg. 1 lines 3-4: a key segment equal to 2^gamma - 1 forces a reload."""
+    """Algorithm 1 reload rule: a key segment equal to 2^gamma - 1 forces a reload."""
     gamma, k, r = 61, 3, 20
     p = (1 << gamma) - 1
     key = _ints_to_bits([3, p, 9], gamma)
