@@ -190,13 +190,32 @@ static int build_xform(pa_plan_t *pl, Xform &X, uint64_t G, uint64_t K) {
     X.wt_hi = up(powers(gl_pow(th, nlo), nhi));
     X.iwt_lo = up(powers(thi, nlo));
     X.iwt_hi = up(powers(gl_pow(thi, nlo), nhi, ninv));
+    // column-pass weights: theta^beta_r and theta^beta_r / 2, beta_r = (-G C r) mod N
+    {
+        std::vector<u64> cw(2 * (size_t)X.R);
+        const u64 half = gl_inv(2);
+        for (u32 r = 0; r < X.R; r++) {
+            const u64 beta = (0ULL - G * X.C * (u64)r) & (X.N - 1);
+            cw[r] = gl_pow(th, beta);
+            cw[X.R + r] = gl_mul(cw[r], half);
+        }
+        X.colw = up(cw);
+    }
+    if (err) return err;
+    {
+        void *d = nullptr;
+        if (cudaMalloc(&d, X.N * sizeof(u64)) != cudaSuccess) return PA_ERR_NOMEM;
+        pl->tables.allocs.push_back(d);
+        X.coltw = (const u64 *)d;
+        if (launch_fill_coltw(X, (u64 *)d, nullptr) || cudaDeviceSynchronize() != cudaSuccess) return PA_ERR_CUDA;
+    }
     return err;
 }
 
 // Device bytes of a plan's workspace (shared by pa_plan and the server's admission).
 struct WsSizes {
-    uint64_t Y, S, ybuf, tbuf, H, cstate, cta, flags;
-    uint64_t total() const { return Y + S + ybuf + tbuf + H + cstate + 2 * cta + flags; }
+    uint64_t Y, S, ybuf, tbuf, H, cstate, cta, flags, tables;
+    uint64_t total() const { return Y + S + ybuf + tbuf + H + cstate + 2 * cta + flags + tables; }
 };
 static WsSizes ws_sizes(uint32_t gamma, uint64_t k, uint64_t N1, uint64_t N2) {
     WsSizes z;
@@ -210,6 +229,7 @@ static WsSizes ws_sizes(uint32_t gamma, uint64_t k, uint64_t N1, uint64_t N2) {
     z.cstate = nch;
     z.cta = nch / PA_CARRY_T + 1;
     z.flags = (4 + k) * sizeof(int);
+    z.tables = (N1 + N2) * 8;  // full column-pass twiddle tables
     return z;
 }
 

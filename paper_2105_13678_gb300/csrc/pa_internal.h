@@ -96,6 +96,13 @@ struct Xform {
     const u64 *iipw_lo, *iipw_hi;    // omega_N^-e
     const u64 *wt_lo, *wt_hi;        // theta^e
     const u64 *iwt_lo, *iwt_hi;      // theta^-e / N
+    // Column-pass tables.  With j = r C + c, (-G j) mod N = (beta_r + alpha_c) mod N,
+    // beta_r = (-G C r) mod N, alpha_c = (-G c) mod N, so the weight is
+    // theta^beta_r * theta^alpha_c / 2^[beta_r + alpha_c >= N].  The row factor
+    // (and the halving) is applied before the column transform, the column
+    // factor after it, merged with the inter-pass twiddle:
+    const u64 *colw;                 // [0, R): theta^beta_r; [R, 2R): theta^beta_r / 2
+    const u64 *coltw;                // N entries, [r][c]: omega_N^(c bitrev_R(r)) theta^alpha_c
 };
 
 // Where the digits of operand o come from.
@@ -146,5 +153,6 @@ int launch_extract(const u64 *t, u64 gamma, u64 r, const int *reload, u64 k, u64
                    int *status, void *stream);
 int launch_canonical_zero(const int *flag, u64 *y, u64 words, void *stream);
 int launch_selftest_field(const u64 *a, const u64 *b, u64 *out, u64 n, void *stream);
+int launch_fill_coltw(const Xform &X, u64 *coltw, void *stream);
 
 }  // namespace pa

@@ -131,16 +131,19 @@ __device__ __forceinline__ u64 op_digit(const OpDesc &d, u64 j, u64 slo, u64 shi
     return dig;
 }
 
-// Weighted digits j of both operands of a pair: digit * theta^((-G j) mod N).
-__device__ __forceinline__ void weighted_pair(const Xform &X, const OpDesc &dx, const OpDesc &da, u64 j, u64 &wx,
-                                              u64 &wa, bool &ones) {
+// Digits j = r C + c of both operands of a pair, times the row part of the
+// weight theta^((-G j) mod N) (the column part is applied after the column
+// transform, inside coltw).
+__device__ __forceinline__ void weighted_pair(const Xform &X, const OpDesc &dx, const OpDesc &da, u32 r, u32 c,
+                                              u64 alpha_c, u64 &wx, u64 &wa, bool &ones) {
+    const u64 j = (u64)r * X.C + c;
     const u64 slo = digit_start(X.G, j, X.N, X.logN);
     const u64 shi = digit_start(X.G, j + 1, X.N, X.logN);
     bool dummy = true;
     const u64 gx = op_digit(dx, j, slo, shi, ones);
     const u64 ga = op_digit(da, j, slo, shi, dummy);
-    const u64 e = (0ULL - X.G * j) & (X.N - 1);
-    const u64 w = tbl2(X.wt_lo, X.wt_hi, e, X.hb);
+    const u64 beta_r = (0ULL - X.G * X.C * (u64)r) & (X.N - 1);
+    const u64 w = __ldg(X.colw + r + (beta_r + alpha_c >= X.N ? X.R : 0));
     wx = gx ? gd_mul(gx, w) : 0;
     wa = ga ? gd_mul(ga, w) : 0;
 }
@@ -159,10 +162,10 @@ __device__ __forceinline__ void weighted_pair(const Xform &X, const OpDesc &dx, 
     } while (0)
 
 
-template <int NS, bool LAST>
+template <int NS, bool FIRST, bool LAST>
 __device__ __forceinline__ void fwd_col_round(const Xform &X, const OpDesc &dx, const OpDesc &da,
                                               u64 *__restrict__ smx, u64 *__restrict__ sma, u64 *__restrict__ Yx,
-                                              u64 *__restrict__ Ya, u32 c0, u32 s0, bool first, bool &ones) {
+                                              u64 *__restrict__ Ya, u32 c0, u32 s0, bool &ones) {
     const u32 l = X.logR, tc = X.tc;
     const u32 sh = l - s0 - NS, stride = 1u << sh;
     const u32 ntask = (X.R >> NS) * tc;
@@ -170,12 +173,13 @@ __device__ __forceinline__ void fwd_col_round(const Xform &X, const OpDesc &dx, 
     for (u32 task = threadIdx.x; task < ntask; task += blockDim.x) {
         const u32 c = task & (tc - 1), g = task >> logtc;
         const u32 lo = g & (stride - 1), base = ((g >> sh) << (l - s0)) + lo;
+        const u64 alpha_c = (0ULL - X.G * (u64)(c0 + c)) & (X.N - 1);
         u64 vx[8], va[8];
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
             const u32 r = base + m * stride;
-            if (first) {
-                weighted_pair(X, dx, da, (u64)r * X.C + c0 + c, vx[m], va[m], ones);
+            if (FIRST) {
+                weighted_pair(X, dx, da, r, c0 + c, alpha_c, vx[m], va[m], ones);
             } else {
                 vx[m] = smx[pidx(r * tc + c)];
                 va[m] = sma[pidx(r * tc + c)];
@@ -187,9 +191,8 @@ __device__ __forceinline__ void fwd_col_round(const Xform &X, const OpDesc &dx, 
         for (int m = 0; m < (1 << NS); m++) {
             const u32 r = base + m * stride;
             if (LAST) {
-                // position r holds column frequency bitrev(r): twiddle omega_N^(c * k_r)
-                const u64 e = (u64)(c0 + c) * bitrev(r, l);
-                const u64 t = tbl2(X.ipw_lo, X.ipw_hi, e, X.hb);
+                // position r holds column frequency bitrev(r): omega_N^(c k_r) theta^alpha_c
+                const u64 t = __ldg(X.coltw + (u64)r * X.C + c0 + c);
                 Yx[(u64)r * X.C + c0 + c] = gd_mul(vx[m], t);
                 Ya[(u64)r * X.C + c0 + c] = gd_mul(va[m], t);
             } else {
@@ -201,7 +204,7 @@ __device__ __forceinline__ void fwd_col_round(const Xform &X, const OpDesc &dx, 
 }
 
 // One CTA: a tile of tc columns of both operands of pair blockIdx.y.
-__global__ void __launch_bounds__(PA_COL_T) k_fwd_col(Xform X, Operands S, u64 *__restrict__ Y) {
+__global__ void __launch_bounds__(PA_COL_T, 3) k_fwd_col(Xform X, Operands S, u64 *__restrict__ Y) {
     extern __shared__ u64 sm[];
     const u32 tc = X.tc, c0 = blockIdx.x * tc, i = blockIdx.y;
     OpDesc dx, da;
@@ -213,21 +216,27 @@ __global__ void __launch_bounds__(PA_COL_T) k_fwd_col(Xform X, Operands S, u64 *
     if (l == 0) {
         for (u32 c = threadIdx.x; c < tc; c += blockDim.x) {
             u64 wx, wa;
-            weighted_pair(X, dx, da, c0 + c, wx, wa, ones);
-            Yx[c0 + c] = wx;
-            Ya[c0 + c] = wa;
+            const u64 alpha_c = (0ULL - X.G * (u64)(c0 + c)) & (X.N - 1);
+            weighted_pair(X, dx, da, 0, c0 + c, alpha_c, wx, wa, ones);
+            const u64 t = __ldg(X.coltw + c0 + c);
+            Yx[c0 + c] = gd_mul(wx, t);
+            Ya[c0 + c] = gd_mul(wa, t);
         }
     } else {
         const u32 nr = (l + 2) / 3;
         for (u32 rd = 0; rd < nr; rd++) {
             const u32 s0 = 3 * rd, ns = min(3u, l - s0);
             const bool first = rd == 0, last = rd == nr - 1;
-#define PA_FWD_COL(NSV)                                                                 \
-    do {                                                                                \
-        if (last)                                                                       \
-            fwd_col_round<NSV, true>(X, dx, da, smx, sma, Yx, Ya, c0, s0, first, ones);  \
-        else                                                                            \
-            fwd_col_round<NSV, false>(X, dx, da, smx, sma, Yx, Ya, c0, s0, first, ones); \
+#define PA_FWD_COL(NSV)                                                               \
+    do {                                                                              \
+        if (first && last)                                                            \
+            fwd_col_round<NSV, true, true>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones);   \
+        else if (first)                                                               \
+            fwd_col_round<NSV, true, false>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones);  \
+        else if (last)                                                                \
+            fwd_col_round<NSV, false, true>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones);  \
+        else                                                                          \
+            fwd_col_round<NSV, false, false>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones); \
     } while (0)
             PA_DISPATCH_NS(ns, PA_FWD_COL);
 #undef PA_FWD_COL
@@ -311,7 +320,7 @@ __device__ __forceinline__ void row_inv_round(const Xform &X, u64 *__restrict__ 
 
 // One CTA per row; blockDim = C / ACC threads, each owning ACC accumulators.
 template <int ACC>
-__global__ void __launch_bounds__(512) k_row_mac(Xform X, const u64 *__restrict__ Y, u64 *__restrict__ S) {
+__global__ void __launch_bounds__(512, ACC == 8 ? 2 : 1) k_row_mac(Xform X, const u64 *__restrict__ Y, u64 *__restrict__ S) {
     extern __shared__ u64 sm[];
     const u32 C = X.C, row = blockIdx.x, l = X.logC;
     const u64 N = X.N;
@@ -366,9 +375,9 @@ __global__ void __launch_bounds__(512) k_row_mac(Xform X, const u64 *__restrict_
 
 // ------------------------------------------------------ inverse columns --
 
-template <int NS, bool LASTSTAGE>
+template <int NS, bool LASTSTAGE, bool TOGLOBAL>
 __device__ __forceinline__ void inv_col_round(const Xform &X, const u64 *__restrict__ Sg, u64 *__restrict__ sm,
-                                              u64 *__restrict__ Z, u32 c0, u32 s0, bool first, bool last,
+                                              u64 *__restrict__ Z, u32 c0, u32 s0,
                                               const u64 *__restrict__ add_src, u64 add_base, u64 add_len) {
     const u32 l = X.logR, tc = X.tc;
     const u32 sh = l - s0 - NS, stride = 1u << sh;
@@ -381,13 +390,13 @@ __device__ __forceinline__ void inv_col_round(const Xform &X, const u64 *__restr
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
             const u32 r = base + m * stride;
-            v[m] = first ? __ldg(Sg + (u64)r * X.C + c0 + c) : sm[pidx(r * tc + c)];
+            v[m] = LASTSTAGE ? __ldg(Sg + (u64)r * X.C + c0 + c) : sm[pidx(r * tc + c)];
         }
         dit_regs<NS, LASTSTAGE>(v, s0, lo, stride, X.itwR);
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
             const u32 r = base + m * stride;
-            if (last) {
+            if (TOGLOBAL) {
                 const u64 j = (u64)r * X.C + c0 + c;
                 const u64 e = (0ULL - X.G * j) & (X.N - 1);
                 u64 z = gd_canon(gd_mul(v[m], tbl2(X.iwt_lo, X.iwt_hi, e, X.hb)));
@@ -429,12 +438,16 @@ __global__ void __launch_bounds__(PA_COL_T) k_inv_col(Xform X, const u64 *__rest
     for (int rd = (int)nr - 1; rd >= 0; rd--) {
         const u32 s0 = 3 * rd, ns = min(3u, l - s0);
         const bool first = rd == (int)nr - 1, last = rd == 0;
-#define PA_INV_COL(NSV)                                                                              \
-    do {                                                                                             \
-        if (first)                                                                                   \
-            inv_col_round<NSV, true>(X, Sg, sm, Z, c0, s0, first, last, add_src, add_base, add_len);  \
-        else                                                                                         \
-            inv_col_round<NSV, false>(X, Sg, sm, Z, c0, s0, first, last, add_src, add_base, add_len); \
+#define PA_INV_COL(NSV)                                                                       \
+    do {                                                                                      \
+        if (first && last)                                                                    \
+            inv_col_round<NSV, true, true>(X, Sg, sm, Z, c0, s0, add_src, add_base, add_len);   \
+        else if (first)                                                                       \
+            inv_col_round<NSV, true, false>(X, Sg, sm, Z, c0, s0, add_src, add_base, add_len);  \
+        else if (last)                                                                        \
+            inv_col_round<NSV, false, true>(X, Sg, sm, Z, c0, s0, add_src, add_base, add_len);  \
+        else                                                                                  \
+            inv_col_round<NSV, false, false>(X, Sg, sm, Z, c0, s0, add_src, add_base, add_len); \
     } while (0)
         PA_DISPATCH_NS(ns, PA_INV_COL);
 #undef PA_INV_COL
@@ -678,6 +691,21 @@ __global__ void k_selftest_field(const u64 *__restrict__ a, const u64 *__restric
         out[3 * i + 1] = gd_canon(gd_sub(a[i], b[i]));
         out[3 * i + 2] = gd_canon(gd_mul(a[i], b[i]));
     }
+}
+
+// coltw[r C + c] = omega_N^(c bitrev_R(r)) * theta^((-G c) mod N), canonical.
+__global__ void k_fill_coltw(Xform X, u64 *__restrict__ out) {
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < X.N; i += (u64)gridDim.x * blockDim.x) {
+        const u32 r = (u32)(i >> X.logC), c = (u32)(i & (X.C - 1));
+        const u64 e = (u64)c * bitrev(r, X.logR);
+        const u64 alpha = (0ULL - X.G * (u64)c) & (X.N - 1);
+        out[i] = gd_canon(gd_mul(tbl2(X.ipw_lo, X.ipw_hi, e, X.hb), tbl2(X.wt_lo, X.wt_hi, alpha, X.hb)));
+    }
+}
+
+int launch_fill_coltw(const Xform &X, u64 *coltw, void *stream) {
+    k_fill_coltw<<<256, 256, 0, (cudaStream_t)stream>>>(X, coltw);
+    return (int)cudaGetLastError();
 }
 
 int launch_selftest_field(const u64 *a, const u64 *b, u64 *out, u64 n, void *stream) {

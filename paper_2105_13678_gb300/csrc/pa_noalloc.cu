@@ -62,7 +62,7 @@ struct TableJob {
     u32 count;
 };
 struct TableJobs {
-    TableJob t[24];
+    TableJob t[26];
 };
 
 // Table y of the batch: dst[i] = scale * base^i for i < count.
@@ -136,6 +136,24 @@ void geometry_and_tables(Xform &X, uint64_t G, uint64_t K, uint32_t l, u32 stage
     add(X.wt_hi, gl_pow(th, nlo), nhi, 1);
     add(X.iwt_lo, thi, nlo, 1);
     add(X.iwt_hi, gl_pow(thi, nlo), nhi, ninv);
+    // column weights theta^beta_r (and / 2) are filled by k_fill_colw; coltw by launch_fill_coltw
+    X.colw = cv.take(2 * (unsigned long long)X.R);
+    X.coltw = cv.take(X.N);
+}
+
+// colw[r] = theta^beta_r, colw[R + r] = theta^beta_r / 2, beta_r = (-G C r) mod N.
+__global__ void k_fill_colw(Xform X, u64 theta, u64 half) {
+    u64 *out = const_cast<u64 *>(X.colw);
+    for (u32 r = blockIdx.x * blockDim.x + threadIdx.x; r < X.R; r += gridDim.x * blockDim.x) {
+        const u64 beta = (0ULL - X.G * X.C * (u64)r) & (X.N - 1);
+        u64 v = 1, b = theta;
+        for (u64 e = beta; e; e >>= 1) {
+            if (e & 1) v = gd_mul(v, b);
+            b = gd_mul(b, b);
+        }
+        out[r] = gd_canon(v);
+        out[X.R + r] = gd_canon(gd_mul(v, half));
+    }
 }
 
 }  // namespace
@@ -180,6 +198,16 @@ extern "C" int pa_hash_noalloc(uint64_t n_bits, uint64_t r_bits, const pa_params
     if (prepare_kernels()) return PA_ERR_CUDA;
     k_fill_tables<<<dim3(16, nj), 256, 0, s>>>(jobs);
     int e = (int)cudaGetLastError();
+    const u64 half = gl_inv(2);
+    for (Xform *X : {&X1, &X2}) {
+        u64 w = 0, th = 0;
+        pa_field_constants(X->logN, (uint64_t *)&w, (uint64_t *)&th);
+        if (!e) {
+            k_fill_colw<<<8, 256, 0, s>>>(*X, th, half);
+            e = (int)cudaGetLastError();
+        }
+        if (!e) e = launch_fill_coltw(*X, const_cast<u64 *>(X->coltw), stream);
+    }
     if (!e) e = cudaMemsetAsync(flags, 0, flag_bytes, s);
 
     Operands ops;
