@@ -127,7 +127,7 @@ struct CarryDev {
     int *allones;         // set when the resolved value is 2^G - 1 (== 0)
 };
 
-constexpr u32 PA_CARRY_D = 16;     // digits per thread chunk
+constexpr u32 PA_CARRY_D = 8;      // digits per thread chunk
 constexpr u32 PA_CARRY_T = 256;    // threads per CTA in the carry kernels
 constexpr u32 PA_COL_T = 256;      // threads per CTA in the column passes
 constexpr u32 PA_MAX_LOGN = 24;    // largest transform the kernels implement

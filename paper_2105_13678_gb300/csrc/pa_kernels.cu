@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(PA_CARRY_T) k_carry_a(CarryDev cd, const u64 *
     const u64 j0 = t * PA_CARRY_D;
     u64 zz[PA_CARRY_D];
     u32 bd[PA_CARRY_D];
-    const ulonglong2 *z2 = reinterpret_cast<const ulonglong2 *>(z + j0);
+    const ulonglong2 *z2 = reinterpret_cast<const ulonglong2 *>(z + j0);  // j0 is a multiple of 8
 #pragma unroll
     for (u32 d = 0; d < PA_CARRY_D / 2; d++) {
         const ulonglong2 w = __ldg(z2 + d);
@@ -512,7 +512,6 @@ __global__ void __launch_bounds__(PA_CARRY_T) k_carry_a(CarryDev cd, const u64 *
     }
     const u64 Ht = (u64)acc;
     Hs[threadIdx.x] = Ht;
-    cd.H[t] = Ht;
     if (threadIdx.x == 0) Hprev = chunk_carry_out(cd, z, t == 0 ? cd.nchunks - 1 : t - 1);
     __syncthreads();
     const u64 Hin = threadIdx.x ? Hs[threadIdx.x - 1] : Hprev;
@@ -560,27 +559,44 @@ __global__ void __launch_bounds__(PA_CARRY_T) k_carry_a(CarryDev cd, const u64 *
     }
 }
 
-// One warp: carry into every CTA range, closed around the ring.
-__global__ void k_carry_b(CarryDev cd, u32 nctas) {
-    const u32 lane = threadIdx.x;
-    unsigned cin = 0;
-    for (u32 base = 0; base < nctas; base += 32) {
-        const unsigned st = (base + lane < nctas) ? cd.cta_state[base + lane] : 2u;
-        const unsigned gm = __ballot_sync(0xFFFFFFFFu, st & 1), pm = __ballot_sync(0xFFFFFFFFu, (st >> 1) & 1);
-        cin = (unsigned)((((u64)(gm | pm)) + gm + cin) >> 32);
+// Carry into every CTA range, closed around the ring: each of 1024 threads
+// folds a run of CTA states, a two-level ballot scan gives every run its
+// carry-in, and each thread walks its run.  The carry out of the top (with no
+// carry in) wraps to bit 0; if every range propagates, the value is all ones
+// and no carry is taken.
+__global__ void __launch_bounds__(1024) k_carry_b(CarryDev cd, u32 nctas) {
+    __shared__ unsigned wG[32], wP[32], wcin[32];
+    const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const u32 per = (nctas + 1023) / 1024;
+    const u32 b0 = min(tid * per, nctas), b1 = min(b0 + per, nctas);
+    unsigned G = 0, P = 1;
+    for (u32 b = b0; b < b1; b++) {
+        const unsigned st = cd.cta_state[b];
+        G = (st & 1) | (((st >> 1) & 1) & G);
+        P = ((st >> 1) & 1) & P;
     }
-    // cin is now the carry out of the top with carry-in 0: it wraps to bit 0
-    // (if every range propagates, the value is all ones and no carry is taken).
-    unsigned c = cin;
-    for (u32 base = 0; base < nctas; base += 32) {
-        const unsigned st = (base + lane < nctas) ? cd.cta_state[base + lane] : 2u;
-        const unsigned gm = __ballot_sync(0xFFFFFFFFu, st & 1), pm = __ballot_sync(0xFFFFFFFFu, (st >> 1) & 1);
-        const u64 a = gm | pm, sum = a + gm + c;
-        const u64 into = sum ^ a ^ gm;
-        if (base + lane < nctas) cd.cta_cin[base + lane] = (unsigned char)((into >> lane) & 1);
-        c = (unsigned)(sum >> 32);
+    const unsigned gm = __ballot_sync(0xFFFFFFFFu, G), pm = __ballot_sync(0xFFFFFFFFu, P);
+    if (lane == 0) {
+        wG[warp] = (unsigned)((((u64)(gm | pm)) + gm) >> 32);
+        wP[warp] = (pm == 0xFFFFFFFFu);
     }
-    if (lane == 0) *cd.allones = 1;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned g2 = __ballot_sync(0xFFFFFFFFu, wG[lane]), p2 = __ballot_sync(0xFFFFFFFFu, wP[lane]);
+        const u64 a = g2 | p2;
+        const unsigned ewrap = (unsigned)((a + g2) >> 32);
+        const u64 sum = a + g2 + ewrap;
+        wcin[lane] = (unsigned)(((sum ^ a ^ g2) >> lane) & 1);
+        if (lane == 0) *cd.allones = 1;
+    }
+    __syncthreads();
+    const u64 a = gm | pm, sum = a + gm + wcin[warp];
+    unsigned c = (unsigned)(((sum ^ a ^ gm) >> lane) & 1);
+    for (u32 b = b0; b < b1; b++) {
+        cd.cta_cin[b] = (unsigned char)c;
+        const unsigned st = cd.cta_state[b];
+        c = (st & 1) | (((st >> 1) & 1) & c);
+    }
 }
 
 __global__ void __launch_bounds__(PA_CARRY_T) k_carry_c(CarryDev cd, u64 *__restrict__ y) {
@@ -775,14 +791,16 @@ int launch_carry(const Xform &X, const CarryDev &cd, u64 *z, u64 *out_bits, u64 
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(out_bits, 0, out_words * sizeof(u64), s);
     if (e) return e;
-    const bool parallel = cd.nchunks >= PA_CARRY_T && (X.G >> X.logN) >= 4;
+    // chunks of PA_CARRY_D digits must span >= 64 bits so that adding the
+    // previous chunk's carry-out leaves a 1-bit carry
+    const bool parallel = cd.nchunks >= PA_CARRY_T && (X.G >> X.logN) * PA_CARRY_D >= 64;
     if (!parallel) {
         TRACED("carry_seq", X.stage, stream, (k_carry_seq<<<1, 32, 0, s>>>(cd, z, out_bits)));
         return (int)cudaGetLastError();
     }
     const u32 nctas = (u32)(cd.nchunks / PA_CARRY_T);
     TRACED("carry_a", X.stage, stream, (k_carry_a<<<nctas, PA_CARRY_T, 0, s>>>(cd, z, out_bits)));
-    TRACED("carry_b", X.stage, stream, (k_carry_b<<<1, 32, 0, s>>>(cd, nctas)));
+    TRACED("carry_b", X.stage, stream, (k_carry_b<<<1, 1024, 0, s>>>(cd, nctas)));
     TRACED("carry_c", X.stage, stream, (k_carry_c<<<nctas, PA_CARRY_T, 0, s>>>(cd, out_bits)));
     return (int)cudaGetLastError();
 }
