@@ -94,6 +94,17 @@ int pa_hash_host(pa_plan_t *plan, const uint64_t *key, const uint64_t *seed, uin
 int pa_debug_mmh(pa_plan_t *plan, const uint64_t *key, const uint64_t *seed, uint64_t *y,
                  int *status, void *stream);
 
+/* Seed reuse.  When the same hash seed (a, b, c) serves many blocks,
+ * pa_seed_prepare transforms a_1..a_k and b once and keeps their spectra (and
+ * a copy of the seed) in the plan: k N_mmh + N_mh words plus the seed, allocated
+ * on the first call (blocking).  pa_hash_prepared then runs Algorithm 1 on a
+ * key with that seed, transforming only the key slices and y: k + 3 transforms
+ * instead of 2k + 4, same output bits as pa_hash with the same seed.  Returns
+ * PA_ERR_INVALID if the plan has no prepared seed.  Both are asynchronous on
+ * `stream` and use the plan's workspace like pa_hash. */
+int pa_seed_prepare(pa_plan_t *plan, const uint64_t *seed, void *stream);
+int pa_hash_prepared(pa_plan_t *plan, const uint64_t *key, uint64_t *out, int *status, void *stream);
+
 /* Algorithm 1 without any device allocation, for callers that cannot call
  * cudaMalloc (device memory owned by another allocator or pool, code paths
  * where an allocation and its possible device synchronisation are not

@@ -67,6 +67,8 @@ SIGNATURES = {
     "pa_hash": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "pa_hash_host": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "pa_debug_mmh": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "pa_seed_prepare": (ctypes.c_int, [_vp, _vp, _vp]),
+    "pa_hash_prepared": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "pa_hash_noalloc": (ctypes.c_int, [_u64, _u64, ctypes.POINTER(pa_params), _vp, _vp, _vp, _vp, _vp]),
     "pa_hash_batch": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                      ctypes.POINTER(_vp), _vp, ctypes.c_int, _vp]),
@@ -160,6 +162,15 @@ class Plan:
 def pa_hash(plan: Plan, key_ptr: int, seed_ptr: int, out_ptr: int, status_ptr: int = 0, stream: int = 0) -> int:
     return check(lib().pa_hash(plan.handle, key_ptr, seed_ptr, out_ptr, status_ptr or None, stream or None),
                  "pa_hash")
+
+
+def pa_seed_prepare(plan: Plan, seed_ptr: int, stream: int = 0) -> int:
+    return check(lib().pa_seed_prepare(plan.handle, seed_ptr, stream or None), "pa_seed_prepare")
+
+
+def pa_hash_prepared(plan: Plan, key_ptr: int, out_ptr: int, status_ptr: int = 0, stream: int = 0) -> int:
+    return check(lib().pa_hash_prepared(plan.handle, key_ptr, out_ptr, status_ptr or None, stream or None),
+                 "pa_hash_prepared")
 
 
 def pa_debug_mmh(plan: Plan, key_ptr: int, seed_ptr: int, y_ptr: int, status_ptr: int = 0, stream: int = 0) -> int:

@@ -135,6 +135,9 @@ struct pa_plan_s {
     int *flags = nullptr;   // [0] reload, [1] y all-ones, [2] t all-ones, [3] -, [4..4+k) slice counters
     size_t flags_bytes = 0;
     uint64_t ws_bytes = 0;
+    // seed reuse (pa_seed_prepare): stored spectra of a_1..a_k and b, seed copy
+    u64 *spec_a = nullptr, *spec_b = nullptr, *seed_copy = nullptr;
+    bool prepared = false;
     // device staging for pa_hash_host: key | seed | out | status
     u64 *dkey = nullptr, *dseed = nullptr, *dout = nullptr;
     int *dstatus = nullptr;
@@ -382,6 +385,20 @@ static int enqueue_mh(pa_plan_t *pl, const u64 *seed, u64 *out, int *status, voi
 
 static int cuda_rc(int e) { return e ? PA_ERR_CUDA : PA_OK; }
 
+static CarryDev carry_dev(pa_plan_t *pl, const Xform &X, int *allones) {
+    CarryDev cd;
+    cd.N = X.N;
+    cd.G = X.G;
+    cd.logN = X.logN;
+    cd.nchunks = X.N / PA_CARRY_D;
+    cd.H = pl->H;
+    cd.state = pl->cstate;
+    cd.cta_state = pl->cta_state;
+    cd.cta_cin = pl->cta_cin;
+    cd.allones = allones;
+    return cd;
+}
+
 extern "C" {
 
 int pa_hash(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint64_t *out, int *status, void *stream) {
@@ -421,6 +438,71 @@ int pa_hash_host(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint6
     if ((e = cudaMemcpyAsync(&st, pl->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s))) return PA_ERR_CUDA;
     if ((e = cudaStreamSynchronize(s))) return PA_ERR_CUDA;
     return st ? PA_RELOAD : PA_OK;
+}
+
+// Seed reuse: transform a_1..a_k (Eq. 2) and b (Eq. 4) once and keep their
+// spectra in the plan; pa_hash_prepared then transforms only the key slices
+// and y.  The plan keeps a copy of the seed (c is read from it).
+int pa_seed_prepare(pa_plan_t *pl, const uint64_t *seed, void *stream) {
+    if (!pl || !seed) return PA_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t sw = ((pl->k + 2) * pl->gamma + 63) / 64;
+    if (!pl->spec_a) {
+        int err = PA_OK;
+        pl->spec_a = (u64 *)pl->alloc(pl->k * pl->mmh.N * 8, &err);
+        pl->spec_b = (u64 *)pl->alloc(pl->mh.N * 8, &err);
+        pl->seed_copy = (u64 *)pl->alloc(sw * 8, &err);
+        if (err) return err;
+    }
+    pl->prepared = false;
+    int e = cudaMemcpyAsync(pl->seed_copy, seed, sw * 8, cudaMemcpyDeviceToDevice, s);
+    Operands ops;
+    ops.key = nullptr;
+    ops.seed = pl->seed_copy;
+    ops.y = nullptr;
+    ops.y_zero = nullptr;
+    ops.reload = pl->flags;
+    ops.n = pl->n;
+    ops.gamma = pl->gamma;
+    ops.k = pl->k;
+    ops.mode = 2;  // a_i
+    if (!e) e = launch_fwd_col_single(pl->mmh, ops, (int)pl->k, pl->Y, stream);
+    if (!e) e = launch_row_store(pl->mmh, pl->Y, pl->spec_a, stream);
+    ops.mode = 4;  // b
+    if (!e) e = launch_fwd_col_single(pl->mh, ops, 1, pl->Y, stream);
+    if (!e) e = launch_row_store(pl->mh, pl->Y, pl->spec_b, stream);
+    if (e) return PA_ERR_CUDA;
+    pl->prepared = true;
+    return PA_OK;
+}
+
+int pa_hash_prepared(pa_plan_t *pl, const uint64_t *key, uint64_t *out, int *status, void *stream) {
+    if (!pl || !key || !out || !pl->prepared) return PA_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    int e = cudaMemsetAsync(pl->flags, 0, pl->flags_bytes, s);
+    Operands ops;
+    ops.key = (const u64 *)key;
+    ops.seed = pl->seed_copy;
+    ops.y = pl->ybuf;
+    ops.y_zero = pl->flags + 1;
+    ops.reload = pl->flags;
+    ops.n = pl->n;
+    ops.gamma = pl->gamma;
+    ops.k = pl->k;
+    // Eq. 2 with stored spectra of a_i
+    ops.mode = 3;  // x_i
+    if (!e) e = launch_fwd_col_single(pl->mmh, ops, (int)pl->k, pl->Y, stream);
+    if (!e) e = launch_row_prepared(pl->mmh, pl->Y, pl->spec_a, pl->S, stream);
+    if (!e) e = launch_inv_col(pl->mmh, pl->S, pl->Y, nullptr, 0, 0, stream);
+    if (!e) e = launch_carry(pl->mmh, carry_dev(pl, pl->mmh, pl->flags + 1), pl->Y, pl->ybuf, (pl->gamma + 63) / 64, stream);
+    // Eq. 4 with the stored spectrum of b
+    ops.mode = 5;  // y
+    if (!e) e = launch_fwd_col_single(pl->mh, ops, 1, pl->Y, stream);
+    if (!e) e = launch_row_prepared(pl->mh, pl->Y, pl->spec_b, pl->S, stream);
+    if (!e) e = launch_inv_col(pl->mh, pl->S, pl->Y, pl->seed_copy, (pl->k + 1) * (u64)pl->gamma, pl->gamma, stream);
+    if (!e) e = launch_carry(pl->mh, carry_dev(pl, pl->mh, pl->flags + 2), pl->Y, pl->tbuf, (2ULL * pl->gamma + 63) / 64, stream);
+    if (!e) e = launch_extract(pl->tbuf, pl->gamma, pl->r, pl->flags, pl->k, (u64 *)out, status, stream);
+    return cuda_rc(e);
 }
 
 const char *pa_status_string(int code) {

@@ -113,7 +113,7 @@ struct Operands {
     const int *y_zero;  // if *y_zero != 0, y is p itself and reads as 0
     int *reload;        // reload flag + per-slice all-ones counters (Algorithm 1)
     u64 n, gamma, k;
-    int mode;           // 0: MMH (x_1..x_k then a_1..a_k), 1: MH (y, b)
+    int mode;           // pairs: 0 MMH (x_i, a_i), 1 MH (y, b); single: 2 a_i, 3 x_i, 4 b, 5 y
 };
 
 // Carry resolution of N digits (value mod 2^G - 1, end-around carry).
@@ -145,6 +145,9 @@ void trace_end(void *token, void *stream);
 int prepare_kernels();
 int launch_fwd_col(const Xform &X, const Operands &S, int num_pairs, u64 *Y, void *stream);
 int launch_row_mac(const Xform &X, const u64 *Y, u64 *S, void *stream);
+int launch_fwd_col_single(const Xform &X, const Operands &S, int num_operands, u64 *Y, void *stream);
+int launch_row_store(const Xform &X, const u64 *Y, u64 *Spec, void *stream);
+int launch_row_prepared(const Xform &X, const u64 *Y, const u64 *Spec, u64 *S, void *stream);
 int launch_inv_col(const Xform &X, const u64 *S, u64 *Z, const u64 *add_src, u64 add_base,
                    u64 add_len, void *stream);
 int launch_carry(const Xform &X, const CarryDev &cd, u64 *z, u64 *out_bits, u64 out_words,

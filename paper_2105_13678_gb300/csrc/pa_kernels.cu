@@ -121,6 +121,32 @@ __device__ __forceinline__ void pair_desc(const Operands &S, u32 i, OpDesc &dx, 
     }
 }
 
+// Single operands (seed preparation and prepared hashing): mode 2 = a_{i+1},
+// 3 = x_{i+1}, 4 = b (forced odd), 5 = y.
+__device__ __forceinline__ void single_desc(const Operands &S, u32 i, OpDesc &d) {
+    d.force_odd = 0;
+    d.check_ones = 0;
+    d.zero = 0;
+    d.src = S.seed;
+    d.len = S.gamma;
+    if (S.mode == 2) {
+        d.base = (u64)i * S.gamma;
+    } else if (S.mode == 3) {
+        d.src = S.key;
+        d.base = (u64)i * S.gamma;
+        const u64 rem = S.n - d.base;
+        d.len = rem < S.gamma ? rem : S.gamma;
+        d.check_ones = 1;
+    } else if (S.mode == 4) {
+        d.base = S.k * S.gamma;
+        d.force_odd = 1;
+    } else {
+        d.src = S.y;
+        d.base = 0;
+        d.zero = (*S.y_zero != 0);
+    }
+}
+
 __device__ __forceinline__ u64 op_digit(const OpDesc &d, u64 j, u64 slo, u64 shi, bool &ones) {
     const u64 hi = shi < d.len ? shi : d.len;
     u64 dig = 0;
@@ -134,18 +160,21 @@ __device__ __forceinline__ u64 op_digit(const OpDesc &d, u64 j, u64 slo, u64 shi
 // Digits j = r C + c of both operands of a pair, times the row part of the
 // weight theta^((-G j) mod N) (the column part is applied after the column
 // transform, inside coltw).
+template <bool PAIR>
 __device__ __forceinline__ void weighted_pair(const Xform &X, const OpDesc &dx, const OpDesc &da, u32 r, u32 c,
                                               u64 alpha_c, u64 &wx, u64 &wa, bool &ones) {
     const u64 j = (u64)r * X.C + c;
     const u64 slo = digit_start(X.G, j, X.N, X.logN);
     const u64 shi = digit_start(X.G, j + 1, X.N, X.logN);
-    bool dummy = true;
     const u64 gx = op_digit(dx, j, slo, shi, ones);
-    const u64 ga = op_digit(da, j, slo, shi, dummy);
     const u64 beta_r = (0ULL - X.G * X.C * (u64)r) & (X.N - 1);
     const u64 w = __ldg(X.colw + r + (beta_r + alpha_c >= X.N ? X.R : 0));
     wx = gx ? gd_mul(gx, w) : 0;
-    wa = ga ? gd_mul(ga, w) : 0;
+    if (PAIR) {
+        bool dummy = true;
+        const u64 ga = op_digit(da, j, slo, shi, dummy);
+        wa = ga ? gd_mul(ga, w) : 0;
+    }
 }
 
 // ------------------------------------------------------ forward columns --
@@ -162,7 +191,7 @@ __device__ __forceinline__ void weighted_pair(const Xform &X, const OpDesc &dx, 
     } while (0)
 
 
-template <int NS, bool FIRST, bool LAST>
+template <int NS, bool PAIR, bool FIRST, bool LAST>
 __device__ __forceinline__ void fwd_col_round(const Xform &X, const OpDesc &dx, const OpDesc &da,
                                               u64 *__restrict__ smx, u64 *__restrict__ sma, u64 *__restrict__ Yx,
                                               u64 *__restrict__ Ya, u32 c0, u32 s0, bool &ones) {
@@ -179,14 +208,14 @@ __device__ __forceinline__ void fwd_col_round(const Xform &X, const OpDesc &dx, 
         for (int m = 0; m < (1 << NS); m++) {
             const u32 r = base + m * stride;
             if (FIRST) {
-                weighted_pair(X, dx, da, r, c0 + c, alpha_c, vx[m], va[m], ones);
+                weighted_pair<PAIR>(X, dx, da, r, c0 + c, alpha_c, vx[m], va[m], ones);
             } else {
                 vx[m] = smx[pidx(r * tc + c)];
-                va[m] = sma[pidx(r * tc + c)];
+                if (PAIR) va[m] = sma[pidx(r * tc + c)];
             }
         }
         dif_regs<NS, LAST>(vx, s0, lo, stride, X.twR);
-        dif_regs<NS, LAST>(va, s0, lo, stride, X.twR);
+        if (PAIR) dif_regs<NS, LAST>(va, s0, lo, stride, X.twR);
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
             const u32 r = base + m * stride;
@@ -194,21 +223,26 @@ __device__ __forceinline__ void fwd_col_round(const Xform &X, const OpDesc &dx, 
                 // position r holds column frequency bitrev(r): omega_N^(c k_r) theta^alpha_c
                 const u64 t = __ldg(X.coltw + (u64)r * X.C + c0 + c);
                 Yx[(u64)r * X.C + c0 + c] = gd_mul(vx[m], t);
-                Ya[(u64)r * X.C + c0 + c] = gd_mul(va[m], t);
+                if (PAIR) Ya[(u64)r * X.C + c0 + c] = gd_mul(va[m], t);
             } else {
                 smx[pidx(r * tc + c)] = vx[m];
-                sma[pidx(r * tc + c)] = va[m];
+                if (PAIR) sma[pidx(r * tc + c)] = va[m];
             }
         }
     }
 }
 
-// One CTA: a tile of tc columns of both operands of pair blockIdx.y.
+// One CTA: a tile of tc columns of operand pair blockIdx.y (PAIR), written to
+// Y[i] and Y[K + i], or of the single operand blockIdx.y, written to Y[i].
+template <bool PAIR>
 __global__ void __launch_bounds__(PA_COL_T, 3) k_fwd_col(Xform X, Operands S, u64 *__restrict__ Y) {
     extern __shared__ u64 sm[];
     const u32 tc = X.tc, c0 = blockIdx.x * tc, i = blockIdx.y;
     OpDesc dx, da;
-    pair_desc(S, i, dx, da);
+    if (PAIR)
+        pair_desc(S, i, dx, da);
+    else
+        single_desc(S, i, dx);
     u64 *Yx = Y + (u64)i * X.N, *Ya = Y + (u64)(X.K + i) * X.N;
     u64 *smx = sm, *sma = sm + pidx(X.R * tc);
     bool ones = true;
@@ -217,26 +251,26 @@ __global__ void __launch_bounds__(PA_COL_T, 3) k_fwd_col(Xform X, Operands S, u6
         for (u32 c = threadIdx.x; c < tc; c += blockDim.x) {
             u64 wx, wa;
             const u64 alpha_c = (0ULL - X.G * (u64)(c0 + c)) & (X.N - 1);
-            weighted_pair(X, dx, da, 0, c0 + c, alpha_c, wx, wa, ones);
+            weighted_pair<PAIR>(X, dx, da, 0, c0 + c, alpha_c, wx, wa, ones);
             const u64 t = __ldg(X.coltw + c0 + c);
             Yx[c0 + c] = gd_mul(wx, t);
-            Ya[c0 + c] = gd_mul(wa, t);
+            if (PAIR) Ya[c0 + c] = gd_mul(wa, t);
         }
     } else {
         const u32 nr = (l + 2) / 3;
         for (u32 rd = 0; rd < nr; rd++) {
             const u32 s0 = 3 * rd, ns = min(3u, l - s0);
             const bool first = rd == 0, last = rd == nr - 1;
-#define PA_FWD_COL(NSV)                                                               \
-    do {                                                                              \
-        if (first && last)                                                            \
-            fwd_col_round<NSV, true, true>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones);   \
-        else if (first)                                                               \
-            fwd_col_round<NSV, true, false>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones);  \
-        else if (last)                                                                \
-            fwd_col_round<NSV, false, true>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones);  \
-        else                                                                          \
-            fwd_col_round<NSV, false, false>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones); \
+#define PA_FWD_COL(NSV)                                                                     \
+    do {                                                                                    \
+        if (first && last)                                                                  \
+            fwd_col_round<NSV, PAIR, true, true>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones);   \
+        else if (first)                                                                     \
+            fwd_col_round<NSV, PAIR, true, false>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones);  \
+        else if (last)                                                                      \
+            fwd_col_round<NSV, PAIR, false, true>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones);  \
+        else                                                                                \
+            fwd_col_round<NSV, PAIR, false, false>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones); \
     } while (0)
             PA_DISPATCH_NS(ns, PA_FWD_COL);
 #undef PA_FWD_COL
@@ -254,11 +288,20 @@ __global__ void __launch_bounds__(PA_COL_T, 3) k_fwd_col(Xform X, Operands S, u6
 }
 
 // --------------------------------------------------- rows + MAC (Eq. 2) --
+//
+// Row modes: ROW_PAIRS transforms both rows of each pair (x_i, a_i) and
+// accumulates their product; ROW_STORE transforms rows of K single operands and
+// stores the spectra (seed preparation); ROW_PREPARED transforms the rows of
+// x_i and multiplies them with stored spectra.  Spectra are stored at the
+// in-place positions of the last forward round.
 
-template <int NS, int ACC, bool LAST>
+enum { ROW_PAIRS = 0, ROW_STORE = 1, ROW_PREPARED = 2 };
+
+template <int NS, int ACC, int MODE, bool LAST>
 __device__ __forceinline__ void row_fwd_round(const Xform &X, const u64 *__restrict__ xrow,
                                               const u64 *__restrict__ arow, u64 *__restrict__ smx,
-                                              u64 *__restrict__ sma, u32 s0, bool first, u64 (&acc)[ACC]) {
+                                              u64 *__restrict__ sma, u64 *__restrict__ spec, u32 s0, bool first,
+                                              u64 (&acc)[ACC]) {
     const u32 l = X.logC, sh = l - s0 - NS, stride = 1u << sh, ngroups = X.C >> NS;
 #pragma unroll
     for (int t = 0; t < (ACC >> NS); t++) {
@@ -270,18 +313,23 @@ __device__ __forceinline__ void row_fwd_round(const Xform &X, const u64 *__restr
             for (int m = 0; m < (1 << NS); m++) {
                 const u32 idx = base + m * stride;
                 vx[m] = first ? __ldg(xrow + idx) : smx[pidx(idx)];
-                va[m] = first ? __ldg(arow + idx) : sma[pidx(idx)];
+                if (MODE == ROW_PAIRS) va[m] = first ? __ldg(arow + idx) : sma[pidx(idx)];
             }
             dif_regs<NS, LAST>(vx, s0, lo, stride, X.twC);
-            dif_regs<NS, LAST>(va, s0, lo, stride, X.twC);
+            if (MODE == ROW_PAIRS) dif_regs<NS, LAST>(va, s0, lo, stride, X.twC);
 #pragma unroll
             for (int m = 0; m < (1 << NS); m++) {
                 const u32 idx = base + m * stride;
                 if (LAST) {
-                    acc[t * (1 << NS) + m] = gd_add(acc[t * (1 << NS) + m], gd_mul(vx[m], va[m]));
+                    if (MODE == ROW_PAIRS)
+                        acc[t * (1 << NS) + m] = gd_add(acc[t * (1 << NS) + m], gd_mul(vx[m], va[m]));
+                    else if (MODE == ROW_PREPARED)
+                        acc[t * (1 << NS) + m] = gd_add(acc[t * (1 << NS) + m], gd_mul(vx[m], __ldg(spec + idx)));
+                    else
+                        spec[idx] = vx[m];
                 } else {
                     smx[pidx(idx)] = vx[m];
-                    sma[pidx(idx)] = va[m];
+                    if (MODE == ROW_PAIRS) sma[pidx(idx)] = va[m];
                 }
             }
         }
@@ -317,10 +365,12 @@ __device__ __forceinline__ void row_inv_round(const Xform &X, u64 *__restrict__ 
     }
 }
 
-
 // One CTA per row; blockDim = C / ACC threads, each owning ACC accumulators.
-template <int ACC>
-__global__ void __launch_bounds__(512, ACC == 8 ? 2 : 1) k_row_mac(Xform X, const u64 *__restrict__ Y, u64 *__restrict__ S) {
+// Y holds the column-pass output; Spec the stored spectra (ROW_STORE writes
+// them, ROW_PREPARED reads them); S receives the inverse-row output.
+template <int ACC, int MODE>
+__global__ void __launch_bounds__(512, ACC == 8 ? 2 : 1)
+    k_row_mac(Xform X, const u64 *__restrict__ Y, u64 *__restrict__ Spec, u64 *__restrict__ S) {
     extern __shared__ u64 sm[];
     const u32 C = X.C, row = blockIdx.x, l = X.logC;
     const u64 N = X.N;
@@ -328,9 +378,13 @@ __global__ void __launch_bounds__(512, ACC == 8 ? 2 : 1) k_row_mac(Xform X, cons
     if (l == 0) {
         if (threadIdx.x == 0) {
             u64 s = 0;
-            for (u32 i = 0; i < X.K; i++)
-                s = gd_add(s, gd_mul(Y[(u64)i * N + row], Y[(u64)(X.K + i) * N + row]));
-            S[row] = s;
+            for (u32 i = 0; i < X.K; i++) {
+                const u64 x = Y[(u64)i * N + row];
+                if (MODE == ROW_PAIRS) s = gd_add(s, gd_mul(x, Y[(u64)(X.K + i) * N + row]));
+                if (MODE == ROW_PREPARED) s = gd_add(s, gd_mul(x, Spec[(u64)i * N + row]));
+                if (MODE == ROW_STORE) Spec[(u64)i * N + row] = x;
+            }
+            if (MODE != ROW_STORE) S[row] = s;
         }
         return;
     }
@@ -341,21 +395,23 @@ __global__ void __launch_bounds__(512, ACC == 8 ? 2 : 1) k_row_mac(Xform X, cons
     for (u32 i = 0; i < X.K; i++) {
         const u64 *xrow = Y + (u64)i * N + (u64)row * C;
         const u64 *arow = Y + (u64)(X.K + i) * N + (u64)row * C;
+        u64 *spec = Spec + (u64)i * N + (u64)row * C;
         for (u32 rd = 0; rd < nr; rd++) {
             const u32 s0 = 3 * rd, ns = min(3u, l - s0);
             const bool first = rd == 0, last = rd == nr - 1;
-#define PA_ROW_FWD(NSV)                                                           \
-    do {                                                                          \
-        if (last)                                                                 \
-            row_fwd_round<NSV, ACC, true>(X, xrow, arow, smx, sma, s0, first, acc);  \
-        else                                                                      \
-            row_fwd_round<NSV, ACC, false>(X, xrow, arow, smx, sma, s0, first, acc); \
+#define PA_ROW_FWD(NSV)                                                                       \
+    do {                                                                                      \
+        if (last)                                                                             \
+            row_fwd_round<NSV, ACC, MODE, true>(X, xrow, arow, smx, sma, spec, s0, first, acc);  \
+        else                                                                                  \
+            row_fwd_round<NSV, ACC, MODE, false>(X, xrow, arow, smx, sma, spec, s0, first, acc); \
     } while (0)
             PA_DISPATCH_NS(ns, PA_ROW_FWD);
 #undef PA_ROW_FWD
             __syncthreads();
         }
     }
+    if (MODE == ROW_STORE) return;
     u64 *Srow = S + (u64)row * C;
     for (int rd = (int)nr - 1; rd >= 0; rd--) {
         const u32 s0 = 3 * rd, ns = min(3u, l - s0);
@@ -751,10 +807,18 @@ int prepare_kernels() {
     static bool done = false;
     if (done) return 0;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_fwd_col, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024))) return e;
+    if ((e = cudaFuncSetAttribute(k_fwd_col<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024))) return e;
+    if ((e = cudaFuncSetAttribute(k_fwd_col<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024))) return e;
     if ((e = cudaFuncSetAttribute(k_inv_col, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024))) return e;
-    if ((e = cudaFuncSetAttribute(k_row_mac<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024))) return e;
-    if ((e = cudaFuncSetAttribute(k_row_mac<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024))) return e;
+#define PA_ROW_ATTR(A, M) \
+    if ((e = cudaFuncSetAttribute(k_row_mac<A, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024))) return e;
+    PA_ROW_ATTR(8, ROW_PAIRS)
+    PA_ROW_ATTR(8, ROW_STORE)
+    PA_ROW_ATTR(8, ROW_PREPARED)
+    PA_ROW_ATTR(16, ROW_PAIRS)
+    PA_ROW_ATTR(16, ROW_STORE)
+    PA_ROW_ATTR(16, ROW_PREPARED)
+#undef PA_ROW_ATTR
     done = true;
     return 0;
 }
@@ -763,20 +827,43 @@ int launch_fwd_col(const Xform &X, const Operands &S, int num_pairs, u64 *Y, voi
     if (int e = prepare_kernels()) return e;
     dim3 grid(X.C / X.tc, num_pairs);
     const size_t smem = 2 * col_smem(X);
-    TRACED("fwd_col", X.stage, stream, (k_fwd_col<<<grid, PA_COL_T, smem, (cudaStream_t)stream>>>(X, S, Y)));
+    TRACED("fwd_col", X.stage, stream, (k_fwd_col<true><<<grid, PA_COL_T, smem, (cudaStream_t)stream>>>(X, S, Y)));
+    return (int)cudaGetLastError();
+}
+
+int launch_fwd_col_single(const Xform &X, const Operands &S, int num_operands, u64 *Y, void *stream) {
+    if (int e = prepare_kernels()) return e;
+    dim3 grid(X.C / X.tc, num_operands);
+    TRACED("fwd_col1", X.stage, stream,
+           (k_fwd_col<false><<<grid, PA_COL_T, col_smem(X), (cudaStream_t)stream>>>(X, S, Y)));
+    return (int)cudaGetLastError();
+}
+
+template <int MODE>
+static int launch_rows(const char *name, const Xform &X, const u64 *Y, u64 *Spec, u64 *S, void *stream) {
+    if (int e = prepare_kernels()) return e;
+    if (X.C > 4096) {
+        TRACED(name, X.stage, stream,
+               (k_row_mac<16, MODE><<<X.R, X.C / 16, row_smem(X), (cudaStream_t)stream>>>(X, Y, Spec, S)));
+    } else {
+        u32 threads = X.C / 8;
+        if (threads < 32) threads = 32;
+        TRACED(name, X.stage, stream,
+               (k_row_mac<8, MODE><<<X.R, threads, row_smem(X), (cudaStream_t)stream>>>(X, Y, Spec, S)));
+    }
     return (int)cudaGetLastError();
 }
 
 int launch_row_mac(const Xform &X, const u64 *Y, u64 *S, void *stream) {
-    if (int e = prepare_kernels()) return e;
-    if (X.C > 4096) {
-        TRACED("row_mac", X.stage, stream, (k_row_mac<16><<<X.R, X.C / 16, row_smem(X), (cudaStream_t)stream>>>(X, Y, S)));
-    } else {
-        u32 threads = X.C / 8;
-        if (threads < 32) threads = 32;
-        TRACED("row_mac", X.stage, stream, (k_row_mac<8><<<X.R, threads, row_smem(X), (cudaStream_t)stream>>>(X, Y, S)));
-    }
-    return (int)cudaGetLastError();
+    return launch_rows<ROW_PAIRS>("row_mac", X, Y, nullptr, S, stream);
+}
+
+int launch_row_store(const Xform &X, const u64 *Y, u64 *Spec, void *stream) {
+    return launch_rows<ROW_STORE>("row_store", X, Y, Spec, nullptr, stream);
+}
+
+int launch_row_prepared(const Xform &X, const u64 *Y, const u64 *Spec, u64 *S, void *stream) {
+    return launch_rows<ROW_PREPARED>("row_prep", X, Y, const_cast<u64 *>(Spec), S, stream);
 }
 
 int launch_inv_col(const Xform &X, const u64 *S, u64 *Z, const u64 *add_src, u64 add_base, u64 add_len,
