@@ -107,6 +107,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_max(x: float, dist, device) -> float:
+    """Slowest rank's value (every rank calls it; no-op on one process)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mbps(n_bits: int, steps: int, world: int, total_ms: float) -> float:
+    """Whole-job throughput: every rank hashed `steps` blocks of n_bits."""
+    return world * n_bits * steps / (total_ms / 1e3) / 1e6
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -195,11 +210,8 @@ def run_gb300(args):
     _lib.trace_enable(False)
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
+    total_ms = reduce_max(sum(step_ms), dist, "cuda")
     if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     torch.cuda.synchronize()
     status = int(dstat.item())
@@ -240,14 +252,10 @@ def run_gb300(args):
         rc = L.pa_hash_host(plan.handle, hkey.data_ptr(), hseed.data_ptr(), hout.data_ptr(), sp)
         assert rc >= 0, rc
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = reduce_max((time.perf_counter() - t0) / e2e_steps, dist, "cuda")
     same = bool(np.array_equal(hout.numpy(), dout.cpu().numpy()))
 
-    value = ws * n * args.steps / (total_ms / 1e3) / 1e6
+    value = job_mbps(n, args.steps, ws, total_ms)
     peaks, peak_kind = measured_peaks()
     roof = roofline(info, trace, args.steps, peaks, peak_kind, step_ms)
 
@@ -285,6 +293,10 @@ def run_gb300(args):
     if rank == 0 and ws == 1 and not args.no_extras:
         line["cpu_baseline"] = cpu_baseline(plan.gamma, r)
     if not args.no_extras and rank == 0:
+        try:
+            line["sweep"] = run_sweep()
+        except Exception as e:  # noqa: BLE001
+            line["sweep"] = {"error": repr(e)}
         try:
             line["batched"] = run_batched()
         except Exception as e:  # noqa: BLE001
@@ -350,6 +362,52 @@ def cpu_baseline(gamma: int, r: int):
     return {"value": round(n / dt / 1e6, 3), "unit": "Mbps", "cores": 1, "kind": "oracle",
             "sample": f"one block n'=3*gamma={n} bits at gamma={g}, r={r} (4 of 10 gamma-bit products "
                       f"of the n=2.6e8 block), {dt:.1f} s", "status": rc}
+
+
+def run_sweep(steps: int = 5):
+    """Block-size sweep (config 3): n in {1e7, 1e8, 2.6e8, 1e9}, r = 0.1 n,
+    seeds 3..6; plain method, L2 flushed between steps; Mbps and the dominant
+    kernel's roofline fractions per size."""
+    import numpy as np
+    import torch
+
+    from paper_2105_13678_gb300 import _lib, synthetic
+    peaks, peak_kind = measured_peaks()
+    out = []
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for n, seed_id in ((10_000_000, 3), (100_000_000, 4), (260_000_000, 5), (1_000_000_000, 6)):
+        r = int(math.ceil(0.1 * n))
+        plan = _lib.Plan(n, r)
+        key, seed = synthetic.block_inputs(seed_id, n, (plan.k + 2) * plan.gamma)
+        dk = torch.from_numpy(key.view(np.int64)).cuda()
+        ds = torch.from_numpy(seed.view(np.int64)).cuda()
+        do = torch.zeros(plan.info.out_words, dtype=torch.int64, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        for _ in range(2):
+            _lib.pa_hash(plan, dk.data_ptr(), ds.data_ptr(), do.data_ptr(), st.data_ptr(), stream.cuda_stream)
+        torch.cuda.synchronize()
+        _lib.trace_enable(True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1 in evs:
+            flush.zero_()
+            e0.record(stream)
+            _lib.pa_hash(plan, dk.data_ptr(), ds.data_ptr(), do.data_ptr(), st.data_ptr(), stream.cuda_stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        trace = _lib.trace_collect()
+        _lib.trace_enable(False)
+        step_ms = [a.elapsed_time(b_) for a, b_ in evs]
+        ms = sum(step_ms) / steps
+        roof = roofline(plan.info, trace, steps, peaks, peak_kind, step_ms)
+        out.append({"n_bits": n, "r_bits": r, "gamma": plan.gamma, "k": plan.k, "mmh_len": plan.info.mmh_len,
+                    "mh_len": plan.info.mh_len, "ms_per_block": round(ms, 4), "mbps": round(n / ms / 1e3, 1),
+                    "dominant_kernel": roof["kernel"] if roof else None,
+                    "frac_mul": roof["mul"]["frac"] if roof else None,
+                    "frac_hbm": roof["hbm"]["frac"] if roof else None, "status": int(st.item())})
+        plan.close()
+        del dk, ds, do
+    return out
 
 
 def run_batched(reps: int = 5):

@@ -129,9 +129,12 @@ def test_repeat_calls_identical():
     assert all(np.array_equal(outs[0], o) for o in outs[1:])
 
 
-@pytest.mark.parametrize("n,r,seed_id", [(10_000_000, 1_000_000, 3), (100_000_000, 10_000_000, 4)])
+@pytest.mark.parametrize("n,r,seed_id", [(10_000_000, 1_000_000, 3), (100_000_000, 10_000_000, 4),
+                                         (260_000_000, 26_000_000, 5), (1_000_000_000, 100_000_000, 6)])
 def test_sweep_sizes(n, r, seed_id):
-    """Block-size sweep points n = 1e7 and 1e8 (r = 0.1 n, seeds 3, 4)."""
+    """Block-size sweep n = 1e7, 1e8, 2.6e8, 1e9 (r = 0.1 n, seeds 3..6); the
+    1e9 block (gamma = 136279841, the largest tabulated exponent) needs the
+    oracle for several minutes."""
     _check(n, r, seed_id, parallel=True)
 
 
