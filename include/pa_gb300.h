@@ -84,10 +84,21 @@ int pa_plan_destroy(pa_plan_t *plan);
 int pa_hash(pa_plan_t *plan, const uint64_t *key, const uint64_t *seed, uint64_t *out,
             int *status, void *stream);
 
-/* Algorithm 1 on HOST buffers: copies key and seed in, runs, copies out and
- * synchronises `stream`.  Returns PA_OK, PA_RELOAD or an error. */
+/* Algorithm 1 on HOST buffers: copies key and seed in (overlapped with the
+ * column transforms), runs, copies out and synchronises `stream`.  Returns
+ * PA_OK, PA_RELOAD or an error. */
 int pa_hash_host(pa_plan_t *plan, const uint64_t *key, const uint64_t *seed, uint64_t *out,
                  void *stream);
+
+/* Asynchronous form of pa_hash_host for streams of blocks: enqueues the copies
+ * (on a plan-owned copy stream), the hash and the copy-out on `stream` and
+ * returns.  `status` is a HOST int (pinned memory recommended, may be NULL)
+ * written with PA_OK / PA_RELOAD when the work completes.  Two staging slots
+ * alternate, so the input copies of one call overlap the transforms of the
+ * previous call; key, seed, out and status must stay valid until `stream` has
+ * passed the call.  Pinned host buffers are needed for the overlap. */
+int pa_hash_host_async(pa_plan_t *plan, const uint64_t *key, const uint64_t *seed, uint64_t *out, int *status,
+                       void *stream);
 
 /* The MMH value y = sum a_i x_i mod p of Eq. 2 (ceil(gamma/64) device words,
  * canonical in [0, p)), for checking the intermediate.  Asynchronous. */

@@ -66,6 +66,7 @@ SIGNATURES = {
     "pa_plan_destroy": (ctypes.c_int, [_vp]),
     "pa_hash": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "pa_hash_host": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "pa_hash_host_async": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "pa_debug_mmh": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "pa_seed_prepare": (ctypes.c_int, [_vp, _vp, _vp]),
     "pa_hash_prepared": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),

@@ -138,11 +138,26 @@ struct pa_plan_s {
     // seed reuse (pa_seed_prepare): stored spectra of a_1..a_k and b, seed copy
     u64 *spec_a = nullptr, *spec_b = nullptr, *seed_copy = nullptr;
     bool prepared = false;
-    // device staging for pa_hash_host: key | seed | out | status
-    u64 *dkey = nullptr, *dseed = nullptr, *dout = nullptr;
-    int *dstatus = nullptr;
+    // host-buffer entry points: two staging slots (key | seed | out | status),
+    // a copy stream, per-group "landed" events and per-slot "free" events
+    struct Staging {
+        u64 *dkey = nullptr, *dseed = nullptr, *dout = nullptr;
+        int *dstatus = nullptr;
+        int *hstatus = nullptr;  // pinned
+        std::vector<cudaEvent_t> ready;
+        cudaEvent_t free_ev = nullptr;
+        bool used = false;
+    } stage[2];
+    int next_stage = 0;
+    cudaStream_t copy_stream = nullptr;
     std::vector<void *> ws_allocs;
     ~pa_plan_s() {
+        for (auto &st : stage) {
+            for (cudaEvent_t e : st.ready) cudaEventDestroy(e);
+            if (st.free_ev) cudaEventDestroy(st.free_ev);
+            if (st.hstatus) cudaFreeHost(st.hstatus);
+        }
+        if (copy_stream) cudaStreamDestroy(copy_stream);
         for (void *p : ws_allocs) cudaFree(p);
     }
     void *alloc(size_t bytes, int *err) {
@@ -322,6 +337,7 @@ static int enqueue_mmh(pa_plan_t *pl, const u64 *key, const u64 *seed, u64 *y, b
     int e;
     if ((e = cudaMemsetAsync(pl->flags, 0, pl->flags_bytes, s))) return e;
     Operands ops;
+    ops.pair0 = 0;
     ops.key = key;
     ops.seed = seed;
     ops.y = nullptr;
@@ -355,6 +371,7 @@ static int enqueue_mmh(pa_plan_t *pl, const u64 *key, const u64 *seed, u64 *y, b
 static int enqueue_mh(pa_plan_t *pl, const u64 *seed, u64 *out, int *status, void *stream) {
     int e;
     Operands ops;
+    ops.pair0 = 0;
     ops.key = nullptr;
     ops.seed = seed;
     ops.y = pl->ybuf;
@@ -415,29 +432,94 @@ int pa_debug_mmh(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint6
     return cuda_rc(e);
 }
 
-int pa_hash_host(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint64_t *out, void *stream) {
+// Host buffers.  Key and seed are copied on the plan's copy stream in a few
+// groups of slices; the column pass of a group starts as soon as its slices
+// have landed.  Two staging slots alternate, so the copies of one call overlap
+// the transforms of the previous call on the same stream.
+// Pairs per column launch (about a third of the k pairs) and the number of
+// launches (every group non-empty).
+static uint64_t host_group_size(uint64_t k) { return (k + 2) / 3; }
+static int host_groups(uint64_t k) { return (int)((k + host_group_size(k) - 1) / host_group_size(k)); }
+
+int pa_hash_host_async(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint64_t *out, int *status,
+                       void *stream) {
     if (!pl || !key || !seed || !out) return PA_ERR_INVALID;
-    const size_t kw = (pl->n + 63) / 64, sw = ((pl->k + 2) * pl->gamma + 63) / 64, ow = (pl->r + 63) / 64;
+    const uint64_t kw = (pl->n + 63) / 64, sw = ((pl->k + 2) * pl->gamma + 63) / 64, ow = (pl->r + 63) / 64;
+    const uint64_t g = pl->gamma, k = pl->k;
+    const int ng = host_groups(k);
+    const uint64_t per = host_group_size(k);
     cudaStream_t s = (cudaStream_t)stream;
-    if (!pl->dkey) {
+    if (!pl->copy_stream && cudaStreamCreateWithFlags(&pl->copy_stream, cudaStreamNonBlocking)) return PA_ERR_CUDA;
+    auto &st = pl->stage[pl->next_stage];
+    pl->next_stage ^= 1;
+    if (!st.dkey) {
         void *d = nullptr;
         if (cudaMalloc(&d, (kw + sw + ow + 1) * 8) != cudaSuccess) return PA_ERR_NOMEM;
         pl->ws_allocs.push_back(d);
-        pl->dkey = (u64 *)d;
-        pl->dseed = pl->dkey + kw;
-        pl->dout = pl->dseed + sw;
-        pl->dstatus = (int *)(pl->dout + ow);
+        st.dkey = (u64 *)d;
+        st.dseed = st.dkey + kw;
+        st.dout = st.dseed + sw;
+        st.dstatus = (int *)(st.dout + ow);
+        if (cudaMallocHost(&st.hstatus, sizeof(int))) return PA_ERR_NOMEM;
+        st.ready.resize(ng + 1, nullptr);
+        for (auto &e : st.ready)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming)) return PA_ERR_CUDA;
+        if (cudaEventCreateWithFlags(&st.free_ev, cudaEventDisableTiming)) return PA_ERR_CUDA;
     }
-    int e;
-    if ((e = cudaMemcpyAsync(pl->dkey, key, kw * 8, cudaMemcpyHostToDevice, s))) return PA_ERR_CUDA;
-    if ((e = cudaMemcpyAsync(pl->dseed, seed, sw * 8, cudaMemcpyHostToDevice, s))) return PA_ERR_CUDA;
-    int rc = pa_hash(pl, (const uint64_t *)pl->dkey, (const uint64_t *)pl->dseed, (uint64_t *)pl->dout, pl->dstatus, stream);
+    int e = 0;
+    // the slot's previous inputs must have been consumed before they are overwritten
+    if (st.used) e = cudaStreamWaitEvent(pl->copy_stream, st.free_ev, 0);
+    auto copy_words = [&](u64 *dst, const uint64_t *src, uint64_t w0, uint64_t w1) {
+        if (w1 > w0 && !e)
+            e = cudaMemcpyAsync(dst + w0, src + w0, (w1 - w0) * 8, cudaMemcpyHostToDevice, pl->copy_stream);
+    };
+    for (int q = 0; q < ng && !e; q++) {
+        const uint64_t i0 = q * per, i1 = std::min(k, i0 + per);
+        const uint64_t b0 = i0 * g, b1k = std::min(pl->n, i1 * g), b1s = i1 * g;
+        copy_words(st.dkey, key, b0 / 64, std::min(kw, (b1k + 63) / 64));
+        copy_words(st.dseed, seed, b0 / 64, std::min(sw, (b1s + 63) / 64));
+        if (!e) e = cudaEventRecord(st.ready[q], pl->copy_stream);
+    }
+    copy_words(st.dseed, seed, (k * g) / 64, sw);  // b and c
+    if (!e) e = cudaEventRecord(st.ready[ng], pl->copy_stream);
+    if (!e) e = cudaMemsetAsync(pl->flags, 0, pl->flags_bytes, s);
+    Operands ops;
+    ops.pair0 = 0;
+    ops.key = st.dkey;
+    ops.seed = st.dseed;
+    ops.y = nullptr;
+    ops.y_zero = nullptr;
+    ops.reload = pl->flags;
+    ops.n = pl->n;
+    ops.gamma = pl->gamma;
+    ops.k = pl->k;
+    ops.mode = 0;
+    for (int q = 0; q < ng && !e; q++) {
+        const uint64_t i0 = q * per, i1 = std::min(k, i0 + per);
+        e = cudaStreamWaitEvent(s, st.ready[q], 0);
+        ops.pair0 = (u32)i0;
+        if (!e) e = launch_fwd_col(pl->mmh, ops, (int)(i1 - i0), pl->Y, stream);
+    }
+    if (!e) e = launch_row_mac(pl->mmh, pl->Y, pl->S, stream);
+    if (!e) e = launch_inv_col(pl->mmh, pl->S, pl->Y, nullptr, 0, 0, stream);
+    if (!e) e = launch_carry(pl->mmh, carry_dev(pl, pl->mmh, pl->flags + 1), pl->Y, pl->ybuf, (g + 63) / 64, stream);
+    if (!e) e = cudaStreamWaitEvent(s, st.ready[ng], 0);
+    if (!e) e = enqueue_mh(pl, st.dseed, st.dout, st.dstatus, stream);
+    if (!e) e = cudaEventRecord(st.free_ev, s);
+    if (!e) e = cudaMemcpyAsync(out, st.dout, ow * 8, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(status ? status : st.hstatus, st.dstatus, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e) return PA_ERR_CUDA;
+    st.used = true;
+    return PA_OK;
+}
+
+int pa_hash_host(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint64_t *out, void *stream) {
+    if (!pl) return PA_ERR_INVALID;
+    auto &st = pl->stage[pl->next_stage];
+    int rc = pa_hash_host_async(pl, key, seed, out, nullptr, stream);
     if (rc) return rc;
-    if ((e = cudaMemcpyAsync(out, pl->dout, ow * 8, cudaMemcpyDeviceToHost, s))) return PA_ERR_CUDA;
-    int st = 0;
-    if ((e = cudaMemcpyAsync(&st, pl->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s))) return PA_ERR_CUDA;
-    if ((e = cudaStreamSynchronize(s))) return PA_ERR_CUDA;
-    return st ? PA_RELOAD : PA_OK;
+    if (cudaStreamSynchronize((cudaStream_t)stream)) return PA_ERR_CUDA;
+    return *st.hstatus ? PA_RELOAD : PA_OK;
 }
 
 // Seed reuse: transform a_1..a_k (Eq. 2) and b (Eq. 4) once and keep their
@@ -457,6 +539,7 @@ int pa_seed_prepare(pa_plan_t *pl, const uint64_t *seed, void *stream) {
     pl->prepared = false;
     int e = cudaMemcpyAsync(pl->seed_copy, seed, sw * 8, cudaMemcpyDeviceToDevice, s);
     Operands ops;
+    ops.pair0 = 0;
     ops.key = nullptr;
     ops.seed = pl->seed_copy;
     ops.y = nullptr;
@@ -481,6 +564,7 @@ int pa_hash_prepared(pa_plan_t *pl, const uint64_t *key, uint64_t *out, int *sta
     cudaStream_t s = (cudaStream_t)stream;
     int e = cudaMemsetAsync(pl->flags, 0, pl->flags_bytes, s);
     Operands ops;
+    ops.pair0 = 0;
     ops.key = (const u64 *)key;
     ops.seed = pl->seed_copy;
     ops.y = pl->ybuf;

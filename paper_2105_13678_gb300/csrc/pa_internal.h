@@ -114,6 +114,7 @@ struct Operands {
     int *reload;        // reload flag + per-slice all-ones counters (Algorithm 1)
     u64 n, gamma, k;
     int mode;           // pairs: 0 MMH (x_i, a_i), 1 MH (y, b); single: 2 a_i, 3 x_i, 4 b, 5 y
+    u32 pair0;          // first pair / operand handled by the launch (blockIdx.y offset)
 };
 
 // Carry resolution of N digits (value mod 2^G - 1, end-around carry).

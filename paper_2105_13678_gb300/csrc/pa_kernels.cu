@@ -237,7 +237,7 @@ __device__ __forceinline__ void fwd_col_round(const Xform &X, const OpDesc &dx, 
 template <bool PAIR>
 __global__ void __launch_bounds__(PA_COL_T, 3) k_fwd_col(Xform X, Operands S, u64 *__restrict__ Y) {
     extern __shared__ u64 sm[];
-    const u32 tc = X.tc, c0 = blockIdx.x * tc, i = blockIdx.y;
+    const u32 tc = X.tc, c0 = blockIdx.x * tc, i = blockIdx.y + S.pair0;
     OpDesc dx, da;
     if (PAIR)
         pair_desc(S, i, dx, da);

@@ -211,6 +211,7 @@ extern "C" int pa_hash_noalloc(uint64_t n_bits, uint64_t r_bits, const pa_params
     if (!e) e = cudaMemsetAsync(flags, 0, flag_bytes, s);
 
     Operands ops;
+    ops.pair0 = 0;
     ops.key = (const u64 *)key;
     ops.seed = (const u64 *)seed;
     ops.y = ybuf;

@@ -111,14 +111,23 @@ def test_bits_past_n_ignored():
     assert st == st2 == 0 and np.array_equal(a, b)
 
 
-def test_host_entry_point_matches_device():
+@pytest.mark.parametrize("n,r,gamma", [(1 << 20, 104858, 0), (7 * 4423 + 5, 300, 4423), (3_000_001, 290_000, 0),
+                                       (4 * 4423, 100, 4423)])
+def test_host_entry_point_matches_device(n, r, gamma):
+    """pa_hash_host (pipelined host-to-device copies) equals pa_hash; the last
+    case plants an all-ones slice, so both must report a reload."""
     from paper_2105_13678_gb300 import _lib
-    n, r = 1 << 20, 104858
-    plan = _plan(n, r)
+    plan = _plan(n, r, gamma)
     key, hseed = synthetic.block_inputs(1, n, (plan.k + 2) * plan.gamma)
-    st, out = _lib.pa_hash_host(plan, key, hseed)
-    st2, out2, _, _ = gpu_hash(plan, key, hseed)
-    assert st == st2 == 0 and np.array_equal(out, out2)
+    if n == 4 * 4423:
+        kv = oracle.words_to_int(key) | (((1 << 4423) - 1) << 4423)
+        key = oracle.int_to_words(kv, key.size)
+    for _ in range(2):
+        st, out = _lib.pa_hash_host(plan, key, hseed)
+        st2, out2, _, _ = gpu_hash(plan, key, hseed)
+        assert st == st2 and np.array_equal(out, out2)
+    rc, ref, _ = oracle.pa_hash(key, n, hseed, r, plan.gamma, plan.k)
+    assert st == rc and np.array_equal(out, ref)
 
 
 def test_repeat_calls_identical():
@@ -152,3 +161,29 @@ def test_paper_points_cv_dv():
         r = int(np.floor(ratio * n))
         p = _check(n, r, 11, parallel=True)
         assert p.k * p.gamma == n
+
+
+def test_host_async_stream_of_blocks():
+    """pa_hash_host_async: several blocks in flight on one stream (staging slots
+    alternate, copies overlap the previous block); every output equals pa_hash."""
+    import torch
+    from paper_2105_13678_gb300 import _lib
+    n, r = 2_000_003, 200_000
+    plan = _plan(n, r)
+    keys, seeds, outs = [], [], []
+    for i in range(5):
+        key, seed = synthetic.block_inputs(300 + i, n, (plan.k + 2) * plan.gamma)
+        keys.append(torch.from_numpy(key.view(np.int64)).pin_memory())
+        seeds.append(torch.from_numpy(seed.view(np.int64)).pin_memory())
+        outs.append(torch.zeros(plan.info.out_words, dtype=torch.int64).pin_memory())
+    stat = torch.full((5,), -9, dtype=torch.int32).pin_memory()
+    sp = torch.cuda.current_stream().cuda_stream
+    for i in range(5):
+        _lib.check(_lib.lib().pa_hash_host_async(plan.handle, keys[i].data_ptr(), seeds[i].data_ptr(),
+                                                 outs[i].data_ptr(), stat.data_ptr() + 4 * i, sp), "async")
+    torch.cuda.synchronize()
+    assert (stat.numpy() == 0).all()
+    for i in range(5):
+        st, ref, _, _ = gpu_hash(plan, keys[i].numpy().view(np.uint64), seeds[i].numpy().view(np.uint64))
+        assert st == 0 and np.array_equal(outs[i].numpy().view(np.uint64), ref)
+    plan.close()
