@@ -53,8 +53,14 @@ typedef struct pa_params {
     uint32_t gamma;        /* 0: smallest Mersenne exponent >= r + gamma_margin;
                               otherwise a Mersenne exponent > r to use as is   */
     uint32_t gamma_margin; /* default 128: gamma - r >= margin keeps the
-                              2^(r - gamma) term of the Sec. 3.2 bounds tiny   */
-    uint32_t reserved[6];  /* must be zero */
+                              2^(r - gamma) term of the Sec. 3.2 bounds tiny;
+                              with params != NULL, 0 means gamma > r strictly */
+    uint32_t tune;         /* 1: time the candidate four-step splits and column
+                              tiles of each transform shape on this plan's
+                              workspace at pa_plan time and keep the fastest
+                              (cached per process); 0: default geometry.
+                              The output bits do not depend on it.           */
+    uint32_t reserved[5];  /* must be zero */
 } pa_params;
 
 typedef struct pa_plan_info {
@@ -200,6 +206,9 @@ int pa_trace_collect(pa_trace_entry *out, int max_entries, int *count);
 int pa_plan_estimate_bytes(uint64_t n_bits, uint64_t r_bits, const pa_params *params, uint64_t *bytes);
 int pa_field_constants(uint32_t log_n, uint64_t *omega, uint64_t *theta);
 int pa_transform_len(uint64_t G, uint64_t K, uint32_t *log_n);
+/* Four-step geometry of a plan's transform (stage 0: Eq. 2, stage 1: Eq. 4):
+ * N = 2^log_r x 2^log_c, column passes work on tiles of tile_cols columns. */
+int pa_plan_geometry(const pa_plan_t *plan, int stage, uint32_t *log_r, uint32_t *log_c, uint32_t *tile_cols);
 /* Device check of the F_q arithmetic used inside the transforms: for i < n,
  * out[3i], out[3i+1], out[3i+2] = (a[i] + b[i], a[i] - b[i], a[i] * b[i]) mod q,
  * canonical; a, b, out are device arrays (any 64-bit inputs).  Asynchronous. */

@@ -32,8 +32,8 @@ _vp = ctypes.c_void_p
 
 
 class pa_params(ctypes.Structure):
-    _fields_ = [("gamma", ctypes.c_uint32), ("gamma_margin", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 6)]
+    _fields_ = [("gamma", ctypes.c_uint32), ("gamma_margin", ctypes.c_uint32), ("tune", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 5)]
 
 
 class pa_plan_info(ctypes.Structure):
@@ -88,6 +88,8 @@ SIGNATURES = {
     "pa_field_constants": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "pa_transform_len": (ctypes.c_int, [_u64, _u64, ctypes.POINTER(ctypes.c_uint32)]),
     "pa_selftest_field": (ctypes.c_int, [_vp, _vp, _vp, _u64, _vp]),
+    "pa_plan_geometry": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
+                                        ctypes.POINTER(ctypes.c_uint32)]),
 }
 
 _lib = None
@@ -122,25 +124,33 @@ def check(code: int, what: str) -> int:
     return code
 
 
-def params(gamma: int = 0, margin: int = 128) -> pa_params:
+def params(gamma: int = 0, margin: int = 128, tune: bool = False) -> pa_params:
     p = pa_params()
     p.gamma = gamma
     p.gamma_margin = margin
+    p.tune = 1 if tune else 0
     return p
 
 
 class Plan:
     """Owns a ``pa_plan_t``: step 0 of Algorithm 1 plus the device workspace."""
 
-    def __init__(self, n_bits: int, r_bits: int, gamma: int = 0, margin: int = 128):
+    def __init__(self, n_bits: int, r_bits: int, gamma: int = 0, margin: int = 128, tune: bool = False):
         h = _vp()
-        p = params(gamma, margin)
+        p = params(gamma, margin, tune)
         check(lib().pa_plan(n_bits, r_bits, ctypes.byref(p), ctypes.byref(h)), "pa_plan")
         self.handle = h
         info = pa_plan_info()
         check(lib().pa_plan_info_get(h, ctypes.byref(info)), "pa_plan_info_get")
         self.info = info
         self.n, self.r, self.gamma, self.k = info.n_bits, info.r_bits, info.gamma, info.k
+
+    def geometry(self, stage: int):
+        """(log2 R, log2 C, column tile width) of the stage's transform."""
+        a, b, c = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        check(lib().pa_plan_geometry(self.handle, stage, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+              "pa_plan_geometry")
+        return int(a.value), int(b.value), int(c.value)
 
     def close(self):
         if self.handle:

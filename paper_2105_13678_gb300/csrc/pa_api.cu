@@ -13,6 +13,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -172,29 +173,52 @@ struct pa_plan_s {
     }
 };
 
-static int build_xform(pa_plan_t *pl, Xform &X, uint64_t G, uint64_t K) {
+// Default four-step split and column tile for a length 2^l transform.
+static void default_geometry(uint32_t l, u32 *logR, u32 *tc) {
+    *logR = std::min(l / 2, PA_MAX_LOGR);
+    u32 t = 8;
+    while (t > 1 && ((uint64_t)1 << *logR) * t > 4096) t >>= 1;
+    while (t > (1u << (l - *logR))) t >>= 1;
+    *tc = t;
+}
+
+// Geometry is valid for the kernels: R <= 2^11, C <= 8192, tile R * tc <= 4096, tc <= C.
+static bool geometry_ok(uint32_t l, u32 logR, u32 tc) {
+    if (logR > PA_MAX_LOGR || logR > l) return false;
+    const u32 logC = l - logR;
+    if (logC > 13) return false;
+    return tc >= 1 && tc <= 8 && (tc & (tc - 1)) == 0 && tc <= (1u << logC) && ((uint64_t)1 << logR) * tc <= 4096;
+}
+
+static int build_xform(pa_plan_t *pl, Xform &X, uint64_t G, uint64_t K, u32 logR_sel = ~0u, u32 tc_sel = 0,
+                       DevTables *sink = nullptr) {
     uint32_t l;
     int rc = choose_len(G, K, &l);
     if (rc) return rc;
+    u32 logR, tc;
+    default_geometry(l, &logR, &tc);
+    if (logR_sel != ~0u) {
+        if (!geometry_ok(l, logR_sel, tc_sel)) return PA_ERR_INVALID;
+        logR = logR_sel;
+        tc = tc_sel;
+    }
+    DevTables &tabs = sink ? *sink : pl->tables;
     X.N = 1ULL << l;
     X.G = G;
     X.K = (u32)K;
     X.logN = l;
-    X.logR = std::min(l / 2, PA_MAX_LOGR);
+    X.logR = logR;
     X.logC = l - X.logR;
     X.R = 1u << X.logR;
     X.C = 1u << X.logC;
     X.hb = (l + 1) / 2;
-    u32 tc = 8;
-    while (tc > 1 && (uint64_t)X.R * tc > 4096) tc >>= 1;
-    while (tc > X.C) tc >>= 1;
     X.tc = tc;
     const u64 w = root_of_unity(l), wi = gl_inv(w);
     const u64 th = root_of_two(l), thi = gl_inv(th);
     const u64 ninv = gl_inv(X.N % GL_Q);
     const u64 wR = gl_pow(w, X.C), wC = gl_pow(w, X.R);
     int err = PA_OK;
-    auto up = [&](const std::vector<u64> &v) { return pl->tables.upload(v, &err); };
+    auto up = [&](const std::vector<u64> &v) { return tabs.upload(v, &err); };
     X.twR = up(powers(wR, X.R / 2));
     X.itwR = up(powers(gl_inv(wR), X.R / 2));
     X.twC = up(powers(wC, X.C / 2));
@@ -223,12 +247,23 @@ static int build_xform(pa_plan_t *pl, Xform &X, uint64_t G, uint64_t K) {
     {
         void *d = nullptr;
         if (cudaMalloc(&d, X.N * sizeof(u64)) != cudaSuccess) return PA_ERR_NOMEM;
-        pl->tables.allocs.push_back(d);
+        tabs.allocs.push_back(d);
         X.coltw = (const u64 *)d;
         if (launch_fill_coltw(X, (u64 *)d, nullptr) || cudaDeviceSynchronize() != cudaSuccess) return PA_ERR_CUDA;
     }
     return err;
 }
+
+// ------------------------------------------------------------ autotuner --
+// For a transform shape (G, K, N) the tuner times every valid four-step split
+// log2 R in {d - 1, d, d + 1} (d = the default) and column tile width in
+// {2, 4, 8} on the plan's own workspace (forward column pass, row pass with
+// the multiply-accumulate, inverse column pass; one warm-up, best of three)
+// and keeps the fastest.  Results are cached per process.
+static std::mutex g_tune_mu;
+static std::map<std::tuple<uint64_t, uint64_t, uint32_t>, std::pair<u32, u32>> g_tune_cache;
+
+static int tune_geometry(pa_plan_t *pl, int stage, uint64_t G, uint64_t K, uint32_t l, u32 *logR_out, u32 *tc_out);
 
 // Device bytes of a plan's workspace (shared by pa_plan and the server's admission).
 struct WsSizes {
@@ -274,15 +309,12 @@ int pa_plan(uint64_t n_bits, uint64_t r_bits, const pa_params *params, pa_plan_t
         delete pl;
         return PA_ERR_UNSUPPORTED;
     }
-    rc = build_xform(pl, pl->mmh, gamma, pl->k);
-    if (!rc) rc = build_xform(pl, pl->mh, 2ULL * gamma, 1);
-    pl->mmh.stage = 0;
-    pl->mh.stage = 1;
-    if (rc) {
+    uint32_t l1, l2;
+    if ((rc = choose_len(gamma, pl->k, &l1)) || (rc = choose_len(2ULL * gamma, 1, &l2))) {
         delete pl;
         return rc;
     }
-    const WsSizes z = ws_sizes(gamma, pl->k, pl->mmh.N, pl->mh.N);
+    const WsSizes z = ws_sizes(gamma, pl->k, 1ULL << l1, 1ULL << l2);
     int err = PA_OK;
     pl->Y = (u64 *)pl->alloc(z.Y, &err);
     pl->S = (u64 *)pl->alloc(z.S, &err);
@@ -297,6 +329,19 @@ int pa_plan(uint64_t n_bits, uint64_t r_bits, const pa_params *params, pa_plan_t
     if (err) {
         delete pl;
         return err;
+    }
+    const bool tune = params && params->tune;
+    for (int stage = 0; stage < 2 && !rc; stage++) {
+        Xform &X = stage ? pl->mh : pl->mmh;
+        const uint64_t G = stage ? 2ULL * gamma : gamma, K = stage ? 1 : pl->k;
+        u32 logR = ~0u, tc = 0;
+        if (tune) rc = tune_geometry(pl, stage, G, K, stage ? l2 : l1, &logR, &tc);
+        if (!rc) rc = build_xform(pl, X, G, K, logR, tc);
+        X.stage = (u32)stage;
+    }
+    if (rc) {
+        delete pl;
+        return rc;
     }
     *out = pl;
     return PA_OK;
@@ -609,6 +654,85 @@ const char *pa_version(void) { return "pa_gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
 
+static int tune_geometry(pa_plan_t *pl, int stage, uint64_t G, uint64_t K, uint32_t l, u32 *logR_out, u32 *tc_out) {
+    const auto key = std::make_tuple(G, K, l);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            *logR_out = it->second.first;
+            *tc_out = it->second.second;
+            return PA_OK;
+        }
+    }
+    u32 dR, dtc;
+    default_geometry(l, &dR, &dtc);
+    // synthetic operands: a fixed bit pattern as key and seed
+    const uint64_t words = std::max<uint64_t>((pl->n + 63) / 64, ((pl->k + 2) * pl->gamma + 63) / 64) + 2;
+    void *src = nullptr;
+    if (cudaMalloc(&src, words * 8) != cudaSuccess) return PA_ERR_NOMEM;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = PA_OK;
+    if (cudaMemset(src, 0xA5, words * 8) || cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) ||
+        cudaEventCreate(&e0) || cudaEventCreate(&e1) || cudaMemset(pl->flags, 0, pl->flags_bytes))
+        rc = PA_ERR_CUDA;
+    float best = 1e30f;
+    u32 bestR = dR, besttc = dtc;
+    for (int dr = -1; dr <= 1 && !rc; dr++) {
+        if ((int)dR + dr < 0) continue;
+        const u32 logR = (u32)((int)dR + dr);
+        for (u32 tc : {2u, 4u, 8u}) {
+            if (!geometry_ok(l, logR, tc)) continue;
+            DevTables tmp;
+            Xform X;
+            if (build_xform(pl, X, G, K, logR, tc, &tmp)) continue;
+            X.stage = (u32)stage;
+            Operands ops;
+            ops.pair0 = 0;
+            ops.key = (const u64 *)src;
+            ops.seed = (const u64 *)src;
+            ops.y = (const u64 *)src;
+            ops.y_zero = pl->flags + 1;
+            ops.reload = pl->flags;
+            ops.n = pl->n;
+            ops.gamma = pl->gamma;
+            ops.k = pl->k;
+            ops.mode = stage;
+            float t_min = 1e30f;
+            for (int rep = 0; rep < 4 && !rc; rep++) {
+                int e = cudaEventRecord(e0, s);
+                if (!e) e = launch_fwd_col(X, ops, (int)K, pl->Y, s);
+                if (!e) e = launch_row_mac(X, pl->Y, pl->S, s);
+                if (!e) e = launch_inv_col(X, pl->S, pl->Y, nullptr, 0, 0, s);
+                if (!e) e = cudaEventRecord(e1, s);
+                if (!e) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (!e) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e) rc = PA_ERR_CUDA;
+                if (rep > 0) t_min = std::min(t_min, ms);
+            }
+            if (!rc && t_min < best) {
+                best = t_min;
+                bestR = logR;
+                besttc = tc;
+            }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    cudaFree(src);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = std::make_pair(bestR, besttc);
+    }
+    *logR_out = bestR;
+    *tc_out = besttc;
+    return PA_OK;
+}
+
 // Step-0 parameters and transform lengths for (n, r), host arithmetic only.
 int pa::choose_params(uint64_t n_bits, uint64_t r_bits, const pa_params *params, uint32_t *gamma, uint64_t *k,
                       uint32_t *log_mmh, uint32_t *log_mh) {
@@ -646,6 +770,16 @@ int pa_field_constants(uint32_t log_n, uint64_t *omega, uint64_t *theta) {
 int pa_selftest_field(const uint64_t *a, const uint64_t *b, uint64_t *out, uint64_t n, void *stream) {
     if (!a || !b || !out) return PA_ERR_INVALID;
     return launch_selftest_field((const u64 *)a, (const u64 *)b, (u64 *)out, n, stream) ? PA_ERR_CUDA : PA_OK;
+}
+
+// Four-step geometry of a plan's transform (stage 0: Eq. 2, 1: Eq. 4).
+int pa_plan_geometry(const pa_plan_t *pl, int stage, uint32_t *log_r, uint32_t *log_c, uint32_t *tile_cols) {
+    if (!pl || !log_r || !log_c || !tile_cols || stage < 0 || stage > 1) return PA_ERR_INVALID;
+    const Xform &X = stage ? pl->mh : pl->mmh;
+    *log_r = X.logR;
+    *log_c = X.logC;
+    *tile_cols = X.tc;
+    return PA_OK;
 }
 
 // Digit split chosen for a modulus of G bits and K operand pairs.

@@ -164,3 +164,21 @@ def test_serve_poll_and_stats_latency():
     assert st["completed"] == 1 and st["p50_latency_ms"] > 0
     rc, out, _ = oracle.pa_hash(key, n, seed, r, g, k)
     assert np.array_equal(host(o), out)
+
+
+@pytest.mark.parametrize("n,r", [(1 << 20, 104858), (30_000_000, 9_000_000), (5_000_000, 250_000)])
+def test_autotuned_plan_gives_the_same_bits(n, r):
+    """pa_params.tune picks the four-step split and column tile by timing;
+    the output bits must not depend on the choice."""
+    from paper_2105_13678_gb300 import _lib
+    p0 = _lib.Plan(n, r)
+    p1 = _lib.Plan(n, r, tune=True)
+    key, seed = synthetic.block_inputs(55, n, (p0.k + 2) * p0.gamma)
+    s0, o0, y0, _ = gpu_hash(p0, key, seed)
+    s1, o1, y1, _ = gpu_hash(p1, key, seed)
+    assert s0 == s1 == 0 and np.array_equal(o0, o1) and np.array_equal(y0, y1)
+    if n <= (1 << 20):
+        rc, ref, _ = oracle.pa_hash(key, n, seed, r, p0.gamma, p0.k)
+        assert np.array_equal(o1, ref)
+    p0.close()
+    p1.close()
