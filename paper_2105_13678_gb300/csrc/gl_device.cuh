@@ -90,6 +90,27 @@ __device__ __forceinline__ u64 gd_mul(u64 a, u64 b) {
     return mk64(r0, r1);
 }
 
+// d * w (mod q) for a digit d < 2^32 and any w < 2^64: the 96-bit product
+// p2:p1:p0 is p1:p0 + p2 (2^32 - 1) (mod q); one carry adds 2^32 - 1.
+__device__ __forceinline__ u64 gd_mul_small(u32 d, u64 w) {
+    u32 r0, r1;
+    asm("{\n\t"
+        ".reg .u32 p0, p1, p2, t1, m;\n\t"
+        "mul.lo.u32 p0, %2, %3;\n\t"
+        "mul.hi.u32 t1, %2, %3;\n\t"
+        "mad.lo.cc.u32 p1, %2, %4, t1;\n\t"
+        "madc.hi.u32 p2, %2, %4, 0;\n\t"
+        "mad.lo.cc.u32 %0, p2, 0xFFFFFFFF, p0;\n\t"
+        "madc.hi.cc.u32 %1, p2, 0xFFFFFFFF, p1;\n\t"
+        "addc.u32 m, 0, 0;\n\t"
+        "mad.lo.cc.u32 %0, m, 0xFFFFFFFF, %0;\n\t"
+        "addc.u32 %1, %1, 0;\n\t"
+        "}"
+        : "=&r"(r0), "=&r"(r1)
+        : "r"(d), "r"(lo32(w)), "r"(hi32(w)));
+    return mk64(r0, r1);
+}
+
 // Canonical representative in [0, q).
 __device__ __forceinline__ u64 gd_canon(u64 x) { return x >= 0xFFFFFFFF00000001ULL ? x - 0xFFFFFFFF00000001ULL : x; }
 

@@ -119,9 +119,11 @@ struct Operands {
 
 // Carry resolution of N digits (value mod 2^G - 1, end-around carry).
 struct CarryDev {
-    u64 N, G;
+    u64 N, G;             // digit geometry of the transform: s_j = ceil(G j / N)
     u32 logN;
-    u64 nchunks;          // N / PA_CARRY_D
+    int linear;           // 0: ring mod 2^G - 1 over all N digits; 1: digits [0, nchunks * D) only,
+                          //    carry out of the top dropped (the low half of an exact product)
+    u64 nchunks;          // digits / PA_CARRY_D
     u64 *H;               // chunk carry-outs (multi-bit), nchunks
     unsigned char *state; // chunk G/P state, nchunks
     unsigned char *cta_state, *cta_cin;

@@ -38,12 +38,23 @@ __device__ __forceinline__ u64 read_bits(const u64 *__restrict__ src, u64 pos, u
     return v & ((1ULL << nb) - 1);
 }
 
+// nb in [0, 31] bits starting at absolute bit position pos, read as 32-bit
+// words (the second word only when the bits cross into it).
+__device__ __forceinline__ u32 read_bits32(const u64 *__restrict__ src, u64 pos, u32 nb) {
+    const u32 *s32 = reinterpret_cast<const u32 *>(src);
+    const u64 wi = pos >> 5;
+    const u32 sh = (u32)(pos & 31);
+    const u32 lo = __ldg(s32 + wi);
+    const u32 hi = (sh + nb > 32) ? __ldg(s32 + wi + 1) : 0u;
+    return __funnelshift_r(lo, hi, sh) & ((1u << nb) - 1u);
+}
+
 // Radix-2 decimation-in-frequency stages s0 .. s0+NS-1 of a length-L
 // transform on the 2^NS elements base + m*stride held in v (lo = base mod
 // stride).  Stage s pairs (i, i + L/2^(s+1)) with twiddle
 // omega_L^((i mod L/2^(s+1)) * 2^s) (Gentleman-Sande).  When the group holds
 // the final stage (LAST), that stage's twiddles are all 1 and are skipped.
-template <int NS, bool LAST>
+template <int NS, bool LAST, bool HZ = false>
 __device__ __forceinline__ void dif_regs(u64 (&v)[8], u32 s0, u32 lo, u32 stride, const u64 *__restrict__ tw) {
 #pragma unroll
     for (int sg = 0; sg < NS; sg++) {
@@ -52,6 +63,12 @@ __device__ __forceinline__ void dif_regs(u64 (&v)[8], u32 s0, u32 lo, u32 stride
         for (int m = 0; m < (1 << NS); m++) {
             if (m & half) continue;
             const u64 a = v[m], b = v[m + half];
+            if (HZ && sg == 0) {
+                // upper half of the group is zero: (a, 0) -> (a, a w)
+                const u32 e = (lo + (u32)(m & (half - 1)) * stride) << s0;
+                v[m + half] = gd_mul(a, __ldg(tw + e));
+                continue;
+            }
             v[m] = gd_add(a, b);
             if (LAST && sg == NS - 1) {
                 v[m + half] = gd_sub(a, b);
@@ -65,7 +82,7 @@ __device__ __forceinline__ void dif_regs(u64 (&v)[8], u32 s0, u32 lo, u32 stride
 
 // Inverse of dif_regs up to a factor 2 per stage (decimation in time,
 // stages in reverse order, inverse twiddles).
-template <int NS, bool LAST>
+template <int NS, bool LAST, bool HO = false>
 __device__ __forceinline__ void dit_regs(u64 (&v)[8], u32 s0, u32 lo, u32 stride, const u64 *__restrict__ itw) {
 #pragma unroll
     for (int sg = NS - 1; sg >= 0; sg--) {
@@ -80,7 +97,7 @@ __device__ __forceinline__ void dit_regs(u64 (&v)[8], u32 s0, u32 lo, u32 stride
                 b = gd_mul(b, __ldg(itw + e));
             }
             v[m] = gd_add(a, b);
-            v[m + half] = gd_sub(a, b);
+            if (!(HO && sg == 0)) v[m + half] = gd_sub(a, b);  // HO: upper outputs unused
         }
     }
 }
@@ -147,12 +164,12 @@ __device__ __forceinline__ void single_desc(const Operands &S, u32 i, OpDesc &d)
     }
 }
 
-__device__ __forceinline__ u64 op_digit(const OpDesc &d, u64 j, u64 slo, u64 shi, bool &ones) {
+__device__ __forceinline__ u32 op_digit(const OpDesc &d, u64 j, u64 slo, u64 shi, bool &ones) {
     const u64 hi = shi < d.len ? shi : d.len;
-    u64 dig = 0;
-    if (slo < hi) dig = read_bits(d.src, d.base + slo, (u32)(hi - slo));
-    ones = ones && (shi <= d.len) && (dig == ((1ULL << (u32)(shi - slo)) - 1));
-    if (d.force_odd && j == 0) dig |= 1;
+    const u32 nb = slo < hi ? (u32)(hi - slo) : 0u;
+    u32 dig = read_bits32(d.src, d.base + (slo < hi ? slo : 0), nb);
+    ones = ones && (shi <= d.len) && (dig == ((1u << (u32)(shi - slo)) - 1u));
+    if (d.force_odd && j == 0) dig |= 1u;
     if (d.zero) dig = 0;
     return dig;
 }
@@ -160,20 +177,25 @@ __device__ __forceinline__ u64 op_digit(const OpDesc &d, u64 j, u64 slo, u64 shi
 // Digits j = r C + c of both operands of a pair, times the row part of the
 // weight theta^((-G j) mod N) (the column part is applied after the column
 // transform, inside coltw).
+// (-G C r) mod N and (-G c) mod N in 32-bit arithmetic (N divides 2^32).
+__device__ __forceinline__ u32 gcmodn(const Xform &X) { return (u32)((X.G * X.C) & (X.N - 1)); }
+__device__ __forceinline__ u32 alpha_of(const Xform &X, u32 c) { return (0u - (u32)X.G * c) & (u32)(X.N - 1); }
+
 template <bool PAIR>
 __device__ __forceinline__ void weighted_pair(const Xform &X, const OpDesc &dx, const OpDesc &da, u32 r, u32 c,
-                                              u64 alpha_c, u64 &wx, u64 &wa, bool &ones) {
+                                              u32 alpha_c, u32 gcm, u64 &wx, u64 &wa, bool &ones) {
     const u64 j = (u64)r * X.C + c;
-    const u64 slo = digit_start(X.G, j, X.N, X.logN);
-    const u64 shi = digit_start(X.G, j + 1, X.N, X.logN);
-    const u64 gx = op_digit(dx, j, slo, shi, ones);
-    const u64 beta_r = (0ULL - X.G * X.C * (u64)r) & (X.N - 1);
-    const u64 w = __ldg(X.colw + r + (beta_r + alpha_c >= X.N ? X.R : 0));
-    wx = gx ? gd_mul(gx, w) : 0;
+    const u64 gj = X.G * j;
+    const u64 slo = (gj + X.N - 1) >> X.logN;
+    const u64 shi = (gj + X.G + X.N - 1) >> X.logN;
+    const u32 gx = op_digit(dx, j, slo, shi, ones);
+    const u32 beta_r = (0u - gcm * r) & (u32)(X.N - 1);
+    const u64 w = __ldg(X.colw + r + (beta_r + alpha_c >= (u32)X.N ? X.R : 0));
+    wx = gx ? gd_mul_small(gx, w) : 0;
     if (PAIR) {
         bool dummy = true;
-        const u64 ga = op_digit(da, j, slo, shi, dummy);
-        wa = ga ? gd_mul(ga, w) : 0;
+        const u32 ga = op_digit(da, j, slo, shi, dummy);
+        wa = ga ? gd_mul_small(ga, w) : 0;
     }
 }
 
@@ -191,31 +213,35 @@ __device__ __forceinline__ void weighted_pair(const Xform &X, const OpDesc &dx, 
     } while (0)
 
 
-template <int NS, bool PAIR, bool FIRST, bool LAST>
+template <int NS, bool PAIR, bool FIRST, bool LAST, bool HZ = false>
 __device__ __forceinline__ void fwd_col_round(const Xform &X, const OpDesc &dx, const OpDesc &da,
                                               u64 *__restrict__ smx, u64 *__restrict__ sma, u64 *__restrict__ Yx,
                                               u64 *__restrict__ Ya, u32 c0, u32 s0, bool &ones) {
     const u32 l = X.logR, tc = X.tc;
+    const u32 gcm = gcmodn(X);
     const u32 sh = l - s0 - NS, stride = 1u << sh;
     const u32 ntask = (X.R >> NS) * tc;
     const u32 logtc = __ffs(tc) - 1;
     for (u32 task = threadIdx.x; task < ntask; task += blockDim.x) {
         const u32 c = task & (tc - 1), g = task >> logtc;
         const u32 lo = g & (stride - 1), base = ((g >> sh) << (l - s0)) + lo;
-        const u64 alpha_c = (0ULL - X.G * (u64)(c0 + c)) & (X.N - 1);
+        const u32 alpha_c = alpha_of(X, c0 + c);
         u64 vx[8], va[8];
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
             const u32 r = base + m * stride;
-            if (FIRST) {
-                weighted_pair<PAIR>(X, dx, da, r, c0 + c, alpha_c, vx[m], va[m], ones);
+            if (HZ && m >= (1 << (NS - 1))) {  // rows >= R/2: digits j >= N/2 are zero
+                vx[m] = 0;
+                va[m] = 0;
+            } else if (FIRST) {
+                weighted_pair<PAIR>(X, dx, da, r, c0 + c, alpha_c, gcm, vx[m], va[m], ones);
             } else {
                 vx[m] = smx[pidx(r * tc + c)];
                 if (PAIR) va[m] = sma[pidx(r * tc + c)];
             }
         }
-        dif_regs<NS, LAST>(vx, s0, lo, stride, X.twR);
-        if (PAIR) dif_regs<NS, LAST>(va, s0, lo, stride, X.twR);
+        dif_regs<NS, LAST, HZ>(vx, s0, lo, stride, X.twR);
+        if (PAIR) dif_regs<NS, LAST, HZ>(va, s0, lo, stride, X.twR);
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
             const u32 r = base + m * stride;
@@ -250,20 +276,25 @@ __global__ void __launch_bounds__(PA_COL_T, 3) k_fwd_col(Xform X, Operands S, u6
     if (l == 0) {
         for (u32 c = threadIdx.x; c < tc; c += blockDim.x) {
             u64 wx, wa;
-            const u64 alpha_c = (0ULL - X.G * (u64)(c0 + c)) & (X.N - 1);
-            weighted_pair<PAIR>(X, dx, da, 0, c0 + c, alpha_c, wx, wa, ones);
+            weighted_pair<PAIR>(X, dx, da, 0, c0 + c, alpha_of(X, c0 + c), gcmodn(X), wx, wa, ones);
             const u64 t = __ldg(X.coltw + c0 + c);
             Yx[c0 + c] = gd_mul(wx, t);
             if (PAIR) Ya[c0 + c] = gd_mul(wa, t);
         }
     } else {
         const u32 nr = (l + 2) / 3;
+        // Eq. 4 stage: y, b < 2^gamma, so digits j >= N/2 (rows >= R/2) are zero
+        const bool hz = X.stage == 1;
         for (u32 rd = 0; rd < nr; rd++) {
             const u32 s0 = 3 * rd, ns = min(3u, l - s0);
             const bool first = rd == 0, last = rd == nr - 1;
 #define PA_FWD_COL(NSV)                                                                     \
     do {                                                                                    \
-        if (first && last)                                                                  \
+        if (first && hz && NSV == 3 && last)                                                \
+            fwd_col_round<NSV, PAIR, true, true, true>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones); \
+        else if (first && hz && NSV == 3)                                                   \
+            fwd_col_round<NSV, PAIR, true, false, true>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones); \
+        else if (first && last)                                                             \
             fwd_col_round<NSV, PAIR, true, true>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones);   \
         else if (first)                                                                     \
             fwd_col_round<NSV, PAIR, true, false>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones);  \
@@ -431,7 +462,7 @@ __global__ void __launch_bounds__(512, ACC == 8 ? 2 : 1)
 
 // ------------------------------------------------------ inverse columns --
 
-template <int NS, bool LASTSTAGE, bool TOGLOBAL>
+template <int NS, bool LASTSTAGE, bool TOGLOBAL, bool HO = false>
 __device__ __forceinline__ void inv_col_round(const Xform &X, const u64 *__restrict__ Sg, u64 *__restrict__ sm,
                                               u64 *__restrict__ Z, u32 c0, u32 s0,
                                               const u64 *__restrict__ add_src, u64 add_base, u64 add_len) {
@@ -448,10 +479,11 @@ __device__ __forceinline__ void inv_col_round(const Xform &X, const u64 *__restr
             const u32 r = base + m * stride;
             v[m] = LASTSTAGE ? __ldg(Sg + (u64)r * X.C + c0 + c) : sm[pidx(r * tc + c)];
         }
-        dit_regs<NS, LASTSTAGE>(v, s0, lo, stride, X.itwR);
+        dit_regs<NS, LASTSTAGE, HO>(v, s0, lo, stride, X.itwR);
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
             const u32 r = base + m * stride;
+            if (HO && m >= (1 << (NS - 1))) continue;  // rows >= R/2 hold bits >= gamma: unused
             if (TOGLOBAL) {
                 const u64 j = (u64)r * X.C + c0 + c;
                 const u64 e = (0ULL - X.G * j) & (X.N - 1);
@@ -491,12 +523,18 @@ __global__ void __launch_bounds__(PA_COL_T) k_inv_col(Xform X, const u64 *__rest
         return;
     }
     const u32 nr = (l + 2) / 3;
+    // Eq. 4 stage: only t mod 2^gamma is needed, i.e. digits j < N/2 (rows < R/2)
+    const bool ho = X.stage == 1;
     for (int rd = (int)nr - 1; rd >= 0; rd--) {
         const u32 s0 = 3 * rd, ns = min(3u, l - s0);
         const bool first = rd == (int)nr - 1, last = rd == 0;
 #define PA_INV_COL(NSV)                                                                       \
     do {                                                                                      \
-        if (first && last)                                                                    \
+        if (last && ho && NSV == 3 && first)                                                  \
+            inv_col_round<NSV, true, true, true>(X, Sg, sm, Z, c0, s0, add_src, add_base, add_len); \
+        else if (last && ho && NSV == 3)                                                      \
+            inv_col_round<NSV, false, true, true>(X, Sg, sm, Z, c0, s0, add_src, add_base, add_len); \
+        else if (first && last)                                                               \
             inv_col_round<NSV, true, true>(X, Sg, sm, Z, c0, s0, add_src, add_base, add_len);   \
         else if (first)                                                                       \
             inv_col_round<NSV, true, false>(X, Sg, sm, Z, c0, s0, add_src, add_base, add_len);  \
@@ -568,7 +606,8 @@ __global__ void __launch_bounds__(PA_CARRY_T) k_carry_a(CarryDev cd, const u64 *
     }
     const u64 Ht = (u64)acc;
     Hs[threadIdx.x] = Ht;
-    if (threadIdx.x == 0) Hprev = chunk_carry_out(cd, z, t == 0 ? cd.nchunks - 1 : t - 1);
+    if (threadIdx.x == 0)
+        Hprev = t ? chunk_carry_out(cd, z, t - 1) : (cd.linear ? 0 : chunk_carry_out(cd, z, cd.nchunks - 1));
     __syncthreads();
     const u64 Hin = threadIdx.x ? Hs[threadIdx.x - 1] : Hprev;
 
@@ -640,7 +679,7 @@ __global__ void __launch_bounds__(1024) k_carry_b(CarryDev cd, u32 nctas) {
     if (warp == 0) {
         const unsigned g2 = __ballot_sync(0xFFFFFFFFu, wG[lane]), p2 = __ballot_sync(0xFFFFFFFFu, wP[lane]);
         const u64 a = g2 | p2;
-        const unsigned ewrap = (unsigned)((a + g2) >> 32);
+        const unsigned ewrap = cd.linear ? 0u : (unsigned)((a + g2) >> 32);
         const u64 sum = a + g2 + ewrap;
         wcin[lane] = (unsigned)(((sum ^ a ^ g2) >> lane) & 1);
         if (lane == 0) *cd.allones = 1;
@@ -699,21 +738,22 @@ __global__ void __launch_bounds__(PA_CARRY_T) k_carry_c(CarryDev cd, u64 *__rest
     if (threadIdx.x == 0 && !all) *cd.allones = 0;
 }
 
-// Small transforms: one thread resolves the whole ring sequentially.
-__global__ void k_carry_seq(CarryDev cd, u64 *__restrict__ z, u64 *__restrict__ y) {
+// Small transforms: one thread resolves the digits sequentially (around the
+// ring, or linearly dropping the top carry).
+__global__ void k_carry_seq(CarryDev cd, u64 ndigits, u64 *__restrict__ z, u64 *__restrict__ y) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     unsigned __int128 c = 0;
     for (int pass = 0; pass < 8; pass++) {
-        for (u64 j = 0; j < cd.N; j++) {
+        for (u64 j = 0; j < ndigits; j++) {
             const u32 b = digit_bits(cd, j);
             const unsigned __int128 v = (unsigned __int128)z[j] + c;
             z[j] = (u64)v & ((1ULL << b) - 1);
             c = v >> b;
         }
-        if (c == 0) break;
+        if (c == 0 || cd.linear) break;
     }
     bool ones = true;
-    for (u64 j = 0; j < cd.N; j++) {
+    for (u64 j = 0; j < ndigits; j++) {
         const u32 b = digit_bits(cd, j);
         const u64 s = digit_start(cd.G, j, cd.N, cd.logN);
         ones = ones && z[j] == ((1ULL << b) - 1);
@@ -874,15 +914,20 @@ int launch_inv_col(const Xform &X, const u64 *S, u64 *Z, const u64 *add_src, u64
     return (int)cudaGetLastError();
 }
 
-int launch_carry(const Xform &X, const CarryDev &cd, u64 *z, u64 *out_bits, u64 out_words, void *stream) {
+int launch_carry(const Xform &X, const CarryDev &cd_in, u64 *z, u64 *out_bits, u64 out_words, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(out_bits, 0, out_words * sizeof(u64), s);
     if (e) return e;
+    // MH stage: only digits [0, N/2) hold bits below gamma; resolve them linearly
+    CarryDev cd = cd_in;
+    const u64 ndigits = (X.stage == 1 && X.N >= 2) ? X.N / 2 : X.N;
+    cd.linear = (X.stage == 1 && X.N >= 2) ? 1 : 0;
+    cd.nchunks = ndigits / PA_CARRY_D;
     // chunks of PA_CARRY_D digits must span >= 64 bits so that adding the
     // previous chunk's carry-out leaves a 1-bit carry
     const bool parallel = cd.nchunks >= PA_CARRY_T && (X.G >> X.logN) * PA_CARRY_D >= 64;
     if (!parallel) {
-        TRACED("carry_seq", X.stage, stream, (k_carry_seq<<<1, 32, 0, s>>>(cd, z, out_bits)));
+        TRACED("carry_seq", X.stage, stream, (k_carry_seq<<<1, 32, 0, s>>>(cd, ndigits, z, out_bits)));
         return (int)cudaGetLastError();
     }
     const u32 nctas = (u32)(cd.nchunks / PA_CARRY_T);
