@@ -111,6 +111,14 @@ int pa_hash_host_async(pa_plan_t *plan, const uint64_t *key, const uint64_t *see
 int pa_debug_mmh(pa_plan_t *plan, const uint64_t *key, const uint64_t *seed, uint64_t *y,
                  int *status, void *stream);
 
+/* Comparison scheme (the prior-art scheme the paper compares against): the
+ * modular-arithmetic hash over the whole key, Eq. 4 with alpha = n, beta = r:
+ * z = ((b x + c) mod 2^n) >> (n - r), b forced odd.  The plan's seed holds
+ * b = bits [0, n) and c = bits [n, 2n) (ceil(2n/64) words; pa_plan_info
+ * reports gamma = n, k = 0, mmh_len = 0).  Only pa_hash and pa_hash_batch
+ * accept such a plan.  n <= about 1.3e8 bits (one exact n x n-bit product). */
+int pa_mh_plan(uint64_t n_bits, uint64_t r_bits, pa_plan_t **out);
+
 /* Seed reuse.  When the same hash seed (a, b, c) serves many blocks,
  * pa_seed_prepare transforms a_1..a_k and b once and keeps their spectra (and
  * a copy of the seed) in the plan: k N_mmh + N_mh words plus the seed, allocated

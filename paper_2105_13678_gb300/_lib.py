@@ -63,6 +63,7 @@ class pa_trace_entry(ctypes.Structure):
 SIGNATURES = {
     "pa_plan": (ctypes.c_int, [_u64, _u64, ctypes.POINTER(pa_params), ctypes.POINTER(_vp)]),
     "pa_plan_info_get": (ctypes.c_int, [_vp, ctypes.POINTER(pa_plan_info)]),
+    "pa_mh_plan": (ctypes.c_int, [_u64, _u64, ctypes.POINTER(_vp)]),
     "pa_plan_destroy": (ctypes.c_int, [_vp]),
     "pa_hash": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "pa_hash_host": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
@@ -133,12 +134,17 @@ def params(gamma: int = 0, margin: int = 128, tune: bool = False) -> pa_params:
 
 
 class Plan:
-    """Owns a ``pa_plan_t``: step 0 of Algorithm 1 plus the device workspace."""
+    """Owns a ``pa_plan_t``: step 0 of Algorithm 1 plus the device workspace.
+    ``modular_hash=True`` builds the comparison scheme (Eq. 4 over the whole key)."""
 
-    def __init__(self, n_bits: int, r_bits: int, gamma: int = 0, margin: int = 128, tune: bool = False):
+    def __init__(self, n_bits: int, r_bits: int, gamma: int = 0, margin: int = 128, tune: bool = False,
+                 modular_hash: bool = False):
         h = _vp()
-        p = params(gamma, margin, tune)
-        check(lib().pa_plan(n_bits, r_bits, ctypes.byref(p), ctypes.byref(h)), "pa_plan")
+        if modular_hash:
+            check(lib().pa_mh_plan(n_bits, r_bits, ctypes.byref(h)), "pa_mh_plan")
+        else:
+            p = params(gamma, margin, tune)
+            check(lib().pa_plan(n_bits, r_bits, ctypes.byref(p), ctypes.byref(h)), "pa_plan")
         self.handle = h
         info = pa_plan_info()
         check(lib().pa_plan_info_get(h, ctypes.byref(info)), "pa_plan_info_get")

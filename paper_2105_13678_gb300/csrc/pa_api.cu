@@ -124,6 +124,7 @@ std::vector<u64> powers(u64 base, size_t count, u64 scale = 1) {
 struct pa_plan_s {
     uint64_t n, r, k;
     uint32_t gamma;
+    bool mh_only = false;   // modular-arithmetic hash over the whole key (gamma = n, k = 0)
     Xform mmh, mh;
     DevTables tables;
     // workspace
@@ -347,6 +348,46 @@ int pa_plan(uint64_t n_bits, uint64_t r_bits, const pa_params *params, pa_plan_t
     return PA_OK;
 }
 
+// Comparison scheme: the modular-arithmetic hash over the whole key (Eq. 4
+// with alpha = n, beta = r), one exact n x n-bit product.
+int pa_mh_plan(uint64_t n_bits, uint64_t r_bits, pa_plan_t **out) {
+    if (!out || n_bits == 0 || r_bits == 0 || r_bits > n_bits || n_bits > 0xFFFFFFFFULL) return PA_ERR_INVALID;
+    *out = nullptr;
+    uint32_t l2;
+    int rc = choose_len(2 * n_bits, 1, &l2);
+    if (rc) return rc;
+    if (prepare_kernels()) return PA_ERR_CUDA;
+    pa_plan_t *pl = new (std::nothrow) pa_plan_s();
+    if (!pl) return PA_ERR_NOMEM;
+    pl->mh_only = true;
+    pl->n = n_bits;
+    pl->r = r_bits;
+    pl->gamma = (uint32_t)n_bits;
+    pl->k = 0;
+    const WsSizes z = ws_sizes(pl->gamma, 0, 1, 1ULL << l2);
+    int err = PA_OK;
+    pl->Y = (u64 *)pl->alloc(z.Y, &err);
+    pl->S = (u64 *)pl->alloc(z.S, &err);
+    pl->ybuf = (u64 *)pl->alloc(z.ybuf, &err);
+    pl->tbuf = (u64 *)pl->alloc(z.tbuf, &err);
+    pl->H = (u64 *)pl->alloc(z.H, &err);
+    pl->cstate = (unsigned char *)pl->alloc(z.cstate, &err);
+    pl->cta_state = (unsigned char *)pl->alloc(z.cta, &err);
+    pl->cta_cin = (unsigned char *)pl->alloc(z.cta, &err);
+    pl->flags_bytes = z.flags;
+    pl->flags = (int *)pl->alloc(z.flags, &err);
+    if (!err) err = build_xform(pl, pl->mh, 2 * n_bits, 1);
+    pl->mh.stage = 1;
+    pl->mmh = pl->mh;
+    pl->mmh.N = 0;
+    if (err) {
+        delete pl;
+        return err;
+    }
+    *out = pl;
+    return PA_OK;
+}
+
 int pa_plan_info_get(const pa_plan_t *pl, pa_plan_info *info) {
     if (!pl || !info) return PA_ERR_INVALID;
     memset(info, 0, sizeof(*info));
@@ -465,6 +506,14 @@ extern "C" {
 
 int pa_hash(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint64_t *out, int *status, void *stream) {
     if (!pl || !key || !seed || !out) return PA_ERR_INVALID;
+    if (pl->mh_only) {
+        // Eq. 4 with alpha = n: the key itself is the MH input y
+        cudaStream_t s = (cudaStream_t)stream;
+        int e = cudaMemsetAsync(pl->flags, 0, pl->flags_bytes, s);
+        if (!e) e = cudaMemcpyAsync(pl->ybuf, key, ((pl->n + 63) / 64) * 8, cudaMemcpyDeviceToDevice, s);
+        if (!e) e = enqueue_mh(pl, (const u64 *)seed, (u64 *)out, status, stream);
+        return cuda_rc(e);
+    }
     int e = enqueue_mmh(pl, (const u64 *)key, (const u64 *)seed, pl->ybuf, false, stream);
     if (!e) e = enqueue_mh(pl, (const u64 *)seed, (u64 *)out, status, stream);
     return cuda_rc(e);
@@ -472,6 +521,7 @@ int pa_hash(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint64_t *
 
 int pa_debug_mmh(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint64_t *y, int *status, void *stream) {
     if (!pl || !key || !seed || !y) return PA_ERR_INVALID;
+    if (pl->mh_only) return PA_ERR_INVALID;
     int e = enqueue_mmh(pl, (const u64 *)key, (const u64 *)seed, (u64 *)y, true, stream);
     if (!e && status) e = cudaMemcpyAsync(status, pl->flags, sizeof(int), cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
     return cuda_rc(e);
@@ -489,6 +539,7 @@ static int host_groups(uint64_t k) { return (int)((k + host_group_size(k) - 1) /
 int pa_hash_host_async(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint64_t *out, int *status,
                        void *stream) {
     if (!pl || !key || !seed || !out) return PA_ERR_INVALID;
+    if (pl->mh_only) return PA_ERR_INVALID;
     const uint64_t kw = (pl->n + 63) / 64, sw = ((pl->k + 2) * pl->gamma + 63) / 64, ow = (pl->r + 63) / 64;
     const uint64_t g = pl->gamma, k = pl->k;
     const int ng = host_groups(k);
@@ -572,6 +623,7 @@ int pa_hash_host(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint6
 // and y.  The plan keeps a copy of the seed (c is read from it).
 int pa_seed_prepare(pa_plan_t *pl, const uint64_t *seed, void *stream) {
     if (!pl || !seed) return PA_ERR_INVALID;
+    if (pl->mh_only) return PA_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     const uint64_t sw = ((pl->k + 2) * pl->gamma + 63) / 64;
     if (!pl->spec_a) {
