@@ -132,8 +132,26 @@ def measured_peaks():
 
 
 # Algorithmic work of each kernel, per launch, for one plan:
-# bytes = compulsory global reads + writes; mults = F_q products.
-def kernel_model(info, stage: str, kernel: str):
+# bytes = compulsory global reads + writes; products = F_q multiplications;
+# alu = integer-ALU-pipe operations of the F_q arithmetic the kernel must do,
+# counted from the carry-chain sequences of the field code: add 6, sub 8,
+# product 8, digit x weight product 2 (the multiplies themselves run on the
+# FMA pipe).  A radix-2 butterfly is add + sub + product = 22, one with a
+# twiddle of 1 (the last stage of every sub-transform) add + sub = 14.
+ALU_ADD, ALU_SUB, ALU_MUL, ALU_MULS = 6, 8, 8, 2
+
+
+def _dft_work(length: int, count: int):
+    """count radix-2 transforms of `length`: (butterflies, products, alu)."""
+    if length <= 1:
+        return 0, 0, 0
+    lg = int(math.log2(length))
+    full = count * (length // 2) * (lg - 1)
+    trivial = count * (length // 2)
+    return full + trivial, full, full * (ALU_ADD + ALU_SUB + ALU_MUL) + trivial * (ALU_ADD + ALU_SUB)
+
+
+def kernel_model(info, stage: str, kernel: str, geometry=None):
     gamma, k = info.gamma, info.k
     if stage == "mmh":
         N, K = info.mmh_len, k
@@ -142,17 +160,21 @@ def kernel_model(info, stage: str, kernel: str):
         N, K = info.mh_len, 1
         src_bits = 2 * gamma
     logN = int(math.log2(N))
-    logR = min(logN // 2, 11)
+    logR = geometry[0] if geometry else min(logN // 2, 11)
     logC = logN - logR
     R, C = 1 << logR, 1 << logC
     if kernel == "fwd_col":
-        return (src_bits / 8 + 2 * K * N * 8,
-                2 * K * (N + C * (R // 2) * logR + N))
+        _, p, a = _dft_work(R, 2 * K * C)
+        # weights (digit x weight) and the merged column weight / twiddle product
+        return (src_bits / 8 + 2 * K * N * 8, p + 4 * K * N, a + 2 * K * N * (ALU_MULS + ALU_MUL))
     if kernel == "row_mac":
-        return ((2 * K + 1) * N * 8, (2 * K + 1) * R * (C // 2) * logC + K * N + N)
+        _, p, a = _dft_work(C, (2 * K + 1) * R)
+        # multiply-accumulate of K pairs and the inverse twiddle
+        return ((2 * K + 1) * N * 8, p + K * N + N, a + K * N * (ALU_MUL + ALU_ADD) + N * ALU_MUL)
     if kernel == "inv_col":
-        return (2 * N * 8, C * (R // 2) * logR + N)
-    return (None, None)
+        _, p, a = _dft_work(R, C)
+        return (2 * N * 8, p + N, a + N * ALU_MUL)
+    return (None, None, None)
 
 
 # ------------------------------------------------------------- GPU (gb300)
@@ -263,7 +285,8 @@ def run_gb300(args):
 
     value = job_mbps(n, args.steps, ws, total_ms)
     peaks, peak_kind = measured_peaks()
-    roof = roofline(info, trace, args.steps, peaks, peak_kind, step_ms)
+    roof = roofline(info, trace, args.steps, peaks, peak_kind, step_ms,
+                    {"mmh": plan.geometry(0), "mh": plan.geometry(1)})
 
     line = {
         "metric": METRIC,
@@ -325,36 +348,36 @@ def run_gb300(args):
         dist.destroy_process_group()
 
 
-def roofline(info, trace, steps, peaks, peak_kind, step_ms):
-    """Dominant kernel: achieved algorithmic bytes/s (HBM) and F_q products/s
-    (integer multiplier) against their peaks; the larger fraction names the bound."""
+def roofline(info, trace, steps, peaks, peak_kind, step_ms, geometries=None):
+    """Dominant kernel: algorithmic integer-ALU operations per second against
+    the ALU pipe's peak (the unit ncu shows saturating), with the HBM and
+    multiplier fractions beside it."""
     if not trace:
         return None
     name, (launches, tot) = max(trace.items(), key=lambda kv: kv[1][1])
     stage, kern = name.split(".", 1)
-    bytes_, mults = kernel_model(info, stage, kern)
+    geo = (geometries or {}).get(stage)
+    bytes_, mults, alu = kernel_model(info, stage, kern, geo)
     avg_s = tot / 1e3 / max(1, launches)
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    # F_q product = 4 32x32->64 partial products = 8 32-bit IMAD issue slots;
-    # 152 SMs x 64 IMAD/clk/SM at the maximum SM clock.
+    # integer ALU pipe: 16 lanes per SM sub-partition x 4 x 152 SMs at the
+    # maximum SM clock; F_q products: 64 IMAD/clk/SM, 8 IMAD issue slots each
+    alu_peak = 152 * 64 * sm_mhz * 1e6
     mul_peak = 152 * 64 * sm_mhz * 1e6 / 8
     out = {"kernel": name, "launches": launches, "avg_us": round(avg_s * 1e6, 2),
            "share_of_step": round(tot / max(1e-9, sum(step_ms)), 3)}
     if bytes_ is None:
         return out
-    hbm_ach = bytes_ / avg_s / 1e9
-    mul_ach = mults / avg_s
-    f_hbm, f_mul = hbm_ach / hbm_peak, mul_ach / mul_peak
-    if f_hbm >= f_mul:
-        out.update({"bound": "hbm", "achieved": round(hbm_ach, 1), "peak": hbm_peak, "unit": "GB/s",
-                    "frac": round(f_hbm, 4), "peak_source": peak_kind})
-    else:
-        out.update({"bound": "alu", "achieved": round(mul_ach / 1e12, 4), "peak": round(mul_peak / 1e12, 4),
-                    "unit": "T F_q-products/s", "frac": round(f_mul, 4),
-                    "peak_source": "derived: 152 SMs x 64 IMAD/clk x max SM clock / 8 IMAD per F_q product"})
-    out["hbm"] = {"achieved_gbs": round(hbm_ach, 1), "frac": round(f_hbm, 4), "algorithmic_bytes": int(bytes_)}
-    out["mul"] = {"achieved_t_per_s": round(mul_ach / 1e12, 4), "frac": round(f_mul, 4), "products": int(mults)}
+    hbm_ach, mul_ach, alu_ach = bytes_ / avg_s / 1e9, mults / avg_s, alu / avg_s
+    out.update({"bound": "alu", "achieved": round(alu_ach / 1e12, 3), "peak": round(alu_peak / 1e12, 3),
+                "unit": "T int-ALU-ops/s", "frac": round(alu_ach / alu_peak, 4),
+                "peak_source": "derived: 152 SMs x 4 sub-partitions x 16 INT32 ALU lanes x max SM clock",
+                "algorithmic_alu_ops": int(alu)})
+    out["hbm"] = {"achieved_gbs": round(hbm_ach, 1), "peak_gbs": hbm_peak, "frac": round(hbm_ach / hbm_peak, 4),
+                  "algorithmic_bytes": int(bytes_), "peak_source": peak_kind}
+    out["mul"] = {"achieved_t_per_s": round(mul_ach / 1e12, 4), "peak_t_per_s": round(mul_peak / 1e12, 4),
+                  "frac": round(mul_ach / mul_peak, 4), "products": int(mults)}
     out["traffic"] = None
     return out
 
@@ -411,10 +434,12 @@ def run_sweep(steps: int = 5):
         _lib.trace_enable(False)
         step_ms = [a.elapsed_time(b_) for a, b_ in evs]
         ms = sum(step_ms) / steps
-        roof = roofline(plan.info, trace, steps, peaks, peak_kind, step_ms)
+        roof = roofline(plan.info, trace, steps, peaks, peak_kind, step_ms,
+                        {"mmh": plan.geometry(0), "mh": plan.geometry(1)})
         out.append({"n_bits": n, "r_bits": r, "gamma": plan.gamma, "k": plan.k, "mmh_len": plan.info.mmh_len,
                     "mh_len": plan.info.mh_len, "ms_per_block": round(ms, 4), "mbps": round(n / ms / 1e3, 1),
                     "dominant_kernel": roof["kernel"] if roof else None,
+                    "frac_alu": roof["frac"] if roof else None,
                     "frac_mul": roof["mul"]["frac"] if roof else None,
                     "frac_hbm": roof["hbm"]["frac"] if roof else None, "status": int(st.item())})
         plan.close()
