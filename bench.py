@@ -348,6 +348,36 @@ def run_gb300(args):
         dist.destroy_process_group()
 
 
+def kernel_sources_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("pa_kernels.cu", "gl_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2105_13678_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from profiles/traffic.md, if it was
+    measured on the current kernel sources; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.md")) as f:
+            lines = f.read().splitlines()
+    except OSError:
+        return None
+    src = next((ln.split(":", 1)[1].strip() for ln in lines if ln.startswith("sources:")), None)
+    if src != kernel_sources_hash():
+        return None
+    for ln in lines:
+        cells = [c.strip() for c in ln.strip().strip("|").split("|")]
+        if cells and cells[0] == kernel and len(cells) >= 4:
+            try:
+                return int(cells[3])
+            except ValueError:
+                return None
+    return None
+
+
 def roofline(info, trace, steps, peaks, peak_kind, step_ms, geometries=None):
     """Dominant kernel: algorithmic integer-ALU operations per second against
     the ALU pipe's peak (the unit ncu shows saturating), with the HBM and
@@ -378,7 +408,8 @@ def roofline(info, trace, steps, peaks, peak_kind, step_ms, geometries=None):
                   "algorithmic_bytes": int(bytes_), "peak_source": peak_kind}
     out["mul"] = {"achieved_t_per_s": round(mul_ach / 1e12, 4), "peak_t_per_s": round(mul_peak / 1e12, 4),
                   "frac": round(mul_ach / mul_peak, 4), "products": int(mults)}
-    out["traffic"] = None
+    out["traffic"] = ncu_traffic(name)
+    out["traffic_source"] = "profiles/traffic.md (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
     return out
 
 
