@@ -218,8 +218,9 @@ int pa_transform_len(uint64_t G, uint64_t K, uint32_t *log_n);
  * N = 2^log_r x 2^log_c, column passes work on tiles of tile_cols columns. */
 int pa_plan_geometry(const pa_plan_t *plan, int stage, uint32_t *log_r, uint32_t *log_c, uint32_t *tile_cols);
 /* Device check of the F_q arithmetic used inside the transforms: for i < n,
- * out[3i], out[3i+1], out[3i+2] = (a[i] + b[i], a[i] - b[i], a[i] * b[i]) mod q,
- * canonical; a, b, out are device arrays (any 64-bit inputs).  Asynchronous. */
+ * out[4i .. 4i+3] = (a[i] + b[i], a[i] - b[i], a[i] * b[i], (a[i] mod 2^32) * b[i])
+ * mod q, canonical; a, b, out (4n words) are device arrays, any 64-bit inputs.
+ * Asynchronous. */
 int pa_selftest_field(const uint64_t *a, const uint64_t *b, uint64_t *out, uint64_t n, void *stream);
 
 /* Human-readable name of a return code (static string). */

@@ -249,12 +249,12 @@ class Server:
     """``pa_serve_*``: continuous-batching request loop on the current device."""
 
     def __init__(self, hbm_budget_bytes: int, slots: int = 8, max_queue: int = 0, gamma: int = 0,
-                 margin: int = 128):
+                 margin: int = 128, tune: bool = False):
         cfg = pa_serve_config()
         cfg.hbm_budget_bytes = hbm_budget_bytes
         cfg.slots = slots
         cfg.max_queue = max_queue
-        cfg.params = params(gamma, margin)
+        cfg.params = params(gamma, margin, tune)
         h = _vp()
         check(lib().pa_serve_create(ctypes.byref(cfg), ctypes.byref(h)), "pa_serve_create")
         self.handle = h

@@ -258,7 +258,7 @@ static int build_xform(pa_plan_t *pl, Xform &X, uint64_t G, uint64_t K, u32 logR
 // ------------------------------------------------------------ autotuner --
 // For a transform shape (G, K, N) the tuner times every valid four-step split
 // log2 R in {d - 1, d, d + 1} (d = the default) and column tile width in
-// {2, 4, 8} on the plan's own workspace (forward column pass, row pass with
+// {1, 2, 4, 8} on the plan's own workspace (forward column pass, row pass with
 // the multiply-accumulate, inverse column pass; one warm-up, best of three)
 // and keeps the fastest.  Results are cached per process.
 static std::mutex g_tune_mu;
@@ -734,7 +734,7 @@ static int tune_geometry(pa_plan_t *pl, int stage, uint64_t G, uint64_t K, uint3
     for (int dr = -1; dr <= 1 && !rc; dr++) {
         if ((int)dR + dr < 0) continue;
         const u32 logR = (u32)((int)dR + dr);
-        for (u32 tc : {2u, 4u, 8u}) {
+        for (u32 tc : {1u, 2u, 4u, 8u}) {
             if (!geometry_ok(l, logR, tc)) continue;
             DevTables tmp;
             Xform X;

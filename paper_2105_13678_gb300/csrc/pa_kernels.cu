@@ -796,12 +796,14 @@ __global__ void k_canonical_zero(const int *__restrict__ flag, u64 *__restrict__
 }
 
 // Element-wise F_q arithmetic of the transforms, for host-side checking:
-// out[3i] = a+b, out[3i+1] = a-b, out[3i+2] = a*b (canonical); any 64-bit inputs.
+// out[4i] = a+b, out[4i+1] = a-b, out[4i+2] = a*b, out[4i+3] = (a mod 2^32)*b
+// (canonical); any 64-bit inputs.
 __global__ void k_selftest_field(const u64 *__restrict__ a, const u64 *__restrict__ b, u64 *__restrict__ out, u64 n) {
     for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
-        out[3 * i] = gd_canon(gd_add(a[i], b[i]));
-        out[3 * i + 1] = gd_canon(gd_sub(a[i], b[i]));
-        out[3 * i + 2] = gd_canon(gd_mul(a[i], b[i]));
+        out[4 * i] = gd_canon(gd_add(a[i], b[i]));
+        out[4 * i + 1] = gd_canon(gd_sub(a[i], b[i]));
+        out[4 * i + 2] = gd_canon(gd_mul(a[i], b[i]));
+        out[4 * i + 3] = gd_canon(gd_mul_small((u32)a[i], b[i]));
     }
 }
 

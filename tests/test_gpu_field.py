@@ -24,12 +24,13 @@ def test_field_ops_edge_and_random():
     b = np.concatenate([b, rnd[:, 1]])
     da = torch.from_numpy(a.view(np.int64)).cuda()
     db = torch.from_numpy(b.view(np.int64)).cuda()
-    out = torch.zeros(3 * a.size, dtype=torch.int64, device="cuda")
+    out = torch.zeros(4 * a.size, dtype=torch.int64, device="cuda")
     _lib.check(_lib.lib().pa_selftest_field(da.data_ptr(), db.data_ptr(), out.data_ptr(), a.size, None), "selftest")
     torch.cuda.synchronize()
-    got = out.cpu().numpy().view(np.uint64).reshape(-1, 3)
+    got = out.cpu().numpy().view(np.uint64).reshape(-1, 4)
     for i in range(a.size):
         x, y = int(a[i]), int(b[i])
         assert int(got[i, 0]) == (x + y) % Q, (hex(x), hex(y), "add")
         assert int(got[i, 1]) == (x - y) % Q, (hex(x), hex(y), "sub")
         assert int(got[i, 2]) == (x * y) % Q, (hex(x), hex(y), "mul")
+        assert int(got[i, 3]) == ((x & 0xFFFFFFFF) * y) % Q, (hex(x), hex(y), "mul_small")
