@@ -213,15 +213,16 @@ __device__ __forceinline__ void weighted_pair(const Xform &X, const OpDesc &dx, 
     } while (0)
 
 
-template <int NS, bool PAIR, bool FIRST, bool LAST, bool HZ = false>
+// LL, TC: log2 R and the tile width when fixed at compile time (0: read from X).
+template <int NS, bool PAIR, bool FIRST, bool LAST, bool HZ, int LL, int TC>
 __device__ __forceinline__ void fwd_col_round(const Xform &X, const OpDesc &dx, const OpDesc &da,
                                               u64 *__restrict__ smx, u64 *__restrict__ sma, u64 *__restrict__ Yx,
                                               u64 *__restrict__ Ya, u32 c0, u32 s0, bool &ones) {
-    const u32 l = X.logR, tc = X.tc;
+    const u32 l = LL ? (u32)LL : X.logR, tc = TC ? (u32)TC : X.tc;
     const u32 gcm = gcmodn(X);
     const u32 sh = l - s0 - NS, stride = 1u << sh;
-    const u32 ntask = (X.R >> NS) * tc;
-    const u32 logtc = __ffs(tc) - 1;
+    const u32 ntask = ((1u << l) >> NS) * tc;
+    const u32 logtc = TC ? (u32)__builtin_ctz(TC) : (u32)(__ffs(tc) - 1);
     for (u32 task = threadIdx.x; task < ntask; task += blockDim.x) {
         const u32 c = task & (tc - 1), g = task >> logtc;
         const u32 lo = g & (stride - 1), base = ((g >> sh) << (l - s0)) + lo;
@@ -260,10 +261,10 @@ __device__ __forceinline__ void fwd_col_round(const Xform &X, const OpDesc &dx, 
 
 // One CTA: a tile of tc columns of operand pair blockIdx.y (PAIR), written to
 // Y[i] and Y[K + i], or of the single operand blockIdx.y, written to Y[i].
-template <bool PAIR>
+template <bool PAIR, int LL, int TC>
 __global__ void __launch_bounds__(PA_COL_T, 3) k_fwd_col(Xform X, Operands S, u64 *__restrict__ Y) {
     extern __shared__ u64 sm[];
-    const u32 tc = X.tc, c0 = blockIdx.x * tc, i = blockIdx.y + S.pair0;
+    const u32 tc = TC ? (u32)TC : X.tc, c0 = blockIdx.x * tc, i = blockIdx.y + S.pair0;
     OpDesc dx, da;
     if (PAIR)
         pair_desc(S, i, dx, da);
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(PA_COL_T, 3) k_fwd_col(Xform X, Operands S, u6
     u64 *Yx = Y + (u64)i * X.N, *Ya = Y + (u64)(X.K + i) * X.N;
     u64 *smx = sm, *sma = sm + pidx(X.R * tc);
     bool ones = true;
-    const u32 l = X.logR;
+    const u32 l = LL ? (u32)LL : X.logR;
     if (l == 0) {
         for (u32 c = threadIdx.x; c < tc; c += blockDim.x) {
             u64 wx, wa;
@@ -285,23 +286,24 @@ __global__ void __launch_bounds__(PA_COL_T, 3) k_fwd_col(Xform X, Operands S, u6
         const u32 nr = (l + 2) / 3;
         // Eq. 4 stage: y, b < 2^gamma, so digits j >= N/2 (rows >= R/2) are zero
         const bool hz = X.stage == 1;
+#pragma unroll(LL > 0 ? 8 : 1)
         for (u32 rd = 0; rd < nr; rd++) {
             const u32 s0 = 3 * rd, ns = min(3u, l - s0);
             const bool first = rd == 0, last = rd == nr - 1;
 #define PA_FWD_COL(NSV)                                                                     \
     do {                                                                                    \
         if (first && hz && NSV == 3 && last)                                                \
-            fwd_col_round<NSV, PAIR, true, true, true>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones); \
+            fwd_col_round<NSV, PAIR, true, true, true, LL, TC>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones); \
         else if (first && hz && NSV == 3)                                                   \
-            fwd_col_round<NSV, PAIR, true, false, true>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones); \
+            fwd_col_round<NSV, PAIR, true, false, true, LL, TC>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones); \
         else if (first && last)                                                             \
-            fwd_col_round<NSV, PAIR, true, true>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones);   \
+            fwd_col_round<NSV, PAIR, true, true, false, LL, TC>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones);   \
         else if (first)                                                                     \
-            fwd_col_round<NSV, PAIR, true, false>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones);  \
+            fwd_col_round<NSV, PAIR, true, false, false, LL, TC>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones);  \
         else if (last)                                                                      \
-            fwd_col_round<NSV, PAIR, false, true>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones);  \
+            fwd_col_round<NSV, PAIR, false, true, false, LL, TC>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones);  \
         else                                                                                \
-            fwd_col_round<NSV, PAIR, false, false>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones); \
+            fwd_col_round<NSV, PAIR, false, false, false, LL, TC>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones); \
     } while (0)
             PA_DISPATCH_NS(ns, PA_FWD_COL);
 #undef PA_FWD_COL
@@ -328,12 +330,12 @@ __global__ void __launch_bounds__(PA_COL_T, 3) k_fwd_col(Xform X, Operands S, u6
 
 enum { ROW_PAIRS = 0, ROW_STORE = 1, ROW_PREPARED = 2 };
 
-template <int NS, int ACC, int MODE, bool LAST>
+template <int NS, int ACC, int MODE, bool LAST, int LL>
 __device__ __forceinline__ void row_fwd_round(const Xform &X, const u64 *__restrict__ xrow,
                                               const u64 *__restrict__ arow, u64 *__restrict__ smx,
                                               u64 *__restrict__ sma, u64 *__restrict__ spec, u32 s0, bool first,
                                               u64 (&acc)[ACC]) {
-    const u32 l = X.logC, sh = l - s0 - NS, stride = 1u << sh, ngroups = X.C >> NS;
+    const u32 l = LL ? (u32)LL : X.logC, sh = l - s0 - NS, stride = 1u << sh, ngroups = (1u << l) >> NS;
 #pragma unroll
     for (int t = 0; t < (ACC >> NS); t++) {
         const u32 g = threadIdx.x + t * blockDim.x;
@@ -367,10 +369,10 @@ __device__ __forceinline__ void row_fwd_round(const Xform &X, const u64 *__restr
     }
 }
 
-template <int NS, int ACC, bool LAST>
+template <int NS, int ACC, bool LAST, int LL>
 __device__ __forceinline__ void row_inv_round(const Xform &X, u64 *__restrict__ sm, u64 *__restrict__ Srow, u32 row,
                                               u32 s0, bool to_global, const u64 (&acc)[ACC]) {
-    const u32 l = X.logC, sh = l - s0 - NS, stride = 1u << sh, ngroups = X.C >> NS;
+    const u32 l = LL ? (u32)LL : X.logC, sh = l - s0 - NS, stride = 1u << sh, ngroups = (1u << l) >> NS;
     const u32 kr = bitrev(row, X.logR);
 #pragma unroll
     for (int t = 0; t < (ACC >> NS); t++) {
@@ -399,11 +401,11 @@ __device__ __forceinline__ void row_inv_round(const Xform &X, u64 *__restrict__ 
 // One CTA per row; blockDim = C / ACC threads, each owning ACC accumulators.
 // Y holds the column-pass output; Spec the stored spectra (ROW_STORE writes
 // them, ROW_PREPARED reads them); S receives the inverse-row output.
-template <int ACC, int MODE>
+template <int ACC, int MODE, int LL>
 __global__ void __launch_bounds__(512, ACC == 8 ? 2 : 1)
     k_row_mac(Xform X, const u64 *__restrict__ Y, u64 *__restrict__ Spec, u64 *__restrict__ S) {
     extern __shared__ u64 sm[];
-    const u32 C = X.C, row = blockIdx.x, l = X.logC;
+    const u32 l = LL ? (u32)LL : X.logC, C = 1u << l, row = blockIdx.x;
     const u64 N = X.N;
     u64 *smx = sm, *sma = sm + pidx(C);
     if (l == 0) {
@@ -427,15 +429,16 @@ __global__ void __launch_bounds__(512, ACC == 8 ? 2 : 1)
         const u64 *xrow = Y + (u64)i * N + (u64)row * C;
         const u64 *arow = Y + (u64)(X.K + i) * N + (u64)row * C;
         u64 *spec = Spec + (u64)i * N + (u64)row * C;
+#pragma unroll(LL > 0 ? 8 : 1)
         for (u32 rd = 0; rd < nr; rd++) {
             const u32 s0 = 3 * rd, ns = min(3u, l - s0);
             const bool first = rd == 0, last = rd == nr - 1;
 #define PA_ROW_FWD(NSV)                                                                       \
     do {                                                                                      \
         if (last)                                                                             \
-            row_fwd_round<NSV, ACC, MODE, true>(X, xrow, arow, smx, sma, spec, s0, first, acc);  \
-        else                                                                                  \
-            row_fwd_round<NSV, ACC, MODE, false>(X, xrow, arow, smx, sma, spec, s0, first, acc); \
+            row_fwd_round<NSV, ACC, MODE, true, LL>(X, xrow, arow, smx, sma, spec, s0, first, acc);  \
+        else                                                                                      \
+            row_fwd_round<NSV, ACC, MODE, false, LL>(X, xrow, arow, smx, sma, spec, s0, first, acc); \
     } while (0)
             PA_DISPATCH_NS(ns, PA_ROW_FWD);
 #undef PA_ROW_FWD
@@ -444,15 +447,16 @@ __global__ void __launch_bounds__(512, ACC == 8 ? 2 : 1)
     }
     if (MODE == ROW_STORE) return;
     u64 *Srow = S + (u64)row * C;
+#pragma unroll(LL > 0 ? 8 : 1)
     for (int rd = (int)nr - 1; rd >= 0; rd--) {
         const u32 s0 = 3 * rd, ns = min(3u, l - s0);
         const bool from_acc = rd == (int)nr - 1, to_global = rd == 0;
 #define PA_ROW_INV(NSV)                                                        \
     do {                                                                       \
         if (from_acc)                                                          \
-            row_inv_round<NSV, ACC, true>(X, smx, Srow, row, s0, to_global, acc);  \
-        else                                                                   \
-            row_inv_round<NSV, ACC, false>(X, smx, Srow, row, s0, to_global, acc); \
+            row_inv_round<NSV, ACC, true, LL>(X, smx, Srow, row, s0, to_global, acc);  \
+        else                                                                       \
+            row_inv_round<NSV, ACC, false, LL>(X, smx, Srow, row, s0, to_global, acc); \
     } while (0)
         PA_DISPATCH_NS(ns, PA_ROW_INV);
 #undef PA_ROW_INV
@@ -462,14 +466,14 @@ __global__ void __launch_bounds__(512, ACC == 8 ? 2 : 1)
 
 // ------------------------------------------------------ inverse columns --
 
-template <int NS, bool LASTSTAGE, bool TOGLOBAL, bool HO = false>
+template <int NS, bool LASTSTAGE, bool TOGLOBAL, bool HO, int LL, int TC>
 __device__ __forceinline__ void inv_col_round(const Xform &X, const u64 *__restrict__ Sg, u64 *__restrict__ sm,
                                               u64 *__restrict__ Z, u32 c0, u32 s0,
                                               const u64 *__restrict__ add_src, u64 add_base, u64 add_len) {
-    const u32 l = X.logR, tc = X.tc;
+    const u32 l = LL ? (u32)LL : X.logR, tc = TC ? (u32)TC : X.tc;
     const u32 sh = l - s0 - NS, stride = 1u << sh;
-    const u32 ntask = (X.R >> NS) * tc;
-    const u32 logtc = __ffs(tc) - 1;
+    const u32 ntask = ((1u << l) >> NS) * tc;
+    const u32 logtc = TC ? (u32)__builtin_ctz(TC) : (u32)(__ffs(tc) - 1);
     for (u32 task = threadIdx.x; task < ntask; task += blockDim.x) {
         const u32 c = task & (tc - 1), g = task >> logtc;
         const u32 lo = g & (stride - 1), base = ((g >> sh) << (l - s0)) + lo;
@@ -502,11 +506,12 @@ __device__ __forceinline__ void inv_col_round(const Xform &X, const u64 *__restr
     }
 }
 
+template <int LL, int TC>
 __global__ void __launch_bounds__(PA_COL_T) k_inv_col(Xform X, const u64 *__restrict__ Sg, u64 *__restrict__ Z,
                                                       const u64 *__restrict__ add_src, u64 add_base, u64 add_len) {
     extern __shared__ u64 sm[];
-    const u32 tc = X.tc, c0 = blockIdx.x * tc;
-    const u32 l = X.logR;
+    const u32 tc = TC ? (u32)TC : X.tc, c0 = blockIdx.x * tc;
+    const u32 l = LL ? (u32)LL : X.logR;
     if (l == 0) {
         for (u32 c = threadIdx.x; c < tc; c += blockDim.x) {
             const u64 j = c0 + c;
@@ -525,23 +530,24 @@ __global__ void __launch_bounds__(PA_COL_T) k_inv_col(Xform X, const u64 *__rest
     const u32 nr = (l + 2) / 3;
     // Eq. 4 stage: only t mod 2^gamma is needed, i.e. digits j < N/2 (rows < R/2)
     const bool ho = X.stage == 1;
+#pragma unroll(LL > 0 ? 8 : 1)
     for (int rd = (int)nr - 1; rd >= 0; rd--) {
         const u32 s0 = 3 * rd, ns = min(3u, l - s0);
         const bool first = rd == (int)nr - 1, last = rd == 0;
 #define PA_INV_COL(NSV)                                                                       \
     do {                                                                                      \
         if (last && ho && NSV == 3 && first)                                                  \
-            inv_col_round<NSV, true, true, true>(X, Sg, sm, Z, c0, s0, add_src, add_base, add_len); \
+            inv_col_round<NSV, true, true, true, LL, TC>(X, Sg, sm, Z, c0, s0, add_src, add_base, add_len); \
         else if (last && ho && NSV == 3)                                                      \
-            inv_col_round<NSV, false, true, true>(X, Sg, sm, Z, c0, s0, add_src, add_base, add_len); \
+            inv_col_round<NSV, false, true, true, LL, TC>(X, Sg, sm, Z, c0, s0, add_src, add_base, add_len); \
         else if (first && last)                                                               \
-            inv_col_round<NSV, true, true>(X, Sg, sm, Z, c0, s0, add_src, add_base, add_len);   \
+            inv_col_round<NSV, true, true, false, LL, TC>(X, Sg, sm, Z, c0, s0, add_src, add_base, add_len);   \
         else if (first)                                                                       \
-            inv_col_round<NSV, true, false>(X, Sg, sm, Z, c0, s0, add_src, add_base, add_len);  \
+            inv_col_round<NSV, true, false, false, LL, TC>(X, Sg, sm, Z, c0, s0, add_src, add_base, add_len);  \
         else if (last)                                                                        \
-            inv_col_round<NSV, false, true>(X, Sg, sm, Z, c0, s0, add_src, add_base, add_len);  \
+            inv_col_round<NSV, false, true, false, LL, TC>(X, Sg, sm, Z, c0, s0, add_src, add_base, add_len);  \
         else                                                                                  \
-            inv_col_round<NSV, false, false>(X, Sg, sm, Z, c0, s0, add_src, add_base, add_len); \
+            inv_col_round<NSV, false, false, false, LL, TC>(X, Sg, sm, Z, c0, s0, add_src, add_base, add_len); \
     } while (0)
         PA_DISPATCH_NS(ns, PA_INV_COL);
 #undef PA_INV_COL
@@ -845,53 +851,89 @@ static inline u32 pidx_host(u32 i) { return i + (i >> 4); }
 static size_t col_smem(const Xform &X) { return (size_t)pidx_host(X.R * X.tc) * sizeof(u64); }
 static size_t row_smem(const Xform &X) { return (size_t)2 * pidx_host(X.C) * sizeof(u64); }
 
+// Instantiations with compile-time geometry for the production shapes (the
+// default split of 2^20 .. 2^24 transforms); everything else uses LL = TC = 0.
+#define PA_FOR_COL_SHAPES(F) F(0, 0) F(10, 4) F(11, 2)
+#define PA_FOR_ROW_SHAPES8(F) F(0) F(10) F(11) F(12)
+#define PA_FOR_ROW_SHAPES16(F) F(0) F(13)
+
 int prepare_kernels() {
     static bool done = false;
     if (done) return 0;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_fwd_col<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024))) return e;
-    if ((e = cudaFuncSetAttribute(k_fwd_col<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024))) return e;
-    if ((e = cudaFuncSetAttribute(k_inv_col, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024))) return e;
-#define PA_ROW_ATTR(A, M) \
-    if ((e = cudaFuncSetAttribute(k_row_mac<A, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024))) return e;
-    PA_ROW_ATTR(8, ROW_PAIRS)
-    PA_ROW_ATTR(8, ROW_STORE)
-    PA_ROW_ATTR(8, ROW_PREPARED)
-    PA_ROW_ATTR(16, ROW_PAIRS)
-    PA_ROW_ATTR(16, ROW_STORE)
-    PA_ROW_ATTR(16, ROW_PREPARED)
-#undef PA_ROW_ATTR
+    const int big = 200 * 1024;
+#define PA_ATTR_COL(LLV, TCV)                                                                                   \
+    if ((e = cudaFuncSetAttribute(k_fwd_col<true, LLV, TCV>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) \
+        return e;                                                                                               \
+    if ((e = cudaFuncSetAttribute(k_fwd_col<false, LLV, TCV>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) \
+        return e;                                                                                               \
+    if ((e = cudaFuncSetAttribute(k_inv_col<LLV, TCV>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    PA_FOR_COL_SHAPES(PA_ATTR_COL)
+#undef PA_ATTR_COL
+#define PA_ATTR_ROW(A, LLV)                                                                                          \
+    if ((e = cudaFuncSetAttribute(k_row_mac<A, ROW_PAIRS, LLV>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))    \
+        return e;                                                                                                    \
+    if ((e = cudaFuncSetAttribute(k_row_mac<A, ROW_STORE, LLV>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))    \
+        return e;                                                                                                    \
+    if ((e = cudaFuncSetAttribute(k_row_mac<A, ROW_PREPARED, LLV>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) \
+        return e;
+#define PA_ATTR_ROW8(LLV) PA_ATTR_ROW(8, LLV)
+#define PA_ATTR_ROW16(LLV) PA_ATTR_ROW(16, LLV)
+    PA_FOR_ROW_SHAPES8(PA_ATTR_ROW8)
+    PA_FOR_ROW_SHAPES16(PA_ATTR_ROW16)
+#undef PA_ATTR_ROW8
+#undef PA_ATTR_ROW16
+#undef PA_ATTR_ROW
     done = true;
     return 0;
 }
 
-int launch_fwd_col(const Xform &X, const Operands &S, int num_pairs, u64 *Y, void *stream) {
+template <bool PAIR>
+static int launch_cols(const char *name, const Xform &X, const Operands &S, int count, u64 *Y, void *stream) {
     if (int e = prepare_kernels()) return e;
-    dim3 grid(X.C / X.tc, num_pairs);
-    const size_t smem = 2 * col_smem(X);
-    TRACED("fwd_col", X.stage, stream, (k_fwd_col<true><<<grid, PA_COL_T, smem, (cudaStream_t)stream>>>(X, S, Y)));
-    return (int)cudaGetLastError();
+    dim3 grid(X.C / X.tc, count);
+    const size_t smem = (PAIR ? 2 : 1) * col_smem(X);
+    cudaStream_t s = (cudaStream_t)stream;
+#define PA_LAUNCH_COL(LLV, TCV)                                                                \
+    if ((LLV == 0 && TCV == 0) || (X.logR == (u32)LLV && X.tc == (u32)TCV)) {                  \
+        TRACED(name, X.stage, stream, (k_fwd_col<PAIR, LLV, TCV><<<grid, PA_COL_T, smem, s>>>(X, S, Y))); \
+        return (int)cudaGetLastError();                                                        \
+    }
+    PA_LAUNCH_COL(10, 4)
+    PA_LAUNCH_COL(11, 2)
+    PA_LAUNCH_COL(0, 0)
+#undef PA_LAUNCH_COL
+    return (int)cudaErrorInvalidValue;
+}
+
+int launch_fwd_col(const Xform &X, const Operands &S, int num_pairs, u64 *Y, void *stream) {
+    return launch_cols<true>("fwd_col", X, S, num_pairs, Y, stream);
 }
 
 int launch_fwd_col_single(const Xform &X, const Operands &S, int num_operands, u64 *Y, void *stream) {
-    if (int e = prepare_kernels()) return e;
-    dim3 grid(X.C / X.tc, num_operands);
-    TRACED("fwd_col1", X.stage, stream,
-           (k_fwd_col<false><<<grid, PA_COL_T, col_smem(X), (cudaStream_t)stream>>>(X, S, Y)));
-    return (int)cudaGetLastError();
+    return launch_cols<false>("fwd_col1", X, S, num_operands, Y, stream);
 }
 
 template <int MODE>
 static int launch_rows(const char *name, const Xform &X, const u64 *Y, u64 *Spec, u64 *S, void *stream) {
     if (int e = prepare_kernels()) return e;
+    cudaStream_t s = (cudaStream_t)stream;
     if (X.C > 4096) {
-        TRACED(name, X.stage, stream,
-               (k_row_mac<16, MODE><<<X.R, X.C / 16, row_smem(X), (cudaStream_t)stream>>>(X, Y, Spec, S)));
+        if (X.logC == 13)
+            TRACED(name, X.stage, stream, (k_row_mac<16, MODE, 13><<<X.R, X.C / 16, row_smem(X), s>>>(X, Y, Spec, S)));
+        else
+            TRACED(name, X.stage, stream, (k_row_mac<16, MODE, 0><<<X.R, X.C / 16, row_smem(X), s>>>(X, Y, Spec, S)));
     } else {
         u32 threads = X.C / 8;
         if (threads < 32) threads = 32;
-        TRACED(name, X.stage, stream,
-               (k_row_mac<8, MODE><<<X.R, threads, row_smem(X), (cudaStream_t)stream>>>(X, Y, Spec, S)));
+        if (X.logC == 11)
+            TRACED(name, X.stage, stream, (k_row_mac<8, MODE, 11><<<X.R, threads, row_smem(X), s>>>(X, Y, Spec, S)));
+        else if (X.logC == 12)
+            TRACED(name, X.stage, stream, (k_row_mac<8, MODE, 12><<<X.R, threads, row_smem(X), s>>>(X, Y, Spec, S)));
+        else if (X.logC == 10)
+            TRACED(name, X.stage, stream, (k_row_mac<8, MODE, 10><<<X.R, threads, row_smem(X), s>>>(X, Y, Spec, S)));
+        else
+            TRACED(name, X.stage, stream, (k_row_mac<8, MODE, 0><<<X.R, threads, row_smem(X), s>>>(X, Y, Spec, S)));
     }
     return (int)cudaGetLastError();
 }
@@ -911,9 +953,19 @@ int launch_row_prepared(const Xform &X, const u64 *Y, const u64 *Spec, u64 *S, v
 int launch_inv_col(const Xform &X, const u64 *S, u64 *Z, const u64 *add_src, u64 add_base, u64 add_len,
                    void *stream) {
     if (int e = prepare_kernels()) return e;
-    TRACED("inv_col", X.stage, stream,
-           (k_inv_col<<<X.C / X.tc, PA_COL_T, col_smem(X), (cudaStream_t)stream>>>(X, S, Z, add_src, add_base, add_len)));
-    return (int)cudaGetLastError();
+    cudaStream_t s = (cudaStream_t)stream;
+    const dim3 grid(X.C / X.tc);
+#define PA_LAUNCH_INV(LLV, TCV)                                                                          \
+    if ((LLV == 0 && TCV == 0) || (X.logR == (u32)LLV && X.tc == (u32)TCV)) {                            \
+        TRACED("inv_col", X.stage, stream,                                                               \
+               (k_inv_col<LLV, TCV><<<grid, PA_COL_T, col_smem(X), s>>>(X, S, Z, add_src, add_base, add_len))); \
+        return (int)cudaGetLastError();                                                                  \
+    }
+    PA_LAUNCH_INV(10, 4)
+    PA_LAUNCH_INV(11, 2)
+    PA_LAUNCH_INV(0, 0)
+#undef PA_LAUNCH_INV
+    return (int)cudaErrorInvalidValue;
 }
 
 int launch_carry(const Xform &X, const CarryDev &cd_in, u64 *z, u64 *out_bits, u64 out_words, void *stream) {
