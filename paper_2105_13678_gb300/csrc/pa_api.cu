@@ -220,10 +220,10 @@ static int build_xform(pa_plan_t *pl, Xform &X, uint64_t G, uint64_t K, u32 logR
     const u64 wR = gl_pow(w, X.C), wC = gl_pow(w, X.R);
     int err = PA_OK;
     auto up = [&](const std::vector<u64> &v) { return tabs.upload(v, &err); };
-    X.twR = up(powers(wR, X.R / 2));
-    X.itwR = up(powers(gl_inv(wR), X.R / 2));
-    X.twC = up(powers(wC, X.C / 2));
-    X.itwC = up(powers(gl_inv(wC), X.C / 2));
+    X.twR = up(powers(wR, X.R));
+    X.itwR = up(powers(gl_inv(wR), X.R));
+    X.twC = up(powers(wC, X.C));
+    X.itwC = up(powers(gl_inv(wC), X.C));
     const size_t nlo = (size_t)1 << X.hb, nhi = (size_t)(X.N >> X.hb);
     X.ipw_lo = up(powers(w, nlo));
     X.ipw_hi = up(powers(gl_pow(w, nlo), nhi));

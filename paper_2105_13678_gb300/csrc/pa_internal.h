@@ -90,8 +90,8 @@ struct Xform {
     u32 tc;      // columns per CTA tile in the column passes
     u32 K;       // operand pairs accumulated in the transform domain
     u32 stage;   // 0: MMH (Eq. 2), 1: MH (Eq. 4); used for trace names
-    const u64 *twR, *itwR;           // omega_R^e, omega_R^-e, e < R/2
-    const u64 *twC, *itwC;           // omega_C^e, omega_C^-e, e < C/2
+    const u64 *twR, *itwR;           // omega_R^e, omega_R^-e, e < R
+    const u64 *twC, *itwC;           // omega_C^e, omega_C^-e, e < C
     const u64 *ipw_lo, *ipw_hi;      // omega_N^e (two-level), e < N
     const u64 *iipw_lo, *iipw_hi;    // omega_N^-e
     const u64 *wt_lo, *wt_hi;        // theta^e

@@ -49,11 +49,35 @@ __device__ __forceinline__ u32 read_bits32(const u64 *__restrict__ src, u64 pos,
     return __funnelshift_r(lo, hi, sh) & ((1u << nb) - 1u);
 }
 
-// Radix-2 decimation-in-frequency stages s0 .. s0+NS-1 of a length-L
-// transform on the 2^NS elements base + m*stride held in v (lo = base mod
-// stride).  Stage s pairs (i, i + L/2^(s+1)) with twiddle
-// omega_L^((i mod L/2^(s+1)) * 2^s) (Gentleman-Sande).  When the group holds
-// the final stage (LAST), that stage's twiddles are all 1 and are skipped.
+// Rounds of the in-place transforms.  A round covers stages s0 .. s0+NS-1 of
+// a length-L transform (omega_L = 7^((q-1)/L)) on the 2^NS elements
+// base + m*stride, lo = base mod stride.  Stage s pairs (i, i + L/2^(s+1))
+// with twiddle omega_L^((i mod L/2^(s+1)) * 2^s) (Gentleman-Sande DIF).
+// In the final round of a transform stride = 1 and lo = 0, so its twiddles
+// are the constants omega_8^k: omega_8 = omega_L^(L/8) = -2^24 for every L
+// (2^96 = -1), so omega_8^k = (-1)^k 2^(24k) and the sign swaps the operands
+// of the difference.
+
+// Round rd of a length-2^l transform: the first round takes the 1..3 leftover
+// stages and every later round 3, so the final round is a full radix-8 round.
+__device__ __forceinline__ u32 round_ns(u32 l, u32 rd) { return rd ? 3u : l - 3u * ((l + 2) / 3 - 1); }
+__device__ __forceinline__ u32 round_s0(u32 l, u32 rd) { return rd ? round_ns(l, 0) + 3u * (rd - 1) : 0u; }
+
+// x * 2^(24 k), k = 0..3 (2^72 = 2^40 - 2^8 mod q).
+__device__ __forceinline__ u64 mul_p24(u64 x, int k) {
+    if (k == 1) return gd_mul(x, 1ULL << 24);
+    if (k == 2) return gd_mul(x, 1ULL << 48);
+    if (k == 3) return gd_mul(x, 0x000000FFFFFFFF00ULL);
+    return x;
+}
+
+// x * omega_8^k, k = 0..3.
+__device__ __forceinline__ u64 mul_w8(u64 x, int k) {
+    if (k == 1) return gd_mul(x, 0xFFFFFFFEFF000001ULL);
+    if (k == 3) return gd_mul(x, 0xFFFFFEFF00000101ULL);
+    return mul_p24(x, k);
+}
+
 template <int NS, bool LAST, bool HZ = false>
 __device__ __forceinline__ void dif_regs(u64 (&v)[8], u32 s0, u32 lo, u32 stride, const u64 *__restrict__ tw) {
 #pragma unroll
@@ -63,15 +87,20 @@ __device__ __forceinline__ void dif_regs(u64 (&v)[8], u32 s0, u32 lo, u32 stride
         for (int m = 0; m < (1 << NS); m++) {
             if (m & half) continue;
             const u64 a = v[m], b = v[m + half];
+            const int k = (m & (half - 1)) * (4 / half);  // LAST: twiddle omega_8^k
             if (HZ && sg == 0) {
                 // upper half of the group is zero: (a, 0) -> (a, a w)
-                const u32 e = (lo + (u32)(m & (half - 1)) * stride) << s0;
-                v[m + half] = gd_mul(a, __ldg(tw + e));
+                if (LAST) {
+                    v[m + half] = mul_w8(a, k);
+                } else {
+                    const u32 e = (lo + (u32)(m & (half - 1)) * stride) << s0;
+                    v[m + half] = gd_mul(a, __ldg(tw + e));
+                }
                 continue;
             }
             v[m] = gd_add(a, b);
-            if (LAST && sg == NS - 1) {
-                v[m + half] = gd_sub(a, b);
+            if (LAST) {
+                v[m + half] = mul_p24((k & 1) ? gd_sub(b, a) : gd_sub(a, b), k);
             } else {
                 const u32 e = (lo + (u32)(m & (half - 1)) * stride) << (s0 + sg);
                 v[m + half] = gd_mul(gd_sub(a, b), __ldg(tw + e));
@@ -81,7 +110,8 @@ __device__ __forceinline__ void dif_regs(u64 (&v)[8], u32 s0, u32 lo, u32 stride
 }
 
 // Inverse of dif_regs up to a factor 2 per stage (decimation in time,
-// stages in reverse order, inverse twiddles).
+// stages in reverse order, inverse twiddles; in the final round
+// omega_8^-k = (-1)^(k+1) 2^(24 (4-k)) for k = 1..3).
 template <int NS, bool LAST, bool HO = false>
 __device__ __forceinline__ void dit_regs(u64 (&v)[8], u32 s0, u32 lo, u32 stride, const u64 *__restrict__ itw) {
 #pragma unroll
@@ -92,12 +122,17 @@ __device__ __forceinline__ void dit_regs(u64 (&v)[8], u32 s0, u32 lo, u32 stride
             if (m & half) continue;
             const u64 a = v[m];
             u64 b = v[m + half];
-            if (!(LAST && sg == NS - 1)) {
+            bool neg = false;
+            if (LAST) {
+                const int k = (m & (half - 1)) * (4 / half);
+                if (k) b = mul_p24(b, 4 - k);
+                neg = k == 2;
+            } else {
                 const u32 e = (lo + (u32)(m & (half - 1)) * stride) << (s0 + sg);
                 b = gd_mul(b, __ldg(itw + e));
             }
-            v[m] = gd_add(a, b);
-            if (!(HO && sg == 0)) v[m + half] = gd_sub(a, b);  // HO: upper outputs unused
+            v[m] = neg ? gd_sub(a, b) : gd_add(a, b);
+            if (!(HO && sg == 0)) v[m + half] = neg ? gd_add(a, b) : gd_sub(a, b);  // HO: upper outputs unused
         }
     }
 }
@@ -288,13 +323,13 @@ __global__ void __launch_bounds__(PA_COL_T, 3) k_fwd_col(Xform X, Operands S, u6
         const bool hz = X.stage == 1;
 #pragma unroll(LL > 0 ? 8 : 1)
         for (u32 rd = 0; rd < nr; rd++) {
-            const u32 s0 = 3 * rd, ns = min(3u, l - s0);
+            const u32 s0 = round_s0(l, rd), ns = round_ns(l, rd);
             const bool first = rd == 0, last = rd == nr - 1;
 #define PA_FWD_COL(NSV)                                                                     \
     do {                                                                                    \
-        if (first && hz && NSV == 3 && last)                                                \
+        if (first && hz && last)                                                            \
             fwd_col_round<NSV, PAIR, true, true, true, LL, TC>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones); \
-        else if (first && hz && NSV == 3)                                                   \
+        else if (first && hz)                                                               \
             fwd_col_round<NSV, PAIR, true, false, true, LL, TC>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones); \
         else if (first && last)                                                             \
             fwd_col_round<NSV, PAIR, true, true, false, LL, TC>(X, dx, da, smx, sma, Yx, Ya, c0, s0, ones);   \
@@ -431,7 +466,7 @@ __global__ void __launch_bounds__(512, ACC == 8 ? 2 : 1)
         u64 *spec = Spec + (u64)i * N + (u64)row * C;
 #pragma unroll(LL > 0 ? 8 : 1)
         for (u32 rd = 0; rd < nr; rd++) {
-            const u32 s0 = 3 * rd, ns = min(3u, l - s0);
+            const u32 s0 = round_s0(l, rd), ns = round_ns(l, rd);
             const bool first = rd == 0, last = rd == nr - 1;
 #define PA_ROW_FWD(NSV)                                                                       \
     do {                                                                                      \
@@ -449,7 +484,7 @@ __global__ void __launch_bounds__(512, ACC == 8 ? 2 : 1)
     u64 *Srow = S + (u64)row * C;
 #pragma unroll(LL > 0 ? 8 : 1)
     for (int rd = (int)nr - 1; rd >= 0; rd--) {
-        const u32 s0 = 3 * rd, ns = min(3u, l - s0);
+        const u32 s0 = round_s0(l, rd), ns = round_ns(l, rd);
         const bool from_acc = rd == (int)nr - 1, to_global = rd == 0;
 #define PA_ROW_INV(NSV)                                                        \
     do {                                                                       \
@@ -532,13 +567,13 @@ __global__ void __launch_bounds__(PA_COL_T) k_inv_col(Xform X, const u64 *__rest
     const bool ho = X.stage == 1;
 #pragma unroll(LL > 0 ? 8 : 1)
     for (int rd = (int)nr - 1; rd >= 0; rd--) {
-        const u32 s0 = 3 * rd, ns = min(3u, l - s0);
+        const u32 s0 = round_s0(l, rd), ns = round_ns(l, rd);
         const bool first = rd == (int)nr - 1, last = rd == 0;
 #define PA_INV_COL(NSV)                                                                       \
     do {                                                                                      \
-        if (last && ho && NSV == 3 && first)                                                  \
+        if (last && ho && first)                                                              \
             inv_col_round<NSV, true, true, true, LL, TC>(X, Sg, sm, Z, c0, s0, add_src, add_base, add_len); \
-        else if (last && ho && NSV == 3)                                                      \
+        else if (last && ho)                                                                  \
             inv_col_round<NSV, false, true, true, LL, TC>(X, Sg, sm, Z, c0, s0, add_src, add_base, add_len); \
         else if (first && last)                                                               \
             inv_col_round<NSV, true, true, false, LL, TC>(X, Sg, sm, Z, c0, s0, add_src, add_base, add_len);   \

@@ -124,10 +124,10 @@ void geometry_and_tables(Xform &X, uint64_t G, uint64_t K, uint32_t l, u32 stage
         dst = p;
         jobs.t[nj++] = TableJob{p, base, scale, count};
     };
-    add(X.twR, wR, X.R / 2, 1);
-    add(X.itwR, gl_inv(wR), X.R / 2, 1);
-    add(X.twC, wC, X.C / 2, 1);
-    add(X.itwC, gl_inv(wC), X.C / 2, 1);
+    add(X.twR, wR, X.R, 1);
+    add(X.itwR, gl_inv(wR), X.R, 1);
+    add(X.twC, wC, X.C, 1);
+    add(X.itwC, gl_inv(wC), X.C, 1);
     add(X.ipw_lo, w, nlo, 1);
     add(X.ipw_hi, gl_pow(w, nlo), nhi, 1);
     add(X.iipw_lo, wi, nlo, 1);

@@ -42,6 +42,10 @@ def test_field_constants():
         assert pow(w, 1 << l, Q) == 1
         if l:
             assert pow(w, 1 << (l - 1), Q) == Q - 1
+        if l >= 3:
+            # the radix-8 rounds hard-code omega_8 = -2^24 (and 2^96 = -1)
+            assert pow(w, 1 << (l - 3), Q) == Q - (1 << 24)
+    assert pow(2, 96, Q) == Q - 1
     with pytest.raises(_lib.PAError):
         _lib.field_constants(27)
 
