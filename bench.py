@@ -29,6 +29,7 @@ sys.path.insert(0, ROOT)
 N_BITS = 260_000_000
 RATIO = 0.1
 METRIC = "input-key Mbps at n=2.6e8 bits (plain MMH-MH PA, r=0.1n)"
+BACKEND_NAMES = {1: "goldilocks", 2: "p3"}
 PAPER_MBPS = 261.0  # abstract / Table 6: 261 Mbps at 2.6e8 on an i5-7300HQ (context, other hardware)
 
 
@@ -151,7 +152,45 @@ def _dft_work(length: int, count: int):
     return full + trivial, full, full * (ALU_ADD + ALU_SUB + ALU_MUL) + trivial * (ALU_ADD + ALU_SUB)
 
 
+# Three-prime backend, per 32-bit residue: a DIF butterfly is one add with its
+# [0, 2p) reduction (3 ALU ops) and one difference (1); a DIT butterfly two
+# reduced adds (6); a Montgomery multiply-accumulate 4; a digit read 5.  The
+# multiplies (Shoup and Montgomery products) run on the IMAD (FMA) pipe.
+P3_DIF, P3_DIT, P3_MAC, P3_DIGIT = 4, 6, 4, 5
+
+
+def kernel_model_p3(info, stage: str, kernel: str, geometry=None):
+    gamma, k = info.gamma, info.k
+    if stage == "mmh":
+        T, K = info.mmh_len, k
+        src_bits = info.n_bits + k * gamma
+    else:
+        T, K = info.mh_len, 1
+        src_bits = 2 * gamma
+    logT = int(math.log2(T))
+    logR = geometry[0] if geometry else min(logT // 2, 10)
+    logC = logT - logR
+    R, C = 1 << logR, 1 << logC
+    if kernel == "p3_fwd_col":
+        ops = 3 * 2 * K
+        # first stage: upper half zero (a, 0) -> (a, a w): products only
+        bfly = ops * C * (R // 2) * (logR - 1)
+        return (src_bits / 8 + ops * T * 4, ops * C * (R // 2) * logR + ops * T + ops * T // 2,
+                bfly * P3_DIF + ops * (T // 2) * P3_DIGIT)
+    if kernel == "p3_row_mac":
+        fwd = 3 * 2 * K * R * (C // 2) * logC
+        inv = 3 * R * (C // 2) * logC
+        return (3 * (2 * K + 1) * T * 4, fwd + inv + 3 * K * T * 2 + 3 * T,
+                fwd * P3_DIF + inv * P3_DIT + 3 * K * T * P3_MAC)
+    if kernel == "p3_inv_col":
+        inv = 3 * C * (R // 2) * logR
+        return (2 * 3 * T * 4, inv, inv * P3_DIT)
+    return (None, None, None)
+
+
 def kernel_model(info, stage: str, kernel: str, geometry=None):
+    if kernel.startswith("p3_"):
+        return kernel_model_p3(info, stage, kernel, geometry)
     gamma, k = info.gamma, info.k
     if stage == "mmh":
         N, K = info.mmh_len, k
@@ -242,23 +281,44 @@ def run_gb300(args):
     # per-kernel device time inside the timed region: `trace` (collected above)
     launches_per_step = sum(v[0] for v in trace.values()) / max(1, args.steps)
 
-    # seed reuse: the same block with its hash seed prepared once (pa_seed_prepare)
-    _lib.pa_seed_prepare(plan, dseed.data_ptr(), sp)
+    # the other backend on the same block (same bits), and seed reuse, which
+    # the Goldilocks transforms provide (pa_seed_prepare)
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b_) for a, b_ in ev) / args.steps
+
+    other = _lib.BACKEND_GOLDILOCKS if plan.backend == _lib.BACKEND_P3 else _lib.BACKEND_P3
+    backends = {BACKEND_NAMES[plan.backend]: {"value": round(job_mbps(n, args.steps, 1, total_ms), 1),
+                                              "ms_per_step": round(total_ms / args.steps, 4)}}
+    try:
+        plan_o = _lib.Plan(n, r, tune=bool(args.tune), backend=other)
+        dout_o = torch.zeros_like(dout)
+        o_ms = timed(lambda: _lib.pa_hash(plan_o, dkey.data_ptr(), dseed.data_ptr(), dout_o.data_ptr(),
+                                          dstat.data_ptr(), sp))
+        backends[BACKEND_NAMES[other]] = {"value": round(n / (o_ms / 1e3) / 1e6, 1), "ms_per_step": round(o_ms, 4),
+                                          "same_output": bool(torch.equal(dout, dout_o))}
+        plan_o.close()
+    except _lib.PAError as e:
+        backends[BACKEND_NAMES[other]] = {"unavailable": str(e)}
+    plan_g = plan if plan.backend == _lib.BACKEND_GOLDILOCKS else _lib.Plan(n, r, tune=bool(args.tune),
+                                                                            backend=_lib.BACKEND_GOLDILOCKS)
+    _lib.pa_seed_prepare(plan_g, dseed.data_ptr(), sp)
     dout2 = torch.zeros_like(dout)
-    for _ in range(args.warmup):
-        _lib.pa_hash_prepared(plan, dkey.data_ptr(), dout2.data_ptr(), dstat.data_ptr(), sp)
-    torch.cuda.synchronize()
-    evs2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for e0, e1 in evs2:
-        flush.zero_()
-        e0.record(stream)
-        _lib.pa_hash_prepared(plan, dkey.data_ptr(), dout2.data_ptr(), dstat.data_ptr(), sp)
-        e1.record(stream)
-    torch.cuda.synchronize()
-    prep_ms = sum(a.elapsed_time(b_) for a, b_ in evs2) / args.steps
+    prep_ms = timed(lambda: _lib.pa_hash_prepared(plan_g, dkey.data_ptr(), dout2.data_ptr(), dstat.data_ptr(), sp))
     seed_reuse = {"value": round(n / (prep_ms / 1e3) / 1e6, 1), "unit": "Mbps", "ms_per_step": round(prep_ms, 4),
-                  "same_output": bool(torch.equal(dout, dout2)),
+                  "same_output": bool(torch.equal(dout, dout2)), "backend": "goldilocks",
                   "workload": "same block, hash seed transformed once (pa_seed_prepare), pa_hash_prepared per step"}
+    if plan_g is not plan:
+        plan_g.close()
 
     # end to end through the host-buffer entry point (pinned host memory)
     hkey = torch.from_numpy(key.view(np.int64)).pin_memory()
@@ -299,10 +359,11 @@ def run_gb300(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "u64",
+        "dtype": "u32" if plan.backend == _lib.BACKEND_P3 else "u64",
         "data": "synthetic uniform random key and seed bits (splitmix64 seed 2)",
         "config": {"workload": f"plain single block n={n:.3g} bits, r={args.ratio:g}n={r} (seed 2)",
                    "n_bits": n, "r_bits": r, "gamma": plan.gamma, "k": plan.k,
+                   "backend": BACKEND_NAMES[plan.backend],
                    "mmh_transform_len": info.mmh_len, "mh_transform_len": info.mh_len,
                    "geometry_mmh": plan.geometry(0), "geometry_mh": plan.geometry(1), "autotuned": bool(args.tune),
                    "parallelism": f"replicas x{ws}", "l2": "flushed (256 MB write) between timed steps",
@@ -315,6 +376,7 @@ def run_gb300(args):
                 "d2h_bytes_per_step": int(info.out_words * 8 + 4), "same_output": same},
         "roofline": roof,
         "seed_reuse": seed_reuse,
+        "backends": backends,
         "kernels": {k_: {"launches": v[0], "avg_us": round(1e3 * v[1] / max(1, v[0]), 2)}
                     for k_, v in sorted(trace.items(), key=lambda kv: -kv[1][1])},
         "step_ms_p50": round(statistics.median(step_ms), 4),
@@ -351,7 +413,7 @@ def run_gb300(args):
 def kernel_sources_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("pa_kernels.cu", "gl_device.cuh"):
+    for f in ("pa_kernels.cu", "gl_device.cuh", "pa_p3.cu"):
         with open(os.path.join(ROOT, "paper_2105_13678_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

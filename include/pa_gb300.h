@@ -60,17 +60,32 @@ typedef struct pa_params {
                               workspace at pa_plan time and keep the fastest
                               (cached per process); 0: default geometry.
                               The output bits do not depend on it.           */
-    uint32_t reserved[5];  /* must be zero */
+    uint32_t backend;      /* PA_BACKEND_AUTO (0), PA_BACKEND_GOLDILOCKS or
+                              PA_BACKEND_P3; the output bits do not depend on it */
+    uint32_t reserved[4];  /* must be zero */
 } pa_params;
+
+/* Arithmetic of the exact products (a design choice; the paper fixes only
+ * the results of Eq. 2 and Eq. 4):
+ *   GOLDILOCKS  one transform over q = 2^64 - 2^32 + 1 with the irrational-
+ *               base weighted transform (cyclic mod 2^G - 1 without padding);
+ *   P3          zero-padded transforms over three 30-bit primes, the
+ *               coefficients recovered by the Chinese remainder theorem
+ *               (about half the integer work per transformed element);
+ *               not available with pa_seed_prepare (PA_ERR_UNSUPPORTED);
+ *   AUTO        GOLDILOCKS (the faster of the two on GB300 at present). */
+#define PA_BACKEND_AUTO 0u
+#define PA_BACKEND_GOLDILOCKS 1u
+#define PA_BACKEND_P3 2u
 
 typedef struct pa_plan_info {
     uint64_t n_bits, r_bits;
     uint32_t gamma;           /* Mersenne exponent, p = 2^gamma - 1           */
-    uint32_t reserved0;
+    uint32_t backend;         /* PA_BACKEND_GOLDILOCKS or PA_BACKEND_P3          */
     uint64_t k;               /* segments, ceil(n / gamma)                      */
     uint64_t key_words, seed_words, out_words;
-    uint64_t mmh_len;         /* cyclic transform length for Eq. 2 (mod 2^gamma - 1) */
-    uint64_t mh_len;          /* cyclic transform length for Eq. 4 (mod 2^(2 gamma) - 1) */
+    uint64_t mmh_len;         /* transform length for Eq. 2                      */
+    uint64_t mh_len;          /* transform length for Eq. 4                      */
     uint64_t workspace_bytes; /* device bytes owned by the plan                 */
 } pa_plan_info;
 

@@ -33,11 +33,11 @@ _vp = ctypes.c_void_p
 
 class pa_params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_uint32), ("gamma_margin", ctypes.c_uint32), ("tune", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 5)]
+                ("backend", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 4)]
 
 
 class pa_plan_info(ctypes.Structure):
-    _fields_ = [("n_bits", _u64), ("r_bits", _u64), ("gamma", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
+    _fields_ = [("n_bits", _u64), ("r_bits", _u64), ("gamma", ctypes.c_uint32), ("backend", ctypes.c_uint32),
                 ("k", _u64), ("key_words", _u64), ("seed_words", _u64), ("out_words", _u64),
                 ("mmh_len", _u64), ("mh_len", _u64), ("workspace_bytes", _u64)]
 
@@ -125,11 +125,15 @@ def check(code: int, what: str) -> int:
     return code
 
 
-def params(gamma: int = 0, margin: int = 128, tune: bool = False) -> pa_params:
+BACKEND_AUTO, BACKEND_GOLDILOCKS, BACKEND_P3 = 0, 1, 2
+
+
+def params(gamma: int = 0, margin: int = 128, tune: bool = False, backend: int = BACKEND_AUTO) -> pa_params:
     p = pa_params()
     p.gamma = gamma
     p.gamma_margin = margin
     p.tune = 1 if tune else 0
+    p.backend = backend
     return p
 
 
@@ -138,18 +142,19 @@ class Plan:
     ``modular_hash=True`` builds the comparison scheme (Eq. 4 over the whole key)."""
 
     def __init__(self, n_bits: int, r_bits: int, gamma: int = 0, margin: int = 128, tune: bool = False,
-                 modular_hash: bool = False):
+                 modular_hash: bool = False, backend: int = BACKEND_AUTO):
         h = _vp()
         if modular_hash:
             check(lib().pa_mh_plan(n_bits, r_bits, ctypes.byref(h)), "pa_mh_plan")
         else:
-            p = params(gamma, margin, tune)
+            p = params(gamma, margin, tune, backend)
             check(lib().pa_plan(n_bits, r_bits, ctypes.byref(p), ctypes.byref(h)), "pa_plan")
         self.handle = h
         info = pa_plan_info()
         check(lib().pa_plan_info_get(h, ctypes.byref(info)), "pa_plan_info_get")
         self.info = info
         self.n, self.r, self.gamma, self.k = info.n_bits, info.r_bits, info.gamma, info.k
+        self.backend = info.backend
 
     def geometry(self, stage: int):
         """(log2 R, log2 C, column tile width) of the stage's transform."""
@@ -238,9 +243,9 @@ def transform_len(G: int, K: int) -> int:
     return int(l.value)
 
 
-def plan_estimate_bytes(n: int, r: int, gamma: int = 0, margin: int = 128) -> int:
+def plan_estimate_bytes(n: int, r: int, gamma: int = 0, margin: int = 128, backend: int = BACKEND_AUTO) -> int:
     b = _u64()
-    p = params(gamma, margin)
+    p = params(gamma, margin, backend=backend)
     check(lib().pa_plan_estimate_bytes(n, r, ctypes.byref(p), ctypes.byref(b)), "pa_plan_estimate_bytes")
     return int(b.value)
 
@@ -249,12 +254,12 @@ class Server:
     """``pa_serve_*``: continuous-batching request loop on the current device."""
 
     def __init__(self, hbm_budget_bytes: int, slots: int = 8, max_queue: int = 0, gamma: int = 0,
-                 margin: int = 128, tune: bool = False):
+                 margin: int = 128, tune: bool = False, backend: int = BACKEND_AUTO):
         cfg = pa_serve_config()
         cfg.hbm_budget_bytes = hbm_budget_bytes
         cfg.slots = slots
         cfg.max_queue = max_queue
-        cfg.params = params(gamma, margin, tune)
+        cfg.params = params(gamma, margin, tune, backend)
         h = _vp()
         check(lib().pa_serve_create(ctypes.byref(cfg), ctypes.byref(h)), "pa_serve_create")
         self.handle = h

@@ -125,6 +125,7 @@ struct pa_plan_s {
     uint64_t n, r, k;
     uint32_t gamma;
     bool mh_only = false;   // modular-arithmetic hash over the whole key (gamma = n, k = 0)
+    P3Plan *p3 = nullptr;   // three-prime backend (pa_p3.cu): owns its own workspace
     Xform mmh, mh;
     DevTables tables;
     // workspace
@@ -161,6 +162,7 @@ struct pa_plan_s {
         }
         if (copy_stream) cudaStreamDestroy(copy_stream);
         for (void *p : ws_allocs) cudaFree(p);
+        if (p3) p3_plan_destroy(p3);
     }
     void *alloc(size_t bytes, int *err) {
         void *p = nullptr;
@@ -287,6 +289,25 @@ static WsSizes ws_sizes(uint32_t gamma, uint64_t k, uint64_t N1, uint64_t N2) {
     return z;
 }
 
+// Backend of a plan.  PA_BACKEND_AUTO takes the Goldilocks transforms; the
+// three-prime transforms are opt-in (kAutoP3 off) until they are the faster.
+static int choose_backend(uint32_t gamma, uint64_t k, const pa_params *params, uint32_t l1, int *backend) {
+    const uint32_t want = params ? params->backend : PA_BACKEND_AUTO;
+    if (want > PA_BACKEND_P3) return PA_ERR_INVALID;
+    uint32_t t1 = 0, t2 = 0;
+    const bool p3ok = p3_feasible(gamma, k, &t1, &t2) == PA_OK;
+    if (want == PA_BACKEND_P3) {
+        if (!p3ok) return PA_ERR_UNSUPPORTED;
+        *backend = PA_BACKEND_P3;
+    } else if (want == PA_BACKEND_GOLDILOCKS) {
+        *backend = PA_BACKEND_GOLDILOCKS;
+    } else {
+        constexpr bool kAutoP3 = false;
+        *backend = (kAutoP3 && p3ok && t1 <= l1) ? PA_BACKEND_P3 : PA_BACKEND_GOLDILOCKS;
+    }
+    return PA_OK;
+}
+
 extern "C" {
 
 int pa_plan(uint64_t n_bits, uint64_t r_bits, const pa_params *params, pa_plan_t **out) {
@@ -314,6 +335,24 @@ int pa_plan(uint64_t n_bits, uint64_t r_bits, const pa_params *params, pa_plan_t
     if ((rc = choose_len(gamma, pl->k, &l1)) || (rc = choose_len(2ULL * gamma, 1, &l2))) {
         delete pl;
         return rc;
+    }
+    int backend = PA_BACKEND_GOLDILOCKS;
+    if ((rc = choose_backend(gamma, pl->k, params, l1, &backend))) {
+        delete pl;
+        return rc;
+    }
+    if (backend == PA_BACKEND_P3) {
+        if ((rc = p3_plan_create(n_bits, r_bits, gamma, pl->k, &pl->p3))) {
+            delete pl;
+            return rc;
+        }
+        uint64_t t1 = 0, t2 = 0, ws = 0;
+        p3_plan_query(pl->p3, &t1, &t2, &ws);
+        pl->mmh.N = t1;
+        pl->mh.N = t2;
+        pl->ws_bytes = ws;
+        *out = pl;
+        return PA_OK;
     }
     const WsSizes z = ws_sizes(gamma, pl->k, 1ULL << l1, 1ULL << l2);
     int err = PA_OK;
@@ -401,6 +440,7 @@ int pa_plan_info_get(const pa_plan_t *pl, pa_plan_info *info) {
     info->mmh_len = pl->mmh.N;
     info->mh_len = pl->mh.N;
     info->workspace_bytes = pl->ws_bytes;
+    info->backend = pl->p3 ? PA_BACKEND_P3 : PA_BACKEND_GOLDILOCKS;
     return PA_OK;
 }
 
@@ -514,6 +554,11 @@ int pa_hash(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint64_t *
         if (!e) e = enqueue_mh(pl, (const u64 *)seed, (u64 *)out, status, stream);
         return cuda_rc(e);
     }
+    if (pl->p3) {
+        int e = p3_enqueue_mmh(pl->p3, (const u64 *)key, (const u64 *)seed, p3_ybuf(pl->p3), false, stream);
+        if (!e) e = p3_enqueue_mh(pl->p3, (const u64 *)seed, (u64 *)out, status, stream);
+        return cuda_rc(e);
+    }
     int e = enqueue_mmh(pl, (const u64 *)key, (const u64 *)seed, pl->ybuf, false, stream);
     if (!e) e = enqueue_mh(pl, (const u64 *)seed, (u64 *)out, status, stream);
     return cuda_rc(e);
@@ -522,6 +567,12 @@ int pa_hash(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint64_t *
 int pa_debug_mmh(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint64_t *y, int *status, void *stream) {
     if (!pl || !key || !seed || !y) return PA_ERR_INVALID;
     if (pl->mh_only) return PA_ERR_INVALID;
+    if (pl->p3) {
+        int e = p3_enqueue_mmh(pl->p3, (const u64 *)key, (const u64 *)seed, (u64 *)y, true, stream);
+        if (!e && status)
+            e = cudaMemcpyAsync(status, p3_flags(pl->p3), sizeof(int), cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+        return cuda_rc(e);
+    }
     int e = enqueue_mmh(pl, (const u64 *)key, (const u64 *)seed, (u64 *)y, true, stream);
     if (!e && status) e = cudaMemcpyAsync(status, pl->flags, sizeof(int), cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
     return cuda_rc(e);
@@ -578,6 +629,19 @@ int pa_hash_host_async(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed,
     }
     copy_words(st.dseed, seed, (k * g) / 64, sw);  // b and c
     if (!e) e = cudaEventRecord(st.ready[ng], pl->copy_stream);
+    if (pl->p3) {
+        // three-prime plans start once the whole key and seed have landed
+        if (!e) e = cudaStreamWaitEvent(s, st.ready[ng], 0);
+        for (int q = 0; q < ng && !e; q++) e = cudaStreamWaitEvent(s, st.ready[q], 0);
+        if (!e) e = p3_enqueue_mmh(pl->p3, st.dkey, st.dseed, p3_ybuf(pl->p3), false, stream);
+        if (!e) e = p3_enqueue_mh(pl->p3, st.dseed, st.dout, st.dstatus, stream);
+        if (!e) e = cudaEventRecord(st.free_ev, s);
+        if (!e) e = cudaMemcpyAsync(out, st.dout, ow * 8, cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaMemcpyAsync(status ? status : st.hstatus, st.dstatus, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e) return PA_ERR_CUDA;
+        st.used = true;
+        return PA_OK;
+    }
     if (!e) e = cudaMemsetAsync(pl->flags, 0, pl->flags_bytes, s);
     Operands ops;
     ops.pair0 = 0;
@@ -624,6 +688,7 @@ int pa_hash_host(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint6
 int pa_seed_prepare(pa_plan_t *pl, const uint64_t *seed, void *stream) {
     if (!pl || !seed) return PA_ERR_INVALID;
     if (pl->mh_only) return PA_ERR_INVALID;
+    if (pl->p3) return PA_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     const uint64_t sw = ((pl->k + 2) * pl->gamma + 63) / 64;
     if (!pl->spec_a) {
@@ -806,7 +871,9 @@ int pa_plan_estimate_bytes(uint64_t n_bits, uint64_t r_bits, const pa_params *pa
     if (rc) return rc;
     const uint64_t k = (n_bits + gamma - 1) / gamma;
     if ((rc = choose_len(gamma, k, &l1)) || (rc = choose_len(2ULL * gamma, 1, &l2))) return rc;
-    *bytes = ws_sizes(gamma, k, 1ULL << l1, 1ULL << l2).total();
+    int backend = PA_BACKEND_GOLDILOCKS;
+    if ((rc = choose_backend(gamma, k, params, l1, &backend))) return rc;
+    *bytes = backend == PA_BACKEND_P3 ? p3_plan_bytes(gamma, k) : ws_sizes(gamma, k, 1ULL << l1, 1ULL << l2).total();
     return PA_OK;
 }
 
@@ -827,6 +894,13 @@ int pa_selftest_field(const uint64_t *a, const uint64_t *b, uint64_t *out, uint6
 // Four-step geometry of a plan's transform (stage 0: Eq. 2, 1: Eq. 4).
 int pa_plan_geometry(const pa_plan_t *pl, int stage, uint32_t *log_r, uint32_t *log_c, uint32_t *tile_cols) {
     if (!pl || !log_r || !log_c || !tile_cols || stage < 0 || stage > 1) return PA_ERR_INVALID;
+    if (pl->p3) {
+        const Geo3 *G3 = p3_stage(pl->p3, stage);
+        *log_r = G3->logR;
+        *log_c = G3->logC;
+        *tile_cols = G3->tc;
+        return PA_OK;
+    }
     const Xform &X = stage ? pl->mh : pl->mmh;
     *log_r = X.logR;
     *log_c = X.logC;

@@ -13,6 +13,7 @@
 // needed by Eq. 4 (b*y + c < 2^(2 gamma) - 1).  theta exists for N <= 2^26
 // because 2 has multiplicative order 192 in F_q.
 #pragma once
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 struct pa_params;
@@ -121,6 +122,7 @@ struct Operands {
 struct CarryDev {
     u64 N, G;             // digit geometry of the transform: s_j = ceil(G j / N)
     u32 logN;
+    u32 ub = 0;           // nonzero: uniform digits, s_j = min(j ub, G) (three-prime backend)
     int linear;           // 0: ring mod 2^G - 1 over all N digits; 1: digits [0, nchunks * D) only,
                           //    carry out of the top dropped (the low half of an exact product)
     u64 nchunks;          // digits / PA_CARRY_D
@@ -128,6 +130,24 @@ struct CarryDev {
     unsigned char *state; // chunk G/P state, nchunks
     unsigned char *cta_state, *cta_cin;
     int *allones;         // set when the resolved value is 2^G - 1 (== 0)
+};
+
+// One stage of the three-prime backend (pa_p3.cu): linear convolution of
+// digit vectors of M = T/2 digits of b bits, transform length T = R * C, over
+// the primes p[0..2] (< 2^30, 2^logT | p - 1).  Twiddle tables hold
+// (w, floor(w 2^32 / p)) pairs; device pointers owned by the plan.
+struct Geo3 {
+    u64 T, M;        // transform length, digit slots per operand (T / 2)
+    u64 nd;          // digits holding operand bits: ceil(G / b)
+    u64 G;           // gamma: operand bits, and the modulus 2^G - 1 (Eq. 2) or 2^G (Eq. 4)
+    u64 p01;         // p0 p1
+    u32 logT, logR, logC, R, C, tc, b, K, stage;
+    u32 p[3], pinv[3];          // primes and p^-1 mod 2^32
+    uint2 scale[3], red[3];     // 2^32 / T mod p; (1, floor(2^32 / p))
+    uint2 c12, p0m2, c3;        // p0^-1 mod p1; p0 mod p2; (p0 p1)^-1 mod p2
+    const uint2 *twR[3], *itwR[3];  // omega_R^(+-e), e < R/2
+    const uint2 *twC[3], *itwC[3];  // omega_C^(+-e), e < C/2
+    const uint2 *ctw[3], *ictw[3];  // T entries, [r][c]: omega_T^(+-c bitrev_R(r))
 };
 
 constexpr u32 PA_CARRY_D = 8;      // digits per thread chunk
@@ -144,6 +164,16 @@ int choose_params(uint64_t n_bits, uint64_t r_bits, const struct pa_params *para
 void *trace_begin(const char *name, u32 stage, void *stream);
 void trace_end(void *token, void *stream);
 
+// Every launch goes through TRACED(): when tracing is on (pa_trace_enable) and
+// the stream is not being captured, a CUDA event pair is recorded on the
+// launching stream around the kernel.
+#define TRACED(name, stage, stream, launch)                      \
+    do {                                                         \
+        void *tr_ = trace_begin((name), (stage), (stream));      \
+        launch;                                                  \
+        trace_end(tr_, (stream));                                \
+    } while (0)
+
 // Kernel launch wrappers (pa_kernels.cu).  All return a cudaError_t as int.
 int prepare_kernels();
 int launch_fwd_col(const Xform &X, const Operands &S, int num_pairs, u64 *Y, void *stream);
@@ -155,10 +185,37 @@ int launch_inv_col(const Xform &X, const u64 *S, u64 *Z, const u64 *add_src, u64
                    u64 add_len, void *stream);
 int launch_carry(const Xform &X, const CarryDev &cd, u64 *z, u64 *out_bits, u64 out_words,
                  void *stream);
+// General form: cd.nchunks chunks of PA_CARRY_D digits (any count; ndigits
+// digits for the single-thread path), ring or linear per cd.linear; parallel
+// when there are enough chunks and every chunk spans at least 64 bits.
+int launch_carry_chunks(const CarryDev &cd, u64 ndigits, bool wide_chunks, u32 stage, u64 *z, u64 *out_bits,
+                        u64 out_words, void *stream);
 int launch_extract(const u64 *t, u64 gamma, u64 r, const int *reload, u64 k, u64 *out,
                    int *status, void *stream);
 int launch_canonical_zero(const int *flag, u64 *y, u64 words, void *stream);
 int launch_selftest_field(const u64 *a, const u64 *b, u64 *out, u64 n, void *stream);
 int launch_fill_coltw(const Xform &X, u64 *coltw, void *stream);
+
+// Three-prime backend launchers (pa_p3.cu).
+int p3_prepare_kernels();
+int p3_launch_fwd_col(const Geo3 &X, const Operands &S, int pairs, u32 *Y, void *stream);
+int p3_launch_row_mac(const Geo3 &X, const u32 *Y, u32 *S3, void *stream);
+int p3_launch_inv_col(const Geo3 &X, u32 *S3, void *stream);
+int p3_launch_digits(const Geo3 &X, const u32 *S3, u64 *z, u64 npad, const u64 *c_src, u64 c_base, void *stream);
+int p3_launch_fill_ctw(u32 logR, u32 logC, u32 h, const u32 *lo, const u32 *hi, u32 p, uint2 *out, void *stream);
+
+// Three-prime plans (pa_p3.cu).
+struct P3Plan;
+int p3_feasible(uint32_t gamma, uint64_t k, uint32_t *logT_mmh, uint32_t *logT_mh);
+uint64_t p3_plan_bytes(uint32_t gamma, uint64_t k);
+int p3_plan_create(uint64_t n, uint64_t r, uint32_t gamma, uint64_t k, P3Plan **out);
+void p3_plan_destroy(P3Plan *pl);
+void p3_plan_query(const P3Plan *pl, uint64_t *len_mmh, uint64_t *len_mh, uint64_t *ws_bytes);
+const Geo3 *p3_stage(const P3Plan *pl, int stage);
+int p3_enqueue_mmh(P3Plan *pl, const u64 *key, const u64 *seed, u64 *y, bool canonical, void *stream);
+int p3_enqueue_mh(P3Plan *pl, const u64 *seed, u64 *out, int *status, void *stream);
+u64 *p3_ybuf(P3Plan *pl);
+int *p3_flags(P3Plan *pl);
+size_t p3_flags_bytes(const P3Plan *pl);
 
 }  // namespace pa

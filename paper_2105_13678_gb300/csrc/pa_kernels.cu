@@ -601,9 +601,15 @@ __global__ void __launch_bounds__(PA_COL_T) k_inv_col(Xform X, const u64 *__rest
 // resolves the CTA-level generate/propagate chain around the ring.  Phase C:
 // every chunk receiving a carry increments its bit range.
 
-__device__ __forceinline__ u32 digit_bits(const CarryDev &cd, u64 j) {
-    return (u32)(digit_start(cd.G, j + 1, cd.N, cd.logN) - digit_start(cd.G, j, cd.N, cd.logN));
+__device__ __forceinline__ u64 cd_start(const CarryDev &cd, u64 j) {
+    if (cd.ub) {
+        const u64 s = j * cd.ub;
+        return s < cd.G ? s : cd.G;
+    }
+    return digit_start(cd.G, j, cd.N, cd.logN);
 }
+
+__device__ __forceinline__ u32 digit_bits(const CarryDev &cd, u64 j) { return (u32)(cd_start(cd, j + 1) - cd_start(cd, j)); }
 
 __device__ __forceinline__ u64 chunk_carry_out(const CarryDev &cd, const u64 *__restrict__ z, u64 t) {
     const u64 j0 = t * PA_CARRY_D;
@@ -621,7 +627,8 @@ __global__ void __launch_bounds__(PA_CARRY_T) k_carry_a(CarryDev cd, const u64 *
     __shared__ u64 Hprev;
     __shared__ unsigned wg[PA_CARRY_T / 32], wp[PA_CARRY_T / 32];
     const u64 t = (u64)blockIdx.x * PA_CARRY_T + threadIdx.x;
-    const u64 j0 = t * PA_CARRY_D;
+    const bool act = t < cd.nchunks;  // the last CTA may hold fewer chunks; the rest propagate
+    const u64 j0 = act ? t * PA_CARRY_D : 0;
     u64 zz[PA_CARRY_D];
     u32 bd[PA_CARRY_D];
     const ulonglong2 *z2 = reinterpret_cast<const ulonglong2 *>(z + j0);  // j0 is a multiple of 8
@@ -631,11 +638,11 @@ __global__ void __launch_bounds__(PA_CARRY_T) k_carry_a(CarryDev cd, const u64 *
         zz[2 * d] = w.x;
         zz[2 * d + 1] = w.y;
     }
-    u64 s = digit_start(cd.G, j0, cd.N, cd.logN);
+    u64 s = cd_start(cd, j0);
     const u64 s_begin = s;
 #pragma unroll
     for (u32 d = 0; d < PA_CARRY_D; d++) {
-        const u64 s1 = digit_start(cd.G, j0 + d + 1, cd.N, cd.logN);
+        const u64 s1 = cd_start(cd, j0 + d + 1);
         bd[d] = (u32)(s1 - s);
         s = s1;
     }
@@ -666,7 +673,7 @@ __global__ void __launch_bounds__(PA_CARRY_T) k_carry_a(CarryDev cd, const u64 *
         wv |= bits << bo;
         const u32 nb = bo + bd[d];
         if (nb >= 64) {
-            atomicOr(y + wi, wv);
+            if (act) atomicOr(y + wi, wv);
             wi++;
             wv = (nb > 64) ? (bits >> (64 - bo)) : 0;
             bo = nb - 64;
@@ -674,10 +681,10 @@ __global__ void __launch_bounds__(PA_CARRY_T) k_carry_a(CarryDev cd, const u64 *
             bo = nb;
         }
     }
-    if (bo) atomicOr(y + wi, wv);
-    const bool g = (u64)acc != Ht;  // acc == H_t + (carry from adding H_{t-1})
-    const bool p = !g && ones;
-    cd.state[t] = (unsigned char)((g ? 1 : 0) | (p ? 2 : 0));
+    if (bo && act) atomicOr(y + wi, wv);
+    const bool g = act && (u64)acc != Ht;  // acc == H_t + (carry from adding H_{t-1})
+    const bool p = !act || (!g && ones);
+    if (act) cd.state[t] = (unsigned char)((g ? 1 : 0) | (p ? 2 : 0));
 
     const unsigned gm = __ballot_sync(0xFFFFFFFFu, g), pm = __ballot_sync(0xFFFFFFFFu, p);
     if ((threadIdx.x & 31) == 0) {
@@ -738,7 +745,8 @@ __global__ void __launch_bounds__(1024) k_carry_b(CarryDev cd, u32 nctas) {
 __global__ void __launch_bounds__(PA_CARRY_T) k_carry_c(CarryDev cd, u64 *__restrict__ y) {
     __shared__ unsigned wg[PA_CARRY_T / 32], wp[PA_CARRY_T / 32];
     const u64 t = (u64)blockIdx.x * PA_CARRY_T + threadIdx.x;
-    const unsigned st = cd.state[t];
+    const bool act = t < cd.nchunks;
+    const unsigned st = act ? cd.state[t] : 2u;
     const unsigned gm = __ballot_sync(0xFFFFFFFFu, st & 1), pm = __ballot_sync(0xFFFFFFFFu, (st >> 1) & 1);
     const u32 lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
@@ -752,8 +760,8 @@ __global__ void __launch_bounds__(PA_CARRY_T) k_carry_c(CarryDev cd, u64 *__rest
     const bool e = ((sum ^ a ^ gm) >> lane) & 1;
 
     const u64 j0 = t * PA_CARRY_D;
-    const u64 s_lo = digit_start(cd.G, j0, cd.N, cd.logN);
-    const u64 s_hi = digit_start(cd.G, j0 + PA_CARRY_D, cd.N, cd.logN);
+    const u64 s_lo = act ? cd_start(cd, j0) : 0;
+    const u64 s_hi = act ? cd_start(cd, j0 + PA_CARRY_D) : 0;
     bool fin_ones = true, flipping = e;
     for (u64 wi = s_lo >> 6; (wi << 6) < s_hi; wi++) {
         const u64 wb = wi << 6;
@@ -796,7 +804,7 @@ __global__ void k_carry_seq(CarryDev cd, u64 ndigits, u64 *__restrict__ z, u64 *
     bool ones = true;
     for (u64 j = 0; j < ndigits; j++) {
         const u32 b = digit_bits(cd, j);
-        const u64 s = digit_start(cd.G, j, cd.N, cd.logN);
+        const u64 s = cd_start(cd, j);
         ones = ones && z[j] == ((1ULL << b) - 1);
         if (b) {
             y[s >> 6] |= z[j] << (s & 63);
@@ -871,17 +879,7 @@ int launch_selftest_field(const u64 *a, const u64 *b, u64 *out, u64 n, void *str
 // -------------------------------------------------------------- launchers --
 
 static inline u32 pidx_host(u32 i) { return i + (i >> 4); }
-//
-// Every launch goes through TRACED(): when tracing is on (pa_trace_enable) and
-// the stream is not being captured, a CUDA event pair is recorded on the
-// launching stream around the kernel.
 
-#define TRACED(name, stage, stream, launch)                      \
-    do {                                                         \
-        void *tr_ = trace_begin((name), (stage), (stream));      \
-        launch;                                                  \
-        trace_end(tr_, (stream));                                \
-    } while (0)
 
 static size_t col_smem(const Xform &X) { return (size_t)pidx_host(X.R * X.tc) * sizeof(u64); }
 static size_t row_smem(const Xform &X) { return (size_t)2 * pidx_host(X.C) * sizeof(u64); }
@@ -1003,27 +1001,33 @@ int launch_inv_col(const Xform &X, const u64 *S, u64 *Z, const u64 *add_src, u64
     return (int)cudaErrorInvalidValue;
 }
 
-int launch_carry(const Xform &X, const CarryDev &cd_in, u64 *z, u64 *out_bits, u64 out_words, void *stream) {
+int launch_carry_chunks(const CarryDev &cd, u64 ndigits, bool wide_chunks, u32 stage, u64 *z, u64 *out_bits,
+                        u64 out_words, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(out_bits, 0, out_words * sizeof(u64), s);
     if (e) return e;
+    // chunks of PA_CARRY_D digits must span >= 64 bits so that adding the
+    // previous chunk's carry-out leaves a 1-bit carry
+    const bool parallel = cd.nchunks >= PA_CARRY_T && wide_chunks;
+    if (!parallel) {
+        TRACED("carry_seq", stage, stream, (k_carry_seq<<<1, 32, 0, s>>>(cd, ndigits, z, out_bits)));
+        return (int)cudaGetLastError();
+    }
+    const u32 nctas = (u32)((cd.nchunks + PA_CARRY_T - 1) / PA_CARRY_T);
+    TRACED("carry_a", stage, stream, (k_carry_a<<<nctas, PA_CARRY_T, 0, s>>>(cd, z, out_bits)));
+    TRACED("carry_b", stage, stream, (k_carry_b<<<1, 1024, 0, s>>>(cd, nctas)));
+    TRACED("carry_c", stage, stream, (k_carry_c<<<nctas, PA_CARRY_T, 0, s>>>(cd, out_bits)));
+    return (int)cudaGetLastError();
+}
+
+int launch_carry(const Xform &X, const CarryDev &cd_in, u64 *z, u64 *out_bits, u64 out_words, void *stream) {
     // MH stage: only digits [0, N/2) hold bits below gamma; resolve them linearly
     CarryDev cd = cd_in;
+    cd.ub = 0;
     const u64 ndigits = (X.stage == 1 && X.N >= 2) ? X.N / 2 : X.N;
     cd.linear = (X.stage == 1 && X.N >= 2) ? 1 : 0;
     cd.nchunks = ndigits / PA_CARRY_D;
-    // chunks of PA_CARRY_D digits must span >= 64 bits so that adding the
-    // previous chunk's carry-out leaves a 1-bit carry
-    const bool parallel = cd.nchunks >= PA_CARRY_T && (X.G >> X.logN) * PA_CARRY_D >= 64;
-    if (!parallel) {
-        TRACED("carry_seq", X.stage, stream, (k_carry_seq<<<1, 32, 0, s>>>(cd, ndigits, z, out_bits)));
-        return (int)cudaGetLastError();
-    }
-    const u32 nctas = (u32)(cd.nchunks / PA_CARRY_T);
-    TRACED("carry_a", X.stage, stream, (k_carry_a<<<nctas, PA_CARRY_T, 0, s>>>(cd, z, out_bits)));
-    TRACED("carry_b", X.stage, stream, (k_carry_b<<<1, 1024, 0, s>>>(cd, nctas)));
-    TRACED("carry_c", X.stage, stream, (k_carry_c<<<nctas, PA_CARRY_T, 0, s>>>(cd, out_bits)));
-    return (int)cudaGetLastError();
+    return launch_carry_chunks(cd, ndigits, (X.G >> X.logN) * PA_CARRY_D >= 64, X.stage, z, out_bits, out_words, stream);
 }
 
 int launch_extract(const u64 *t, u64 gamma, u64 r, const int *reload, u64 k, u64 *out, int *status, void *stream) {

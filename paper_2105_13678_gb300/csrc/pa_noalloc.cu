@@ -164,6 +164,8 @@ extern "C" int pa_hash_noalloc(uint64_t n_bits, uint64_t r_bits, const pa_params
     if (params) {
         for (uint32_t v : params->reserved)
             if (v) return PA_ERR_INVALID;
+        if (params->backend > PA_BACKEND_P3) return PA_ERR_INVALID;
+        if (params->backend == PA_BACKEND_P3) return PA_ERR_UNSUPPORTED;  // Goldilocks transforms only
     }
     uint32_t gamma, l1, l2;
     uint64_t k;

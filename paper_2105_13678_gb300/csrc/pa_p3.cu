@@ -1,0 +1,943 @@
+// pa_p3.cu -- the three-prime backend: Eq. 2 and Eq. 4 as exact linear
+// convolutions over three 30-bit NTT primes, recombined by the Chinese
+// remainder theorem.
+//
+// Each operand (a gamma-bit integer) is cut into M = T/2 digits of b bits at
+// bit offsets t*b; the upper half of every length-T transform is zero, so the
+// cyclic convolution of two digit vectors is their linear convolution.  A
+// coefficient S_e = sum_i sum_{u+v=e} x_{i,u} a_{i,v} is below
+// K M (2^b - 1)^2 < p0 p1 p2, so its three residues determine it exactly
+// (Garner's algorithm).  The Mersenne reduction of Eq. 2 then places bit
+// offset o at o mod gamma (2^gamma = 1 mod 2^gamma - 1); Eq. 4 keeps the
+// offsets below gamma (mod 2^gamma).  The digit vector that results is
+// resolved by the carry kernels of pa_kernels.cu (uniform-offset mode).
+//
+// Arithmetic per prime p < 2^30 (4p < 2^32): values live in [0, 2p);
+// twiddles w come with w' = floor(w 2^32 / p) and x w mod p is
+// x w - floor(x w' / 2^32) p in [0, 2p) (Shoup); the transform-domain
+// product of two variable spectra is a Montgomery product (factor 2^-32,
+// removed with the 1/T scaling before the CRT).
+//
+// Data layout: Y[(j * 2K + o) * T + e] (u32) holds operand o's spectrum for
+// prime j, o < K the key slices x_i, o >= K the seed slices a_i (or y, b
+// for Eq. 4); S3[j * T + e] the accumulated spectrum and, after the inverse
+// column pass, the coefficients' residues.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "../../include/pa_gb300.h"
+#include "pa_internal.h"
+
+namespace pa {
+namespace p3 {
+
+constexpr u32 kColThreads = 256;
+
+// ------------------------------------------------------------ device math --
+
+__device__ __forceinline__ u32 px(u32 i) { return i + (i >> 3); }  // 1 pad word per 8
+__device__ __forceinline__ u32 brev(u32 x, u32 bits) { return bits ? (__brev(x) >> (32 - bits)) : 0u; }
+__device__ __forceinline__ u32 red2(u32 x, u32 p2) { return min(x, x - p2); }  // [0, 4p) -> [0, 2p)
+__device__ __forceinline__ u32 canon(u32 x, u32 p) { return min(x, x - p); }   // [0, 2p) -> [0, p)
+// x w mod p in [0, 2p) for any x < 2^32 (w < p, w' = floor(w 2^32 / p))
+__device__ __forceinline__ u32 shoup(u32 x, uint2 w, u32 p) { return x * w.x - __umulhi(x, w.y) * p; }
+// a b 2^-32 mod p in (0, 2p) for a, b < 2p: with m = lo(a b) p^-1 mod 2^32 the
+// low words of a b and m p agree, so (a b - m p) / 2^32 = hi(a b) - hi(m p).
+__device__ __forceinline__ u32 mont(u32 a, u32 b, u32 p, u32 pinv) {
+    const u32 lo = a * b, hi = __umulhi(a, b);
+    return hi - __umulhi(lo * pinv, p) + p;
+}
+
+__device__ __forceinline__ u32 rd32(const u64 *__restrict__ src, u64 pos, u32 nb) {
+    const u32 *s32 = reinterpret_cast<const u32 *>(src);
+    const u64 wi = pos >> 5;
+    const u32 sh = (u32)(pos & 31);
+    const u32 lo = __ldg(s32 + wi);
+    const u32 hi = (sh + nb > 32) ? __ldg(s32 + wi + 1) : 0u;
+    return __funnelshift_r(lo, hi, sh) & (nb >= 32 ? 0xFFFFFFFFu : ((1u << nb) - 1u));
+}
+
+// Round rd of a length-2^l transform: the first round takes the leftover
+// 1..3 stages, every later round 3 (the final round has stride 1, lo = 0).
+__device__ __forceinline__ u32 round_ns(u32 l, u32 rd) { return rd ? 3u : l - 3u * ((l + 2) / 3 - 1); }
+__device__ __forceinline__ u32 round_s0(u32 l, u32 rd) { return rd ? round_ns(l, 0) + 3u * (rd - 1) : 0u; }
+
+// Radix-2 DIF stages s0 .. s0+NS-1 of a length-L transform on the elements
+// base + m*stride (lo = base mod stride); stage s pairs (i, i + L/2^(s+1))
+// with twiddle omega_L^((i mod L/2^(s+1)) 2^s).  HZ: the upper half of the
+// group is zero on entry.  In the final round (LAST) the twiddles of the
+// pairs with i mod L/2^(s+1) = 0 are 1.
+template <int NS, bool LAST, bool HZ>
+__device__ __forceinline__ void dif3(u32 (&v)[8], u32 s0, u32 lo, u32 stride, const uint2 *__restrict__ tw, u32 p) {
+    const u32 p2 = 2 * p;
+#pragma unroll
+    for (int sg = 0; sg < NS; sg++) {
+        const int half = 1 << (NS - 1 - sg);
+#pragma unroll
+        for (int m = 0; m < (1 << NS); m++) {
+            if (m & half) continue;
+            const u32 jj = (u32)(m & (half - 1));
+            const bool one = LAST && jj == 0;
+            const u32 e = (lo + jj * stride) << (s0 + sg);
+            const u32 a = v[m], b = v[m + half];
+            if (HZ && sg == 0) {
+                v[m + half] = one ? a : shoup(a, __ldg(tw + e), p);
+                continue;
+            }
+            v[m] = red2(a + b, p2);
+            const u32 d = a - b + p2;
+            v[m + half] = one ? red2(d, p2) : shoup(d, __ldg(tw + e), p);
+        }
+    }
+}
+
+// Inverse of dif3 up to a factor 2^NS (DIT, stages reversed, inverse
+// twiddles).  HO: the upper outputs of the last stage are not needed.
+template <int NS, bool LAST, bool HO>
+__device__ __forceinline__ void dit3(u32 (&v)[8], u32 s0, u32 lo, u32 stride, const uint2 *__restrict__ itw, u32 p) {
+    const u32 p2 = 2 * p;
+#pragma unroll
+    for (int sg = NS - 1; sg >= 0; sg--) {
+        const int half = 1 << (NS - 1 - sg);
+#pragma unroll
+        for (int m = 0; m < (1 << NS); m++) {
+            if (m & half) continue;
+            const u32 jj = (u32)(m & (half - 1));
+            const bool one = LAST && jj == 0;
+            const u32 e = (lo + jj * stride) << (s0 + sg);
+            const u32 a = v[m];
+            const u32 t = one ? v[m + half] : shoup(v[m + half], __ldg(itw + e), p);
+            v[m] = red2(a + t, p2);
+            if (!(HO && sg == 0)) v[m + half] = red2(a - t + p2, p2);
+        }
+    }
+}
+
+#define P3_DISPATCH_NS(ns, F) \
+    do {                      \
+        if ((ns) == 3)        \
+            F(3);             \
+        else if ((ns) == 2)   \
+            F(2);             \
+        else                  \
+            F(1);             \
+    } while (0)
+
+// ---------------------------------------------------------------- operands --
+
+struct Desc {
+    const u64 *src;
+    u64 base, len;  // operand = bits [base, base + len) of src
+    int force_odd, check_ones, zero;
+};
+
+// Algorithm 1 slices: pair i of Eq. 2 is (x_{i+1}, a_{i+1}); the pair of
+// Eq. 4 is (y, b) with b forced odd.
+__device__ __forceinline__ void descs(const Operands &S, u32 i, Desc &dx, Desc &da) {
+    dx.force_odd = da.force_odd = 0;
+    dx.check_ones = da.check_ones = 0;
+    dx.zero = da.zero = 0;
+    if (S.mode == 0) {
+        dx.src = S.key;
+        dx.base = (u64)i * S.gamma;
+        const u64 rem = S.n - dx.base;
+        dx.len = rem < S.gamma ? rem : S.gamma;
+        dx.check_ones = 1;
+        da.src = S.seed;
+        da.base = (u64)i * S.gamma;
+        da.len = S.gamma;
+    } else {
+        dx.src = S.y;
+        dx.base = 0;
+        dx.len = S.gamma;
+        dx.zero = (*S.y_zero != 0);
+        da.src = S.seed;
+        da.base = S.k * S.gamma;
+        da.len = S.gamma;
+        da.force_odd = 1;
+    }
+}
+
+// Digit e (bits [e b, (e+1) b) of the operand), reduced into [0, 2p).
+__device__ __forceinline__ u32 digit(const Geo3 &X, const Desc &d, u64 e, uint2 red, u32 p, bool &ones) {
+    const u64 pos = e * X.b;
+    if (d.zero || pos >= d.len) {
+        if (d.check_ones && pos < X.G) ones = false;  // zero padding below gamma: not all ones
+        return 0;
+    }
+    const u64 left = d.len - pos;
+    const u32 nb = left < X.b ? (u32)left : X.b;
+    u32 v = rd32(d.src, d.base + pos, nb);
+    if (d.check_ones) ones = ones && (v == (nb >= 32 ? 0xFFFFFFFFu : (1u << nb) - 1u));
+    if (d.force_odd && e == 0) v |= 1u;
+    return shoup(v, red, p);
+}
+
+// ------------------------------------------------------------ column pass --
+
+template <int NS, bool PAIR, bool FIRST, bool LAST>
+__device__ __forceinline__ void fwd3_round(const Geo3 &X, u32 j, const Desc &dx, const Desc &da, u32 *__restrict__ smx,
+                                           u32 *__restrict__ sma, u32 *__restrict__ Yx, u32 *__restrict__ Ya, u32 c0,
+                                           u32 s0, bool &ones) {
+    const u32 l = X.logR, tc = X.tc, p = X.p[j];
+    const u32 sh = l - s0 - NS, stride = 1u << sh;
+    const u32 ntask = (X.R >> NS) * tc;
+    const u32 logtc = __ffs(tc) - 1;
+    const uint2 red = X.red[j];
+    for (u32 task = threadIdx.x; task < ntask; task += blockDim.x) {
+        const u32 c = task & (tc - 1), g = task >> logtc;
+        const u32 lo = g & (stride - 1), base = ((g >> sh) << (l - s0)) + lo;
+        u32 vx[8], va[8];
+#pragma unroll
+        for (int m = 0; m < (1 << NS); m++) {
+            const u32 r = base + m * stride;
+            if (FIRST && m >= (1 << (NS - 1))) {  // rows >= R/2: digit slots >= T/2 are zero
+                vx[m] = 0;
+                va[m] = 0;
+            } else if (FIRST) {
+                const u64 e = (u64)r * X.C + c0 + c;
+                vx[m] = digit(X, dx, e, red, p, ones);
+                if (PAIR) va[m] = digit(X, da, e, red, p, ones);
+            } else {
+                vx[m] = smx[px(r * tc + c)];
+                if (PAIR) va[m] = sma[px(r * tc + c)];
+            }
+        }
+        dif3<NS, LAST, FIRST>(vx, s0, lo, stride, X.twR[j], p);
+        if (PAIR) dif3<NS, LAST, FIRST>(va, s0, lo, stride, X.twR[j], p);
+#pragma unroll
+        for (int m = 0; m < (1 << NS); m++) {
+            const u32 r = base + m * stride;
+            if (LAST) {
+                // position r holds column frequency bitrev(r): times omega_T^(c bitrev(r))
+                const u64 e = (u64)r * X.C + c0 + c;
+                const uint2 t = __ldg(X.ctw[j] + e);
+                Yx[e] = shoup(vx[m], t, p);
+                if (PAIR) Ya[e] = shoup(va[m], t, p);
+            } else {
+                smx[px(r * tc + c)] = vx[m];
+                if (PAIR) sma[px(r * tc + c)] = va[m];
+            }
+        }
+    }
+}
+
+// grid (C / tc, pairs, 3 primes): a tile of tc columns of pair blockIdx.y + pair0.
+template <bool PAIR>
+__global__ void __launch_bounds__(kColThreads) k3_fwd_col(Geo3 X, Operands S, u32 *__restrict__ Y) {
+    extern __shared__ u32 sm3[];
+    const u32 j = blockIdx.z, tc = X.tc, c0 = blockIdx.x * tc, i = blockIdx.y + S.pair0;
+    Desc dx, da;
+    descs(S, i, dx, da);
+    if (j) dx.check_ones = 0;
+    u32 *Yx = Y + ((u64)j * 2 * X.K + i) * X.T, *Ya = Y + ((u64)j * 2 * X.K + X.K + i) * X.T;
+    u32 *smx = sm3, *sma = sm3 + px(X.R * tc);
+    bool ones = true;
+    const u32 l = X.logR, nr = (l + 2) / 3;
+    for (u32 rd = 0; rd < nr; rd++) {
+        const u32 s0 = round_s0(l, rd), ns = round_ns(l, rd);
+        const bool first = rd == 0, last = rd == nr - 1;
+#define P3_FWD(NSV)                                                                                   \
+    do {                                                                                              \
+        if (first)                                                                                    \
+            fwd3_round<NSV, PAIR, true, false>(X, j, dx, da, smx, sma, Yx, Ya, c0, s0, ones);         \
+        else if (last)                                                                                \
+            fwd3_round<NSV, PAIR, false, true>(X, j, dx, da, smx, sma, Yx, Ya, c0, s0, ones);         \
+        else                                                                                          \
+            fwd3_round<NSV, PAIR, false, false>(X, j, dx, da, smx, sma, Yx, Ya, c0, s0, ones);        \
+    } while (0)
+        P3_DISPATCH_NS(ns, P3_FWD);
+#undef P3_FWD
+        __syncthreads();
+    }
+    if (dx.check_ones) {
+        // Algorithm 1 reload rule: slice i is all ones iff every CTA of the slice saw only ones
+        const int all = __syncthreads_and(ones ? 1 : 0);
+        if (threadIdx.x == 0 && all) {
+            int *cnt = S.reload + 4 + i;
+            if (atomicAdd(cnt, 1) + 1 == (int)gridDim.x) atomicExch(S.reload, 1);
+        }
+    }
+}
+
+// --------------------------------------------------- rows + MAC (Eq. 2) --
+
+template <int NS, int ACC, bool LAST>
+__device__ __forceinline__ void row_fwd3(const Geo3 &X, u32 j, const u32 *__restrict__ xrow,
+                                         const u32 *__restrict__ arow, u32 *__restrict__ smx, u32 *__restrict__ sma,
+                                         u32 s0, bool first, u32 (&acc)[ACC]) {
+    const u32 l = X.logC, sh = l - s0 - NS, stride = 1u << sh, ngroups = X.C >> NS, p = X.p[j], pinv = X.pinv[j];
+#pragma unroll
+    for (int t = 0; t < (ACC >> NS); t++) {
+        const u32 g = threadIdx.x + t * blockDim.x;
+        if (g < ngroups) {
+            const u32 lo = g & (stride - 1), base = ((g >> sh) << (l - s0)) + lo;
+            u32 vx[8], va[8];
+#pragma unroll
+            for (int m = 0; m < (1 << NS); m++) {
+                const u32 idx = base + m * stride;
+                vx[m] = first ? __ldg(xrow + idx) : smx[px(idx)];
+                va[m] = first ? __ldg(arow + idx) : sma[px(idx)];
+            }
+            dif3<NS, LAST, false>(vx, s0, lo, stride, X.twC[j], p);
+            dif3<NS, LAST, false>(va, s0, lo, stride, X.twC[j], p);
+#pragma unroll
+            for (int m = 0; m < (1 << NS); m++) {
+                if (LAST) {
+                    u32 &a = acc[t * (1 << NS) + m];
+                    a = red2(a + mont(vx[m], va[m], p, pinv), 2 * p);
+                } else {
+                    const u32 idx = base + m * stride;
+                    smx[px(idx)] = vx[m];
+                    sma[px(idx)] = va[m];
+                }
+            }
+        }
+    }
+}
+
+template <int NS, int ACC, bool LAST>
+__device__ __forceinline__ void row_inv3(const Geo3 &X, u32 j, u32 *__restrict__ sm, u32 *__restrict__ Srow, u32 row,
+                                         u32 s0, bool to_global, const u32 (&acc)[ACC]) {
+    const u32 l = X.logC, sh = l - s0 - NS, stride = 1u << sh, ngroups = X.C >> NS, p = X.p[j];
+    const uint2 *ictw = X.ictw[j] + (u64)row * X.C;
+#pragma unroll
+    for (int t = 0; t < (ACC >> NS); t++) {
+        const u32 g = threadIdx.x + t * blockDim.x;
+        if (g < ngroups) {
+            const u32 lo = g & (stride - 1), base = ((g >> sh) << (l - s0)) + lo;
+            u32 v[8];
+#pragma unroll
+            for (int m = 0; m < (1 << NS); m++) v[m] = LAST ? acc[t * (1 << NS) + m] : sm[px(base + m * stride)];
+            dit3<NS, LAST, false>(v, s0, lo, stride, X.itwC[j], p);
+#pragma unroll
+            for (int m = 0; m < (1 << NS); m++) {
+                const u32 idx = base + m * stride;
+                if (to_global)
+                    Srow[idx] = shoup(v[m], __ldg(ictw + idx), p);  // omega_T^(-c bitrev(row))
+                else
+                    sm[px(idx)] = v[m];
+            }
+        }
+    }
+}
+
+// grid (R, 3 primes); blockDim = C / ACC threads, ACC accumulators each.
+template <int ACC>
+__global__ void __launch_bounds__(1024) k3_row_mac(Geo3 X, const u32 *__restrict__ Y, u32 *__restrict__ S3) {
+    extern __shared__ u32 sm3[];
+    const u32 j = blockIdx.y, row = blockIdx.x, C = X.C, l = X.logC;
+    u32 *smx = sm3, *sma = sm3 + px(C);
+    u32 acc[ACC];
+#pragma unroll
+    for (int m = 0; m < ACC; m++) acc[m] = 0;
+    const u32 nr = (l + 2) / 3;
+    for (u32 i = 0; i < X.K; i++) {
+        const u32 *xrow = Y + ((u64)j * 2 * X.K + i) * X.T + (u64)row * C;
+        const u32 *arow = Y + ((u64)j * 2 * X.K + X.K + i) * X.T + (u64)row * C;
+        for (u32 rd = 0; rd < nr; rd++) {
+            const u32 s0 = round_s0(l, rd), ns = round_ns(l, rd);
+            const bool first = rd == 0, last = rd == nr - 1;
+#define P3_ROWF(NSV)                                                                \
+    do {                                                                            \
+        if (last)                                                                   \
+            row_fwd3<NSV, ACC, true>(X, j, xrow, arow, smx, sma, s0, first, acc);   \
+        else                                                                        \
+            row_fwd3<NSV, ACC, false>(X, j, xrow, arow, smx, sma, s0, first, acc);  \
+    } while (0)
+            P3_DISPATCH_NS(ns, P3_ROWF);
+#undef P3_ROWF
+            __syncthreads();
+        }
+    }
+    u32 *Srow = S3 + (u64)j * X.T + (u64)row * C;
+    for (int rd = (int)nr - 1; rd >= 0; rd--) {
+        const u32 s0 = round_s0(l, rd), ns = round_ns(l, rd);
+        const bool from_acc = rd == (int)nr - 1, to_global = rd == 0;
+#define P3_ROWI(NSV)                                                          \
+    do {                                                                      \
+        if (from_acc)                                                         \
+            row_inv3<NSV, ACC, true>(X, j, smx, Srow, row, s0, to_global, acc);  \
+        else                                                                  \
+            row_inv3<NSV, ACC, false>(X, j, smx, Srow, row, s0, to_global, acc); \
+    } while (0)
+        P3_DISPATCH_NS(ns, P3_ROWI);
+#undef P3_ROWI
+        __syncthreads();
+    }
+}
+
+// -------------------------------------------------------- inverse columns --
+
+template <int NS, bool FIRSTR, bool TOGLOBAL, bool HO>
+__device__ __forceinline__ void inv3_round(const Geo3 &X, u32 j, u32 *__restrict__ S3, u32 *__restrict__ sm, u32 c0,
+                                           u32 s0) {
+    const u32 l = X.logR, tc = X.tc, p = X.p[j];
+    const u32 sh = l - s0 - NS, stride = 1u << sh;
+    const u32 ntask = (X.R >> NS) * tc;
+    const u32 logtc = __ffs(tc) - 1;
+    u32 *Sj = S3 + (u64)j * X.T;
+    for (u32 task = threadIdx.x; task < ntask; task += blockDim.x) {
+        const u32 c = task & (tc - 1), g = task >> logtc;
+        const u32 lo = g & (stride - 1), base = ((g >> sh) << (l - s0)) + lo;
+        u32 v[8];
+#pragma unroll
+        for (int m = 0; m < (1 << NS); m++) {
+            const u32 r = base + m * stride;
+            v[m] = FIRSTR ? Sj[(u64)r * X.C + c0 + c] : sm[px(r * tc + c)];
+        }
+        dit3<NS, FIRSTR, HO>(v, s0, lo, stride, X.itwR[j], p);
+#pragma unroll
+        for (int m = 0; m < (1 << NS); m++) {
+            const u32 r = base + m * stride;
+            if (TOGLOBAL) {
+                if (HO && m >= (1 << (NS - 1))) continue;  // rows >= R/2: coefficients >= T/2, unused
+                Sj[(u64)r * X.C + c0 + c] = v[m];
+            } else {
+                sm[px(r * tc + c)] = v[m];
+            }
+        }
+    }
+}
+
+// grid (C / tc, 3 primes).  In place on S3: every CTA reads its own columns
+// completely (first round) before it writes them (last round).
+__global__ void __launch_bounds__(kColThreads) k3_inv_col(Geo3 X, u32 *__restrict__ S3) {
+    extern __shared__ u32 sm3[];
+    const u32 j = blockIdx.y, tc = X.tc, c0 = blockIdx.x * tc;
+    const u32 l = X.logR, nr = (l + 2) / 3;
+    const bool ho = X.stage == 1;  // Eq. 4: only t mod 2^gamma, i.e. coefficients < T/2
+    for (int rd = (int)nr - 1; rd >= 0; rd--) {
+        const u32 s0 = round_s0(l, rd), ns = round_ns(l, rd);
+        const bool first = rd == (int)nr - 1, last = rd == 0;
+#define P3_INV(NSV)                                                       \
+    do {                                                                  \
+        if (first)                                                        \
+            inv3_round<NSV, true, false, false>(X, j, S3, sm3, c0, s0);   \
+        else if (last && ho)                                              \
+            inv3_round<NSV, false, true, true>(X, j, S3, sm3, c0, s0);    \
+        else if (last)                                                    \
+            inv3_round<NSV, false, true, false>(X, j, S3, sm3, c0, s0);   \
+        else                                                              \
+            inv3_round<NSV, false, false, false>(X, j, S3, sm3, c0, s0);  \
+    } while (0)
+        P3_DISPATCH_NS(ns, P3_INV);
+#undef P3_INV
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------ CRT and Mersenne fold --
+
+// Coefficient e from its three residues (scaled by 2^32 / T): Garner's mixed
+// radix x1 + p0 x2 + p0 p1 x3.
+__device__ __forceinline__ unsigned __int128 crt_value(const Geo3 &X, const u32 *__restrict__ S3, u64 e) {
+    const u32 p0 = X.p[0], p1 = X.p[1], p2 = X.p[2];
+    const u32 r0 = canon(shoup(__ldg(S3 + e), X.scale[0], p0), p0);
+    const u32 r1 = canon(shoup(__ldg(S3 + X.T + e), X.scale[1], p1), p1);
+    const u32 r2 = canon(shoup(__ldg(S3 + 2 * X.T + e), X.scale[2], p2), p2);
+    const u32 x1 = r0;
+    const u32 u1 = canon(shoup(x1, X.red[1], p1), p1);
+    const u32 x2 = canon(shoup(r1 - u1 + p1, X.c12, p1), p1);
+    const u32 u2 = canon(shoup(x1, X.red[2], p2), p2);
+    const u32 w2 = canon(shoup(x2, X.p0m2, p2), p2);
+    const u32 s2 = canon(u2 + w2, p2);
+    const u32 x3 = canon(shoup(r2 - s2 + p2, X.c3, p2), p2);
+    return (unsigned __int128)x1 + (unsigned __int128)((u64)p0 * x2) + (unsigned __int128)X.p01 * x3;
+}
+
+// Sum of the b-bit pieces that land on digit position P: piece k of
+// coefficient P - k (k = 0, 1, 2), for coefficients below ncoef.
+__device__ __forceinline__ u64 position_sum(const Geo3 &X, const u32 *__restrict__ S3, u64 P, u64 ncoef) {
+    const u32 b = X.b;
+    const u64 mask = (1ULL << b) - 1;
+    u64 s = 0;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        if (P < (u64)k) break;
+        const u64 e = P - k;
+        if (e >= ncoef) continue;
+        const unsigned __int128 v = crt_value(X, S3, e);
+        s += k < 2 ? (u64)(v >> (k * b)) & mask : (u64)(v >> (2 * b));
+    }
+    return s;
+}
+
+// Digit t (bit offset t b) of the value to resolve.  Eq. 2 (RING): every
+// position P whose offset P b is congruent mod gamma to a bit of digit t,
+// shifted by its distance from t b.  Eq. 4: position t only, plus digit t of
+// c (bits [c_base, c_base + gamma) of c_src).
+template <bool RING>
+__global__ void k3_digits(Geo3 X, const u32 *__restrict__ S3, u64 *__restrict__ z, u64 npad, const u64 *__restrict__ c_src,
+                          u64 c_base) {
+    const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= npad) return;
+    if (t >= X.nd) {
+        z[t] = 0;
+        return;
+    }
+    const u64 b = X.b, G = X.G;
+    const u64 ncoef = RING ? 2 * X.M - 1 : X.M;
+    u64 acc = position_sum(X, S3, t, ncoef);
+    if (RING) {
+#pragma unroll
+        for (u64 w = 1; w <= 2; w++) {
+            const u64 P = (w * G + t * b + b - 1) / b;  // first position at or above offset w G + t b
+            const u64 sh = P * b - w * G - t * b;      // < b
+            // offsets t b + sh >= G belong to digit 0.. of the next wrap (the top digit is short)
+            if (P <= 2 * X.M && t * b + sh < G) acc += position_sum(X, S3, P, ncoef) << sh;
+        }
+    } else if (c_src) {
+        const u64 pos = t * b;
+        const u32 nb = (u32)min(b, G - pos);
+        acc += rd32(c_src, c_base + pos, nb);
+    }
+    z[t] = acc;
+}
+
+// ------------------------------------------------------------------ tables --
+
+// ctw[r C + c] = omega_T^(dir * c bitrev_R(r)) with its Shoup companion; the
+// power comes from two host tables, lo[e mod 2^h] * hi[e >> h].
+__global__ void k3_fill_ctw(u32 logR, u32 logC, u32 h, const u32 *__restrict__ lo, const u32 *__restrict__ hi, u32 p,
+                            uint2 *__restrict__ out) {
+    const u64 T = 1ULL << (logR + logC);
+    for (u64 idx = (u64)blockIdx.x * blockDim.x + threadIdx.x; idx < T; idx += (u64)gridDim.x * blockDim.x) {
+        const u32 r = (u32)(idx >> logC), c = (u32)(idx & ((1u << logC) - 1));
+        const u64 e = ((u64)c * brev(r, logR)) & (T - 1);
+        const u32 w = (u32)(((u64)__ldg(lo + (e & ((1ULL << h) - 1))) * __ldg(hi + (e >> h))) % p);
+        out[idx] = make_uint2(w, (u32)(((u64)w << 32) / p));
+    }
+}
+
+}  // namespace p3
+
+// ---------------------------------------------------------------- launchers --
+
+using namespace p3;
+
+static size_t col_smem3(const Geo3 &X, bool pair) {
+    return (size_t)(pair ? 2 : 1) * (X.R * X.tc + (X.R * X.tc >> 3) + 8) * sizeof(u32);
+}
+static size_t row_smem3(const Geo3 &X) { return (size_t)2 * (X.C + (X.C >> 3) + 8) * sizeof(u32); }
+
+int p3_prepare_kernels() {
+    static bool done = false;
+    if (done) return 0;
+    const int big = 200 * 1024;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k3_fwd_col<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k3_fwd_col<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k3_row_mac<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k3_row_mac<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k3_inv_col, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    done = true;
+    return 0;
+}
+
+int p3_launch_fwd_col(const Geo3 &X, const Operands &S, int pairs, u32 *Y, void *stream) {
+    if (int e = p3_prepare_kernels()) return e;
+    const dim3 grid(X.C / X.tc, pairs, 3);
+    TRACED("p3_fwd_col", X.stage, stream,
+           (k3_fwd_col<true><<<grid, kColThreads, col_smem3(X, true), (cudaStream_t)stream>>>(X, S, Y)));
+    return (int)cudaGetLastError();
+}
+
+int p3_launch_row_mac(const Geo3 &X, const u32 *Y, u32 *S3, void *stream) {
+    if (int e = p3_prepare_kernels()) return e;
+    const dim3 grid(X.R, 3);
+    if (X.C > 8192)
+        TRACED("p3_row_mac", X.stage, stream,
+               (k3_row_mac<16><<<grid, X.C / 16, row_smem3(X), (cudaStream_t)stream>>>(X, Y, S3)));
+    else
+        TRACED("p3_row_mac", X.stage, stream,
+               (k3_row_mac<8><<<grid, X.C / 8, row_smem3(X), (cudaStream_t)stream>>>(X, Y, S3)));
+    return (int)cudaGetLastError();
+}
+
+int p3_launch_inv_col(const Geo3 &X, u32 *S3, void *stream) {
+    if (int e = p3_prepare_kernels()) return e;
+    const dim3 grid(X.C / X.tc, 3);
+    TRACED("p3_inv_col", X.stage, stream,
+           (k3_inv_col<<<grid, kColThreads, col_smem3(X, false), (cudaStream_t)stream>>>(X, S3)));
+    return (int)cudaGetLastError();
+}
+
+int p3_launch_digits(const Geo3 &X, const u32 *S3, u64 *z, u64 npad, const u64 *c_src, u64 c_base, void *stream) {
+    const u32 threads = 256;
+    const u64 blocks = (npad + threads - 1) / threads;
+    if (X.stage == 0)
+        TRACED("p3_digits", X.stage, stream,
+               (k3_digits<true><<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(X, S3, z, npad, c_src, c_base)));
+    else
+        TRACED("p3_digits", X.stage, stream,
+               (k3_digits<false><<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(X, S3, z, npad, c_src, c_base)));
+    return (int)cudaGetLastError();
+}
+
+int p3_launch_fill_ctw(u32 logR, u32 logC, u32 h, const u32 *lo, const u32 *hi, u32 p, uint2 *out, void *stream) {
+    k3_fill_ctw<<<152 * 8, 256, 0, (cudaStream_t)stream>>>(logR, logC, h, lo, hi, p, out);
+    return (int)cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- host plan --
+
+namespace {
+
+struct PrimeSet {
+    u32 p[3];
+    u32 maxlog;  // 2^maxlog divides every p - 1
+};
+// The three largest primes below 2^30 with 2^23 | p - 1, and the three below
+// 2^30 with 2^24 | p - 1 (the only ones).
+const PrimeSet kSetA = {{998244353u, 754974721u, 469762049u}, 23};
+const PrimeSet kSetB = {{754974721u, 469762049u, 167772161u}, 24};
+
+u32 powmod(u64 b, u64 e, u32 p) {
+    u64 r = 1;
+    b %= p;
+    while (e) {
+        if (e & 1) r = r * b % p;
+        b = b * b % p;
+        e >>= 1;
+    }
+    return (u32)r;
+}
+u32 invmod(u64 a, u32 p) { return powmod(a % p, p - 2, p); }
+
+u32 primitive_root(u32 p) {
+    std::vector<u32> f;
+    u32 m = p - 1;
+    for (u32 d = 2; (u64)d * d <= m; d++)
+        if (m % d == 0) {
+            f.push_back(d);
+            while (m % d == 0) m /= d;
+        }
+    if (m > 1) f.push_back(m);
+    for (u32 g = 2;; g++) {
+        bool ok = true;
+        for (u32 q : f) ok = ok && powmod(g, (p - 1) / q, p) != 1;
+        if (ok) return g;
+    }
+}
+
+uint2 shoup_pair(u32 w, u32 p) { return make_uint2(w, (u32)(((u64)w << 32) / p)); }
+
+u32 inv2_32(u32 p) {  // p^-1 mod 2^32 (p odd), Newton: each step doubles the correct bits
+    u32 x = p;
+    for (int i = 0; i < 5; i++) x *= 2u - p * x;
+    return x;
+}
+
+struct Choice {
+    u32 logT = 0, b = 0;
+    const PrimeSet *ps = nullptr;
+};
+
+// Smallest transform (2^8 .. 2^24) and digit size for operands of G bits and
+// K products: K M (2^b - 1)^2 < p0 p1 p2 with M b >= G; for Eq. 2 (ring) the
+// top carry chunk must span >= 64 bits whenever the parallel carry runs.
+bool choose(uint64_t G, uint64_t K, bool ring, Choice *out) {
+    for (u32 l = 8; l <= 24; l++) {
+        const PrimeSet &ps = l <= kSetA.maxlog ? kSetA : kSetB;
+        const unsigned __int128 P = (unsigned __int128)ps.p[0] * ps.p[1] * ps.p[2];
+        const u64 M = 1ULL << (l - 1);
+        const u64 bmin = std::max<u64>(1, (G + M - 1) / M);
+        for (u64 b = bmin; b <= 30; b++) {
+            const unsigned __int128 m = ((unsigned __int128)1 << b) - 1;
+            if ((unsigned __int128)K * M * m * m >= P) break;
+            const u64 nd = (G + b - 1) / b;
+            const u64 nch = (nd + PA_CARRY_D - 1) / PA_CARRY_D;
+            const bool parallel = nch >= PA_CARRY_T && b * PA_CARRY_D >= 64;
+            if (ring && parallel && G - (nch - 1) * PA_CARRY_D * b < 64) continue;
+            out->logT = l;
+            out->b = (u32)b;
+            out->ps = &ps;
+            return true;
+        }
+    }
+    return false;
+}
+
+void geometry(Geo3 &X, const Choice &ch, uint64_t G, uint64_t K, u32 stage) {
+    const u32 l = ch.logT;
+    X.logT = l;
+    X.T = 1ULL << l;
+    X.M = X.T / 2;
+    X.b = ch.b;
+    X.G = G;
+    X.nd = (G + ch.b - 1) / ch.b;
+    X.K = (u32)K;
+    X.stage = stage;
+    X.logR = std::min<u32>(l / 2, 10);
+    X.logC = l - X.logR;
+    X.R = 1u << X.logR;
+    X.C = 1u << X.logC;
+    u32 tc = std::min<u32>(16, 8192 / X.R);
+    X.tc = std::min<u32>(tc, X.C);
+}
+
+uint64_t table_bytes(const Geo3 &X) { return 3ULL * (X.R + X.C + 2 * X.T) * sizeof(uint2); }
+
+}  // namespace
+
+struct P3Plan {
+    uint64_t n = 0, r = 0, k = 0;
+    uint32_t gamma = 0;
+    Geo3 mmh{}, mh{};
+    std::vector<void *> allocs;
+    uint64_t ws_bytes = 0;
+    u32 *Y = nullptr, *S3 = nullptr;
+    u64 *ybuf = nullptr, *tbuf = nullptr, *H = nullptr;
+    unsigned char *cstate = nullptr, *cta_state = nullptr, *cta_cin = nullptr;
+    int *flags = nullptr;
+    size_t flags_bytes = 0;
+    ~P3Plan() {
+        for (void *p : allocs) cudaFree(p);
+    }
+    void *alloc(size_t bytes, int *err) {
+        void *p = nullptr;
+        if (*err) return nullptr;
+        if (cudaMalloc(&p, bytes ? bytes : 8) != cudaSuccess) {
+            *err = PA_ERR_NOMEM;
+            return nullptr;
+        }
+        allocs.push_back(p);
+        ws_bytes += bytes;
+        return p;
+    }
+};
+
+namespace {
+
+// Twiddle tables and constants of one stage; tables are shared with `other`
+// when both stages use the same transform shape.
+int build_tables(P3Plan *pl, Geo3 &X, const PrimeSet &ps, const Geo3 *other) {
+    for (int j = 0; j < 3; j++) {
+        const u32 p = ps.p[j];
+        X.p[j] = p;
+        X.pinv[j] = inv2_32(p);
+        X.red[j] = make_uint2(1u, (u32)((1ULL << 32) / p));
+        X.scale[j] = shoup_pair((u32)((u64)powmod(2, 32, p) * invmod(X.T, p) % p), p);
+    }
+    const u32 p0 = ps.p[0], p1 = ps.p[1], p2 = ps.p[2];
+    X.p01 = (u64)p0 * p1;
+    X.c12 = shoup_pair(invmod(p0, p1), p1);
+    X.p0m2 = shoup_pair(p0 % p2, p2);
+    X.c3 = shoup_pair(invmod((u64)p0 * p1 % p2, p2), p2);
+    if (other && other->T == X.T && other->logR == X.logR && other->p[0] == X.p[0] && other->twR[0]) {
+        for (int j = 0; j < 3; j++) {
+            X.twR[j] = other->twR[j];
+            X.itwR[j] = other->itwR[j];
+            X.twC[j] = other->twC[j];
+            X.itwC[j] = other->itwC[j];
+            X.ctw[j] = other->ctw[j];
+            X.ictw[j] = other->ictw[j];
+        }
+        return PA_OK;
+    }
+    int err = PA_OK;
+    const u32 l = X.logT, h = (l + 1) / 2;
+    std::vector<u32> lo(1u << h), hi(1u << (l - h));
+    u32 *dlo = (u32 *)pl->alloc(lo.size() * 4, &err), *dhi = (u32 *)pl->alloc(hi.size() * 4, &err);
+    for (int j = 0; j < 3 && !err; j++) {
+        const u32 p = ps.p[j], g = primitive_root(p);
+        const u32 wT = powmod(g, (p - 1) >> l, p);
+        for (int dir = 0; dir < 2 && !err; dir++) {
+            const u32 w = dir ? invmod(wT, p) : wT;
+            const u32 wR = powmod(w, X.C, p), wC = powmod(w, X.R, p);
+            std::vector<uint2> tR(X.R / 2), tC(X.C / 2);
+            u64 a = 1;
+            for (u32 e = 0; e < X.R / 2; e++, a = a * wR % p) tR[e] = shoup_pair((u32)a, p);
+            a = 1;
+            for (u32 e = 0; e < X.C / 2; e++, a = a * wC % p) tC[e] = shoup_pair((u32)a, p);
+            uint2 *dR = (uint2 *)pl->alloc(tR.size() * sizeof(uint2), &err);
+            uint2 *dC = (uint2 *)pl->alloc(tC.size() * sizeof(uint2), &err);
+            uint2 *dT = (uint2 *)pl->alloc(X.T * sizeof(uint2), &err);
+            if (err) break;
+            if (cudaMemcpy(dR, tR.data(), tR.size() * sizeof(uint2), cudaMemcpyHostToDevice) ||
+                cudaMemcpy(dC, tC.data(), tC.size() * sizeof(uint2), cudaMemcpyHostToDevice)) {
+                err = PA_ERR_CUDA;
+                break;
+            }
+            a = 1;
+            for (size_t e = 0; e < lo.size(); e++, a = a * w % p) lo[e] = (u32)a;
+            const u32 wh = powmod(w, 1ULL << h, p);
+            a = 1;
+            for (size_t e = 0; e < hi.size(); e++, a = a * wh % p) hi[e] = (u32)a;
+            if (cudaMemcpy(dlo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice) ||
+                cudaMemcpy(dhi, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice) ||
+                p3_launch_fill_ctw(X.logR, X.logC, h, dlo, dhi, p, dT, nullptr) || cudaDeviceSynchronize()) {
+                err = PA_ERR_CUDA;
+                break;
+            }
+            (dir ? X.itwR : X.twR)[j] = dR;
+            (dir ? X.itwC : X.twC)[j] = dC;
+            (dir ? X.ictw : X.ctw)[j] = dT;
+        }
+    }
+    return err;
+}
+
+}  // namespace
+
+int p3_feasible(uint32_t gamma, uint64_t k, uint32_t *logT_mmh, uint32_t *logT_mh) {
+    Choice c1, c2;
+    if (!choose(gamma, k, true, &c1) || !choose(gamma, 1, false, &c2)) return PA_ERR_UNSUPPORTED;
+    if (logT_mmh) *logT_mmh = c1.logT;
+    if (logT_mh) *logT_mh = c2.logT;
+    return PA_OK;
+}
+
+static void ws_parts(const Geo3 &A, const Geo3 &B, uint64_t k, uint64_t *total_no_tables) {
+    const uint64_t Tm = std::max(A.T, B.T);
+    const uint64_t nch = std::max((A.nd + 7) / 8, (B.nd + 7) / 8) + 1;
+    uint64_t s = 0;
+    s += 3 * std::max<uint64_t>(2 * k * A.T, 2 * B.T) * 4;  // Y (also the digit vector)
+    s += 3 * Tm * 4;                                       // S3
+    s += 2 * ((A.G + 63) / 64 + 2) * 8;                    // ybuf, tbuf
+    s += nch * 9 + 2 * (nch / PA_CARRY_T + 1);             // carry state
+    s += (4 + k) * sizeof(int);
+    *total_no_tables = s;
+}
+
+uint64_t p3_plan_bytes(uint32_t gamma, uint64_t k) {
+    Choice c1, c2;
+    if (!choose(gamma, k, true, &c1) || !choose(gamma, 1, false, &c2)) return 0;
+    Geo3 A{}, B{};
+    geometry(A, c1, gamma, k, 0);
+    geometry(B, c2, gamma, 1, 1);
+    uint64_t s;
+    ws_parts(A, B, k, &s);
+    const bool shared = A.T == B.T && A.logR == B.logR && c1.ps == c2.ps;
+    return s + table_bytes(A) + (shared ? 0 : table_bytes(B)) + 2 * (1ULL << ((std::max(A.logT, B.logT) + 1) / 2)) * 4;
+}
+
+int p3_plan_create(uint64_t n, uint64_t r, uint32_t gamma, uint64_t k, P3Plan **out) {
+    *out = nullptr;
+    Choice c1, c2;
+    if (!choose(gamma, k, true, &c1) || !choose(gamma, 1, false, &c2)) return PA_ERR_UNSUPPORTED;
+    if (p3_prepare_kernels()) return PA_ERR_CUDA;
+    P3Plan *pl = new (std::nothrow) P3Plan();
+    if (!pl) return PA_ERR_NOMEM;
+    pl->n = n;
+    pl->r = r;
+    pl->gamma = gamma;
+    pl->k = k;
+    geometry(pl->mmh, c1, gamma, k, 0);
+    geometry(pl->mh, c2, gamma, 1, 1);
+    int err = build_tables(pl, pl->mmh, *c1.ps, nullptr);
+    if (!err) err = build_tables(pl, pl->mh, *c2.ps, &pl->mmh);
+    const Geo3 &A = pl->mmh, &B = pl->mh;
+    const uint64_t Tm = std::max(A.T, B.T);
+    const uint64_t nch = std::max((A.nd + 7) / 8, (B.nd + 7) / 8) + 1;
+    pl->Y = (u32 *)pl->alloc(3 * std::max<uint64_t>(2 * k * A.T, 2 * B.T) * 4, &err);
+    pl->S3 = (u32 *)pl->alloc(3 * Tm * 4, &err);
+    pl->ybuf = (u64 *)pl->alloc(((gamma + 63) / 64 + 2) * 8, &err);
+    pl->tbuf = (u64 *)pl->alloc(((gamma + 63) / 64 + 2) * 8, &err);
+    pl->H = (u64 *)pl->alloc(nch * 8, &err);
+    pl->cstate = (unsigned char *)pl->alloc(nch, &err);
+    pl->cta_state = (unsigned char *)pl->alloc(nch / PA_CARRY_T + 1, &err);
+    pl->cta_cin = (unsigned char *)pl->alloc(nch / PA_CARRY_T + 1, &err);
+    pl->flags_bytes = (4 + k) * sizeof(int);
+    pl->flags = (int *)pl->alloc(pl->flags_bytes, &err);
+    if (err) {
+        delete pl;
+        return err;
+    }
+    *out = pl;
+    return PA_OK;
+}
+
+void p3_plan_destroy(P3Plan *pl) { delete pl; }
+
+void p3_plan_query(const P3Plan *pl, uint64_t *len_mmh, uint64_t *len_mh, uint64_t *ws_bytes) {
+    if (len_mmh) *len_mmh = pl->mmh.T;
+    if (len_mh) *len_mh = pl->mh.T;
+    if (ws_bytes) *ws_bytes = pl->ws_bytes;
+}
+
+const Geo3 *p3_stage(const P3Plan *pl, int stage) { return stage ? &pl->mh : &pl->mmh; }
+
+static CarryDev p3_carry_dev(P3Plan *pl, const Geo3 &X, bool ring, int *allones) {
+    CarryDev cd;
+    cd.N = 1;
+    cd.G = X.G;
+    cd.logN = 0;
+    cd.ub = X.b;
+    cd.linear = ring ? 0 : 1;
+    cd.nchunks = (X.nd + PA_CARRY_D - 1) / PA_CARRY_D;
+    cd.H = pl->H;
+    cd.state = pl->cstate;
+    cd.cta_state = pl->cta_state;
+    cd.cta_cin = pl->cta_cin;
+    cd.allones = allones;
+    return cd;
+}
+
+// Eq. 2: y = sum_i a_i x_i mod 2^gamma - 1 into y (gamma bits).
+int p3_enqueue_mmh(P3Plan *pl, const u64 *key, const u64 *seed, u64 *y, bool canonical, void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    int e;
+    if ((e = cudaMemsetAsync(pl->flags, 0, pl->flags_bytes, s))) return e;
+    Operands ops;
+    ops.pair0 = 0;
+    ops.key = key;
+    ops.seed = seed;
+    ops.y = nullptr;
+    ops.y_zero = nullptr;
+    ops.reload = pl->flags;
+    ops.n = pl->n;
+    ops.gamma = pl->gamma;
+    ops.k = pl->k;
+    ops.mode = 0;
+    const Geo3 &X = pl->mmh;
+    if ((e = p3_launch_fwd_col(X, ops, (int)pl->k, pl->Y, stream))) return e;
+    if ((e = p3_launch_row_mac(X, pl->Y, pl->S3, stream))) return e;
+    if ((e = p3_launch_inv_col(X, pl->S3, stream))) return e;
+    const CarryDev cd = p3_carry_dev(pl, X, true, pl->flags + 1);
+    u64 *z = (u64 *)pl->Y;
+    const u64 npad = cd.nchunks * PA_CARRY_D;
+    if ((e = p3_launch_digits(X, pl->S3, z, npad, nullptr, 0, stream))) return e;
+    const u64 ywords = (pl->gamma + 63) / 64;
+    if ((e = launch_carry_chunks(cd, npad, X.b * PA_CARRY_D >= 64, 0, z, y, ywords, stream))) return e;
+    if (canonical && (e = launch_canonical_zero(pl->flags + 1, y, ywords, stream))) return e;
+    return 0;
+}
+
+// Eq. 4: out = ((b y + c) mod 2^gamma) >> (gamma - r), y from the plan's buffer.
+int p3_enqueue_mh(P3Plan *pl, const u64 *seed, u64 *out, int *status, void *stream) {
+    int e;
+    Operands ops;
+    ops.pair0 = 0;
+    ops.key = nullptr;
+    ops.seed = seed;
+    ops.y = pl->ybuf;
+    ops.y_zero = pl->flags + 1;
+    ops.reload = pl->flags;
+    ops.n = pl->n;
+    ops.gamma = pl->gamma;
+    ops.k = pl->k;
+    ops.mode = 1;
+    const Geo3 &X = pl->mh;
+    if ((e = p3_launch_fwd_col(X, ops, 1, pl->Y, stream))) return e;
+    if ((e = p3_launch_row_mac(X, pl->Y, pl->S3, stream))) return e;
+    if ((e = p3_launch_inv_col(X, pl->S3, stream))) return e;
+    const CarryDev cd = p3_carry_dev(pl, X, false, pl->flags + 2);
+    u64 *z = (u64 *)pl->Y;
+    const u64 npad = cd.nchunks * PA_CARRY_D;
+    if ((e = p3_launch_digits(X, pl->S3, z, npad, seed, (pl->k + 1) * (u64)pl->gamma, stream))) return e;
+    const u64 twords = (pl->gamma + 63) / 64;
+    if ((e = launch_carry_chunks(cd, npad, X.b * PA_CARRY_D >= 64, 1, z, pl->tbuf, twords, stream))) return e;
+    if ((e = launch_extract(pl->tbuf, pl->gamma, pl->r, pl->flags, pl->k, out, status, stream))) return e;
+    return 0;
+}
+
+u64 *p3_ybuf(P3Plan *pl) { return pl->ybuf; }
+int *p3_flags(P3Plan *pl) { return pl->flags; }
+size_t p3_flags_bytes(const P3Plan *pl) { return pl->flags_bytes; }
+
+}  // namespace pa

@@ -78,3 +78,19 @@ def test_parallel_oracle_driver_matches_serial():
     rc, out, y = oracle.pa_hash(key, n, seed, r, g, k)
     rc2, out2, y2 = oracle_hash_parallel(key, n, seed, r, g, k, workers=3)
     assert rc == rc2 == 0 and np.array_equal(out, out2) and np.array_equal(y, y2)
+
+
+def test_backend_parameter_and_estimates():
+    """pa_params.backend: both backends size their workspace on the host; an
+    unknown backend is rejected; the three-prime plan of the 2.6e8-bit block
+    holds its spectra as 32-bit residues of three primes (3 x 4 bytes per
+    element against 8 for Goldilocks, same Eq. 2 length, half the Eq. 4 length)."""
+    g = _lib.plan_estimate_bytes(260_000_000, 26_000_000, backend=_lib.BACKEND_GOLDILOCKS)
+    p3 = _lib.plan_estimate_bytes(260_000_000, 26_000_000, backend=_lib.BACKEND_P3)
+    auto = _lib.plan_estimate_bytes(260_000_000, 26_000_000)
+    assert auto == g and p3 > 0
+    assert 3 * 2 * 9 * (1 << 21) * 4 < p3 < 3 * g
+    with pytest.raises(_lib.PAError) as e:
+        _lib.plan_estimate_bytes(1000, 10, backend=3)
+    assert e.value.code == -1
+    assert _lib.plan_estimate_bytes(61 * 3, 10, gamma=61, backend=_lib.BACKEND_P3) > 0

@@ -171,8 +171,8 @@ def test_autotuned_plan_gives_the_same_bits(n, r):
     """pa_params.tune picks the four-step split and column tile by timing;
     the output bits must not depend on the choice."""
     from paper_2105_13678_gb300 import _lib
-    p0 = _lib.Plan(n, r)
-    p1 = _lib.Plan(n, r, tune=True)
+    p0 = _lib.Plan(n, r, backend=_lib.BACKEND_GOLDILOCKS)
+    p1 = _lib.Plan(n, r, tune=True, backend=_lib.BACKEND_GOLDILOCKS)
     key, seed = synthetic.block_inputs(55, n, (p0.k + 2) * p0.gamma)
     s0, o0, y0, _ = gpu_hash(p0, key, seed)
     s1, o1, y1, _ = gpu_hash(p1, key, seed)

@@ -12,14 +12,28 @@ from helpers import gpu_hash, oracle_hash_parallel
 pytestmark = pytest.mark.gpu
 
 
-def _plan(n, r, gamma=0, margin=128):
+GOLDILOCKS, P3 = 1, 2
+
+
+def _plan(n, r, gamma=0, margin=128, backend=GOLDILOCKS):
     from paper_2105_13678_gb300 import _lib
-    return _lib.Plan(n, r, gamma=gamma, margin=margin)
+    return _lib.Plan(n, r, gamma=gamma, margin=margin, backend=backend)
+
+
+def _p3_plan(n, r, gamma=0, margin=128):
+    """The three-prime plan, or None where its sizes are not feasible."""
+    from paper_2105_13678_gb300 import _lib
+    try:
+        return _plan(n, r, gamma, margin, P3)
+    except _lib.PAError as e:
+        assert e.code == -7  # PA_ERR_UNSUPPORTED
+        return None
 
 
 def _check(n, r, seed_id, gamma=0, margin=128, parallel=False, key=None, hseed=None):
-    plan = _plan(n, r, gamma, margin)
-    g, k = plan.gamma, plan.k
+    """Both backends (Goldilocks, three-prime) against one oracle result."""
+    plans = [_plan(n, r, gamma, margin, GOLDILOCKS), _p3_plan(n, r, gamma, margin)]
+    g, k = plans[0].gamma, plans[0].k
     assert (g, k) == oracle.plan(n, r, margin=margin, gamma=gamma)
     if key is None:
         key, hseed = synthetic.block_inputs(seed_id, n, (k + 2) * g)
@@ -27,13 +41,17 @@ def _check(n, r, seed_id, gamma=0, margin=128, parallel=False, key=None, hseed=N
         rc, out, y = oracle_hash_parallel(key, n, hseed, r, g, k)
     else:
         rc, out, y = oracle.pa_hash(key, n, hseed, r, g, k)
-    st, gout, gy, st2 = gpu_hash(plan, key, hseed)
-    assert st == rc and st2 == rc
-    assert np.array_equal(gout, out), f"output mismatch n={n} r={r} gamma={g} k={k}"
-    if rc == oracle.ORA_OK:
-        assert np.array_equal(gy, y[: gy.size]), f"MMH value mismatch n={n} r={r} gamma={g} k={k}"
-    plan.close()
-    return plan
+    for plan in plans:
+        if plan is None:
+            continue
+        tag = f"backend={plan.backend} n={n} r={r} gamma={g} k={k}"
+        st, gout, gy, st2 = gpu_hash(plan, key, hseed)
+        assert st == rc and st2 == rc, tag
+        assert np.array_equal(gout, out), f"output mismatch {tag}"
+        if rc == oracle.ORA_OK:
+            assert np.array_equal(gy, y[: gy.size]), f"MMH value mismatch {tag}"
+        plan.close()
+    return plans[0]
 
 
 def test_config1_plain_block_2p20():
@@ -64,9 +82,10 @@ def test_no_padding_and_k1(n, r, gamma):
     _check(n, r, 77, gamma=gamma)
 
 
-def test_reload_on_all_ones_slice():
+@pytest.mark.parametrize("backend", [GOLDILOCKS, P3])
+def test_reload_on_all_ones_slice(backend):
     n, r, gamma = 4 * 4423, 100, 4423
-    plan = _plan(n, r, gamma)
+    plan = _plan(n, r, gamma, backend=backend)
     k = plan.k
     key, hseed = synthetic.block_inputs(5, n, (k + 2) * gamma)
     kv = oracle.words_to_int(key) | (((1 << gamma) - 1) << (2 * gamma))  # slice x_3 all ones
@@ -82,7 +101,7 @@ def test_zero_mmh_value_and_all_ones_representation():
     carry ring may land on the all-ones representation of 0)."""
     gamma = 44497
     n, r = 2 * gamma, 1000
-    plan = _plan(n, r, gamma)
+    plan = _plan(n, r, gamma)  # k and the seed layout (both backends are checked below)
     k = plan.k
     key, hseed = synthetic.block_inputs(9, n, (k + 2) * gamma)
     p = (1 << gamma) - 1
@@ -99,9 +118,10 @@ def test_zero_mmh_value_and_all_ones_representation():
         _check(n, r, 0, gamma=gamma, key=key2, hseed=seed2)
 
 
-def test_bits_past_n_ignored():
+@pytest.mark.parametrize("backend", [GOLDILOCKS, P3])
+def test_bits_past_n_ignored(backend):
     n, r = 100003, 5000
-    plan = _plan(n, r)
+    plan = _plan(n, r, backend=backend)
     k, g = plan.k, plan.gamma
     key, hseed = synthetic.block_inputs(21, n, (k + 2) * g)
     dirty = key.copy()
@@ -111,13 +131,14 @@ def test_bits_past_n_ignored():
     assert st == st2 == 0 and np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("backend", [GOLDILOCKS, P3])
 @pytest.mark.parametrize("n,r,gamma", [(1 << 20, 104858, 0), (7 * 4423 + 5, 300, 4423), (3_000_001, 290_000, 0),
                                        (4 * 4423, 100, 4423)])
-def test_host_entry_point_matches_device(n, r, gamma):
+def test_host_entry_point_matches_device(n, r, gamma, backend):
     """pa_hash_host (pipelined host-to-device copies) equals pa_hash; the last
     case plants an all-ones slice, so both must report a reload."""
     from paper_2105_13678_gb300 import _lib
-    plan = _plan(n, r, gamma)
+    plan = _plan(n, r, gamma, backend=backend)
     key, hseed = synthetic.block_inputs(1, n, (plan.k + 2) * plan.gamma)
     if n == 4 * 4423:
         kv = oracle.words_to_int(key) | (((1 << 4423) - 1) << 4423)
@@ -130,9 +151,10 @@ def test_host_entry_point_matches_device(n, r, gamma):
     assert st == rc and np.array_equal(out, ref)
 
 
-def test_repeat_calls_identical():
+@pytest.mark.parametrize("backend", [GOLDILOCKS, P3])
+def test_repeat_calls_identical(backend):
     n, r = 3_000_000, 300_000
-    plan = _plan(n, r)
+    plan = _plan(n, r, backend=backend)
     key, hseed = synthetic.block_inputs(4, n, (plan.k + 2) * plan.gamma)
     outs = [gpu_hash(plan, key, hseed)[1] for _ in range(3)]
     assert all(np.array_equal(outs[0], o) for o in outs[1:])
@@ -163,13 +185,14 @@ def test_paper_points_cv_dv():
         assert p.k * p.gamma == n
 
 
-def test_host_async_stream_of_blocks():
+@pytest.mark.parametrize("backend", [GOLDILOCKS, P3])
+def test_host_async_stream_of_blocks(backend):
     """pa_hash_host_async: several blocks in flight on one stream (staging slots
     alternate, copies overlap the previous block); every output equals pa_hash."""
     import torch
     from paper_2105_13678_gb300 import _lib
     n, r = 2_000_003, 200_000
-    plan = _plan(n, r)
+    plan = _plan(n, r, backend=backend)
     keys, seeds, outs = [], [], []
     for i in range(5):
         key, seed = synthetic.block_inputs(300 + i, n, (plan.k + 2) * plan.gamma)
@@ -187,3 +210,26 @@ def test_host_async_stream_of_blocks():
         st, ref, _, _ = gpu_hash(plan, keys[i].numpy().view(np.uint64), seeds[i].numpy().view(np.uint64))
         assert st == 0 and np.array_equal(outs[i].numpy().view(np.uint64), ref)
     plan.close()
+
+
+def test_backend_lengths():
+    """Transform lengths of both backends at the 2.6e8-bit block and the
+    1e9-bit block; PA_BACKEND_AUTO gives the Goldilocks plan."""
+    from paper_2105_13678_gb300 import _lib
+    a = _lib.Plan(260_000_000, 26_000_000, backend=P3)
+    assert a.info.mmh_len == 1 << 21 and a.info.mh_len == 1 << 21
+    g = _lib.Plan(260_000_000, 26_000_000)
+    assert g.backend == GOLDILOCKS and g.info.mmh_len == 1 << 21 and g.info.mh_len == 1 << 22
+    b = _lib.Plan(1_000_000_000, 100_000_000, backend=P3)
+    assert b.info.mmh_len == 1 << 24
+    for p in (a, g, b):
+        p.close()
+
+
+@pytest.mark.parametrize("gamma,k", [(521, 1), (521, 3), (607, 2), (4423, 5), (9689, 4), (44497, 3)])
+def test_p3_fold_offsets_wrap(gamma, k):
+    """Three-prime plans where the digit grid M b overshoots gamma by more than a
+    digit (the Mersenne fold places whole digits past gamma back at offset
+    (t b) mod gamma), every k up to the segment count."""
+    n = k * gamma - 3
+    _check(n, max(1, gamma // 3), gamma * 31 + k, gamma=gamma)

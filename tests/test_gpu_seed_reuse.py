@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 def test_prepared_matches_plain_for_several_keys(n, r, gamma):
     import torch
     from paper_2105_13678_gb300 import _lib
-    plan = _lib.Plan(n, r, gamma=gamma)
+    plan = _lib.Plan(n, r, gamma=gamma, backend=_lib.BACKEND_GOLDILOCKS)
     g, k = plan.gamma, plan.k
     _, seed = synthetic.block_inputs(100 + n % 97, n, (k + 2) * g)
     ds = dev(seed)
@@ -41,8 +41,20 @@ def test_prepared_matches_plain_for_several_keys(n, r, gamma):
 def test_prepared_requires_prepare():
     import torch
     from paper_2105_13678_gb300 import _lib
-    plan = _lib.Plan(1 << 16, 1000)
+    plan = _lib.Plan(1 << 16, 1000, backend=_lib.BACKEND_GOLDILOCKS)
     buf = torch.zeros(plan.info.key_words + 8, dtype=torch.int64, device="cuda")
     with pytest.raises(_lib.PAError):
         _lib.pa_hash_prepared(plan, buf.data_ptr(), buf.data_ptr())
+    plan.close()
+
+
+def test_three_prime_plans_refuse_seed_reuse():
+    """Seed reuse exists for the Goldilocks transforms only."""
+    import torch
+    from paper_2105_13678_gb300 import _lib
+    plan = _lib.Plan(1 << 20, 104858, backend=_lib.BACKEND_P3)
+    seed = torch.zeros((plan.k + 2) * plan.gamma // 64 + 1, dtype=torch.int64, device="cuda")
+    with pytest.raises(_lib.PAError) as e:
+        _lib.pa_seed_prepare(plan, seed.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert e.value.code == -7
     plan.close()
