@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--n-bits", type=int, default=N_BITS, help="block size (profiling runs use smaller blocks)")
     ap.add_argument("--ratio", type=float, default=RATIO, help="r / n")
     ap.add_argument("--tune", type=int, default=1, help="autotune the transform geometry at plan time (1) or not (0)")
+    ap.add_argument("--backend", default="auto", choices=["auto", "goldilocks", "p3"],
+                    help="arithmetic of the timed plan (the other backend is timed beside it)")
     return ap.parse_args()
 
 
@@ -232,7 +234,8 @@ def run_gb300(args):
 
     n = args.n_bits
     r = int(math.ceil(args.ratio * n))
-    plan = _lib.Plan(n, r, tune=bool(args.tune))
+    backend = {"auto": _lib.BACKEND_AUTO, "goldilocks": _lib.BACKEND_GOLDILOCKS, "p3": _lib.BACKEND_P3}[args.backend]
+    plan = _lib.Plan(n, r, tune=bool(args.tune), backend=backend)
     info = plan.info
     block_seed = 2 if rank == 0 else (2 << 32) + rank
     key, seed = synthetic.block_inputs(block_seed, n, (plan.k + 2) * plan.gamma)

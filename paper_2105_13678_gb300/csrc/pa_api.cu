@@ -289,8 +289,9 @@ static WsSizes ws_sizes(uint32_t gamma, uint64_t k, uint64_t N1, uint64_t N2) {
     return z;
 }
 
-// Backend of a plan.  PA_BACKEND_AUTO takes the Goldilocks transforms; the
-// three-prime transforms are opt-in (kAutoP3 off) until they are the faster.
+// Backend of a plan.  PA_BACKEND_AUTO takes the three-prime transforms where
+// they are feasible, no longer than the Goldilocks transform of Eq. 2 and at
+// least 2^20 long (the shapes with compile-time kernels), else Goldilocks.
 static int choose_backend(uint32_t gamma, uint64_t k, const pa_params *params, uint32_t l1, int *backend) {
     const uint32_t want = params ? params->backend : PA_BACKEND_AUTO;
     if (want > PA_BACKEND_P3) return PA_ERR_INVALID;
@@ -302,8 +303,7 @@ static int choose_backend(uint32_t gamma, uint64_t k, const pa_params *params, u
     } else if (want == PA_BACKEND_GOLDILOCKS) {
         *backend = PA_BACKEND_GOLDILOCKS;
     } else {
-        constexpr bool kAutoP3 = false;
-        *backend = (kAutoP3 && p3ok && t1 <= l1) ? PA_BACKEND_P3 : PA_BACKEND_GOLDILOCKS;
+        *backend = (p3ok && t1 <= l1 && t1 >= 20) ? PA_BACKEND_P3 : PA_BACKEND_GOLDILOCKS;
     }
     return PA_OK;
 }

@@ -145,8 +145,12 @@ struct Geo3 {
     u32 p[3], pinv[3];          // primes and p^-1 mod 2^32
     uint2 scale[3], red[3];     // 2^32 / T mod p; (1, floor(2^32 / p))
     uint2 c12, p0m2, c3;        // p0^-1 mod p1; p0 mod p2; (p0 p1)^-1 mod p2
-    const uint2 *twR[3], *itwR[3];  // omega_R^(+-e), e < R/2
-    const uint2 *twC[3], *itwC[3];  // omega_C^(+-e), e < C/2
+    // Round twiddle tables: for round rd of the length-R (C) transform, entry
+    // rof[rd] + lo (2^NS - 1) + q holds the q-th twiddle (stage by stage) of
+    // the task with offset lo: omega^(+-(lo + jj stride) 2^(s0 + sg)).
+    const uint2 *twR[3], *itwR[3];
+    const uint2 *twC[3], *itwC[3];
+    u32 rofR[6], rofC[6];
     const uint2 *ctw[3], *ictw[3];  // T entries, [r][c]: omega_T^(+-c bitrev_R(r))
 };
 

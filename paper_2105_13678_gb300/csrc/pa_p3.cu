@@ -70,8 +70,9 @@ __device__ __forceinline__ u32 round_s0(u32 l, u32 rd) { return rd ? round_ns(l,
 // with twiddle omega_L^((i mod L/2^(s+1)) 2^s).  HZ: the upper half of the
 // group is zero on entry.  In the final round (LAST) the twiddles of the
 // pairs with i mod L/2^(s+1) = 0 are 1.
+// rt: the task's round twiddles, stage sg's pair jj at q = 2^NS - 2^(NS-sg) + jj.
 template <int NS, bool LAST, bool HZ>
-__device__ __forceinline__ void dif3(u32 (&v)[8], u32 s0, u32 lo, u32 stride, const uint2 *__restrict__ tw, u32 p) {
+__device__ __forceinline__ void dif3(u32 (&v)[8], const uint2 *__restrict__ rt, u32 p) {
     const u32 p2 = 2 * p;
 #pragma unroll
     for (int sg = 0; sg < NS; sg++) {
@@ -79,25 +80,26 @@ __device__ __forceinline__ void dif3(u32 (&v)[8], u32 s0, u32 lo, u32 stride, co
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
             if (m & half) continue;
-            const u32 jj = (u32)(m & (half - 1));
+            const int jj = m & (half - 1);
             const bool one = LAST && jj == 0;
-            const u32 e = (lo + jj * stride) << (s0 + sg);
+            const int q = (1 << NS) - (1 << (NS - sg)) + jj;
             const u32 a = v[m], b = v[m + half];
             if (HZ && sg == 0) {
-                v[m + half] = one ? a : shoup(a, __ldg(tw + e), p);
+                v[m + half] = one ? a : shoup(a, __ldg(rt + q), p);
                 continue;
             }
             v[m] = red2(a + b, p2);
             const u32 d = a - b + p2;
-            v[m + half] = one ? red2(d, p2) : shoup(d, __ldg(tw + e), p);
+            v[m + half] = one ? red2(d, p2) : shoup(d, __ldg(rt + q), p);
         }
     }
 }
 
 // Inverse of dif3 up to a factor 2^NS (DIT, stages reversed, inverse
-// twiddles).  HO: the upper outputs of the last stage are not needed.
+// twiddles in the same table layout).  HO: the upper outputs of the last
+// stage are not needed.
 template <int NS, bool LAST, bool HO>
-__device__ __forceinline__ void dit3(u32 (&v)[8], u32 s0, u32 lo, u32 stride, const uint2 *__restrict__ itw, u32 p) {
+__device__ __forceinline__ void dit3(u32 (&v)[8], const uint2 *__restrict__ rt, u32 p) {
     const u32 p2 = 2 * p;
 #pragma unroll
     for (int sg = NS - 1; sg >= 0; sg--) {
@@ -105,16 +107,20 @@ __device__ __forceinline__ void dit3(u32 (&v)[8], u32 s0, u32 lo, u32 stride, co
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
             if (m & half) continue;
-            const u32 jj = (u32)(m & (half - 1));
+            const int jj = m & (half - 1);
             const bool one = LAST && jj == 0;
-            const u32 e = (lo + jj * stride) << (s0 + sg);
+            const int q = (1 << NS) - (1 << (NS - sg)) + jj;
             const u32 a = v[m];
-            const u32 t = one ? v[m + half] : shoup(v[m + half], __ldg(itw + e), p);
+            const u32 t = one ? v[m + half] : shoup(v[m + half], __ldg(rt + q), p);
             v[m] = red2(a + t, p2);
             if (!(HO && sg == 0)) v[m + half] = red2(a - t + p2, p2);
         }
     }
 }
+
+// Shared-memory word of element i: one pad word per 8 (px(i + 8k) = px(i) + 9k,
+// so elements m * d apart, d a multiple of 8, are px(i) + m * (d + d / 8)).
+__device__ __forceinline__ u32 pstep(u32 d) { return d + (d >> 3); }
 
 #define P3_DISPATCH_NS(ns, F) \
     do {                      \
@@ -161,9 +167,9 @@ __device__ __forceinline__ void descs(const Operands &S, u32 i, Desc &dx, Desc &
     }
 }
 
-// Digit e (bits [e b, (e+1) b) of the operand), reduced into [0, 2p).
-__device__ __forceinline__ u32 digit(const Geo3 &X, const Desc &d, u64 e, uint2 red, u32 p, bool &ones) {
-    const u64 pos = e * X.b;
+// The digit at bit offset pos of the operand (b bits, fewer at the top),
+// reduced into [0, 2p).
+__device__ __forceinline__ u32 digit_at(const Geo3 &X, const Desc &d, u64 pos, uint2 red, u32 p, bool &ones) {
     if (d.zero || pos >= d.len) {
         if (d.check_ones && pos < X.G) ones = false;  // zero padding below gamma: not all ones
         return 0;
@@ -172,82 +178,102 @@ __device__ __forceinline__ u32 digit(const Geo3 &X, const Desc &d, u64 e, uint2 
     const u32 nb = left < X.b ? (u32)left : X.b;
     u32 v = rd32(d.src, d.base + pos, nb);
     if (d.check_ones) ones = ones && (v == (nb >= 32 ? 0xFFFFFFFFu : (1u << nb) - 1u));
-    if (d.force_odd && e == 0) v |= 1u;
+    if (d.force_odd && pos == 0) v |= 1u;
     return shoup(v, red, p);
+}
+
+// The raw digit at bit offset pos (b bits, fewer at the top; 0 past the operand).
+__device__ __forceinline__ u32 digit_raw(const Geo3 &X, const Desc &d, u64 pos, bool &ones) {
+    if (d.zero || pos >= d.len) {
+        if (d.check_ones && pos < X.G) ones = false;
+        return 0;
+    }
+    const u64 left = d.len - pos;
+    const u32 nb = left < X.b ? (u32)left : X.b;
+    u32 v = rd32(d.src, d.base + pos, nb);
+    if (d.check_ones) ones = ones && (v == (nb >= 32 ? 0xFFFFFFFFu : (1u << nb) - 1u));
+    if (d.force_odd && pos == 0) v |= 1u;
+    return v;
 }
 
 // ------------------------------------------------------------ column pass --
 
-template <int NS, bool PAIR, bool FIRST, bool LAST>
+// LL, TC: log2 R and the tile width when fixed at compile time (0: from X).
+template <int NS, bool PAIR, bool FIRST, bool LAST, int LL, int TC>
 __device__ __forceinline__ void fwd3_round(const Geo3 &X, u32 j, const Desc &dx, const Desc &da, u32 *__restrict__ smx,
                                            u32 *__restrict__ sma, u32 *__restrict__ Yx, u32 *__restrict__ Ya, u32 c0,
-                                           u32 s0, bool &ones) {
-    const u32 l = X.logR, tc = X.tc, p = X.p[j];
+                                           u32 s0, u32 rd, bool &ones) {
+    const u32 l = LL ? (u32)LL : X.logR, tc = TC ? (u32)TC : X.tc, p = X.p[j];
     const u32 sh = l - s0 - NS, stride = 1u << sh;
-    const u32 ntask = (X.R >> NS) * tc;
-    const u32 logtc = __ffs(tc) - 1;
+    const u32 ntask = ((1u << l) >> NS) * tc;
+    const u32 logtc = TC ? (u32)__builtin_ctz(TC) : (u32)(__ffs(tc) - 1);
+    const u32 dsm = pstep(stride * tc);  // tc is a multiple of 8
+    const u64 dY = (u64)stride * X.C;
     const uint2 red = X.red[j];
+    const uint2 *tw = X.twR[j] + X.rofR[rd];
     for (u32 task = threadIdx.x; task < ntask; task += blockDim.x) {
         const u32 c = task & (tc - 1), g = task >> logtc;
         const u32 lo = g & (stride - 1), base = ((g >> sh) << (l - s0)) + lo;
+        const u32 a0 = px(base * tc + c);
+        const u64 e0 = (u64)base * X.C + c0 + c;
         u32 vx[8], va[8];
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
-            const u32 r = base + m * stride;
             if (FIRST && m >= (1 << (NS - 1))) {  // rows >= R/2: digit slots >= T/2 are zero
                 vx[m] = 0;
                 va[m] = 0;
             } else if (FIRST) {
-                const u64 e = (u64)r * X.C + c0 + c;
-                vx[m] = digit(X, dx, e, red, p, ones);
-                if (PAIR) va[m] = digit(X, da, e, red, p, ones);
+                const u64 pos = (e0 + m * dY) * X.b;
+                vx[m] = digit_at(X, dx, pos, red, p, ones);
+                if (PAIR) va[m] = digit_at(X, da, pos, red, p, ones);
             } else {
-                vx[m] = smx[px(r * tc + c)];
-                if (PAIR) va[m] = sma[px(r * tc + c)];
+                vx[m] = smx[a0 + m * dsm];
+                if (PAIR) va[m] = sma[a0 + m * dsm];
             }
         }
-        dif3<NS, LAST, FIRST>(vx, s0, lo, stride, X.twR[j], p);
-        if (PAIR) dif3<NS, LAST, FIRST>(va, s0, lo, stride, X.twR[j], p);
+        const uint2 *rt = tw + lo * ((1u << NS) - 1);
+        dif3<NS, LAST, FIRST>(vx, rt, p);
+        if (PAIR) dif3<NS, LAST, FIRST>(va, rt, p);
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
-            const u32 r = base + m * stride;
             if (LAST) {
                 // position r holds column frequency bitrev(r): times omega_T^(c bitrev(r))
-                const u64 e = (u64)r * X.C + c0 + c;
+                const u64 e = e0 + m * dY;
                 const uint2 t = __ldg(X.ctw[j] + e);
                 Yx[e] = shoup(vx[m], t, p);
                 if (PAIR) Ya[e] = shoup(va[m], t, p);
             } else {
-                smx[px(r * tc + c)] = vx[m];
-                if (PAIR) sma[px(r * tc + c)] = va[m];
+                smx[a0 + m * dsm] = vx[m];
+                if (PAIR) sma[a0 + m * dsm] = va[m];
             }
         }
     }
 }
 
 // grid (C / tc, pairs, 3 primes): a tile of tc columns of pair blockIdx.y + pair0.
-template <bool PAIR>
+template <bool PAIR, int LL, int TC>
 __global__ void __launch_bounds__(kColThreads) k3_fwd_col(Geo3 X, Operands S, u32 *__restrict__ Y) {
     extern __shared__ u32 sm3[];
-    const u32 j = blockIdx.z, tc = X.tc, c0 = blockIdx.x * tc, i = blockIdx.y + S.pair0;
+    const u32 j = blockIdx.z, tc = TC ? (u32)TC : X.tc, c0 = blockIdx.x * tc, i = blockIdx.y + S.pair0;
     Desc dx, da;
     descs(S, i, dx, da);
     if (j) dx.check_ones = 0;
     u32 *Yx = Y + ((u64)j * 2 * X.K + i) * X.T, *Ya = Y + ((u64)j * 2 * X.K + X.K + i) * X.T;
     u32 *smx = sm3, *sma = sm3 + px(X.R * tc);
     bool ones = true;
-    const u32 l = X.logR, nr = (l + 2) / 3;
+    const u32 l = LL ? (u32)LL : X.logR, nr = (l + 2) / 3;
+#pragma unroll(LL > 0 ? 8 : 1)
     for (u32 rd = 0; rd < nr; rd++) {
         const u32 s0 = round_s0(l, rd), ns = round_ns(l, rd);
         const bool first = rd == 0, last = rd == nr - 1;
 #define P3_FWD(NSV)                                                                                   \
     do {                                                                                              \
         if (first)                                                                                    \
-            fwd3_round<NSV, PAIR, true, false>(X, j, dx, da, smx, sma, Yx, Ya, c0, s0, ones);         \
+            fwd3_round<NSV, PAIR, true, false, LL, TC>(X, j, dx, da, smx, sma, Yx, Ya, c0, s0, rd, ones);         \
         else if (last)                                                                                \
-            fwd3_round<NSV, PAIR, false, true>(X, j, dx, da, smx, sma, Yx, Ya, c0, s0, ones);         \
+            fwd3_round<NSV, PAIR, false, true, LL, TC>(X, j, dx, da, smx, sma, Yx, Ya, c0, s0, rd, ones);         \
         else                                                                                          \
-            fwd3_round<NSV, PAIR, false, false>(X, j, dx, da, smx, sma, Yx, Ya, c0, s0, ones);        \
+            fwd3_round<NSV, PAIR, false, false, LL, TC>(X, j, dx, da, smx, sma, Yx, Ya, c0, s0, rd, ones);        \
     } while (0)
         P3_DISPATCH_NS(ns, P3_FWD);
 #undef P3_FWD
@@ -263,106 +289,238 @@ __global__ void __launch_bounds__(kColThreads) k3_fwd_col(Geo3 X, Operands S, u3
     }
 }
 
+// All three primes in one CTA (compile-time geometry, 512 threads): the
+// digits of the first round's nonzero half are read once into registers, then
+// each prime runs its column transform through the same shared tile.
+template <int LL, int TC>
+__global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32 *__restrict__ Y) {
+    constexpr u32 NTH = 512;
+    constexpr u32 NS0 = LL - 3 * ((LL + 2) / 3 - 1);
+    constexpr u32 HALF0 = 1u << (NS0 - 1);
+    constexpr u32 SH0 = LL - NS0;                 // first-round stride 2^SH0 rows
+    constexpr u32 NTASK0 = ((1u << LL) >> NS0) * TC;
+    constexpr u32 NT = NTASK0 / NTH;
+    constexpr u32 LOGTC = __builtin_ctz(TC);
+    static_assert(NT * NTH == NTASK0, "first-round tasks must divide evenly");
+    extern __shared__ u32 sm3[];
+    const u32 c0 = blockIdx.x * TC, i = blockIdx.y + S.pair0;
+    Desc dx, da;
+    descs(S, i, dx, da);
+    u32 *smx = sm3, *sma = sm3 + px((1u << LL) * TC);
+    bool ones = true;
+    u32 rx[NT][HALF0], ra[NT][HALF0];
+#pragma unroll
+    for (u32 t = 0; t < NT; t++) {
+        const u32 task = threadIdx.x + t * NTH;
+        const u32 c = task & (TC - 1), g = task >> LOGTC;  // g < 2^SH0: base = g
+        const u64 e0 = (u64)g * X.C + c0 + c;
+#pragma unroll
+        for (u32 m = 0; m < HALF0; m++) {
+            const u64 pos = (e0 + ((u64)m << SH0) * X.C) * X.b;
+            rx[t][m] = digit_raw(X, dx, pos, ones);
+            ra[t][m] = digit_raw(X, da, pos, ones);
+        }
+    }
+    constexpr u32 nr = (LL + 2) / 3;
+#pragma unroll 1
+    for (u32 j = 0; j < 3; j++) {
+        const u32 p = X.p[j];
+        const uint2 red = X.red[j];
+        u32 *Yx = Y + ((u64)j * 2 * X.K + i) * X.T, *Ya = Y + ((u64)j * 2 * X.K + X.K + i) * X.T;
+        const uint2 *tw = X.twR[j] + X.rofR[0];
+#pragma unroll
+        for (u32 t = 0; t < NT; t++) {
+            const u32 task = threadIdx.x + t * NTH;
+            const u32 c = task & (TC - 1), g = task >> LOGTC;
+            const u32 a0 = px(g * TC + c);
+            constexpr u32 dsm = ((1u << SH0) * TC) + (((1u << SH0) * TC) >> 3);
+            u32 vx[8], va[8];
+#pragma unroll
+            for (u32 m = 0; m < (1u << NS0); m++) {
+                vx[m] = m < HALF0 ? shoup(rx[t][m], red, p) : 0u;
+                va[m] = m < HALF0 ? shoup(ra[t][m], red, p) : 0u;
+            }
+            const uint2 *rt = tw + g * ((1u << NS0) - 1);
+            dif3<NS0, false, true>(vx, rt, p);
+            dif3<NS0, false, true>(va, rt, p);
+#pragma unroll
+            for (u32 m = 0; m < (1u << NS0); m++) {
+                smx[a0 + m * dsm] = vx[m];
+                sma[a0 + m * dsm] = va[m];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (u32 rd = 1; rd < nr; rd++) {
+            const u32 s0 = NS0 + 3 * (rd - 1);
+            if (rd == nr - 1)
+                fwd3_round<3, true, false, true, LL, TC>(X, j, dx, da, smx, sma, Yx, Ya, c0, s0, rd, ones);
+            else
+                fwd3_round<3, true, false, false, LL, TC>(X, j, dx, da, smx, sma, Yx, Ya, c0, s0, rd, ones);
+            __syncthreads();
+        }
+    }
+    if (dx.check_ones) {
+        // Algorithm 1 reload rule: slice i is all ones iff every CTA of the slice saw only ones
+        const int all = __syncthreads_and(ones ? 1 : 0);
+        if (threadIdx.x == 0 && all) {
+            int *cnt = S.reload + 4 + i;
+            if (atomicAdd(cnt, 1) + 1 == (int)gridDim.x) atomicExch(S.reload, 1);
+        }
+    }
+}
+
 // --------------------------------------------------- rows + MAC (Eq. 2) --
 
-template <int NS, int ACC, bool LAST>
-__device__ __forceinline__ void row_fwd3(const Geo3 &X, u32 j, const u32 *__restrict__ xrow,
-                                         const u32 *__restrict__ arow, u32 *__restrict__ smx, u32 *__restrict__ sma,
-                                         u32 s0, bool first, u32 (&acc)[ACC]) {
-    const u32 l = X.logC, sh = l - s0 - NS, stride = 1u << sh, ngroups = X.C >> NS, p = X.p[j], pinv = X.pinv[j];
+// Row rounds: elements base + m*stride with stride >= 8 or (stride = 1 and
+// base a multiple of 8), so their padded words are px(base) + m * pstep(stride).
+template <int NS, int ACC, bool LAST, int LL>
+__device__ __forceinline__ void row_fwd3(const Geo3 &X, u32 j, const u32 (&fx)[ACC], const u32 (&fa)[ACC],
+                                         u32 *__restrict__ smx, u32 *__restrict__ sma, u32 s0, u32 rd, bool first,
+                                         u32 (&acc)[ACC]) {
+    const u32 l = LL ? (u32)LL : X.logC, sh = l - s0 - NS, stride = 1u << sh, ngroups = (1u << l) >> NS;
+    const u32 p = X.p[j], pinv = X.pinv[j];
+    const u32 dsm = pstep(stride);
+    const uint2 *tw = X.twC[j] + X.rofC[rd];
 #pragma unroll
     for (int t = 0; t < (ACC >> NS); t++) {
         const u32 g = threadIdx.x + t * blockDim.x;
         if (g < ngroups) {
             const u32 lo = g & (stride - 1), base = ((g >> sh) << (l - s0)) + lo;
+            const u32 a0 = px(base);
             u32 vx[8], va[8];
 #pragma unroll
             for (int m = 0; m < (1 << NS); m++) {
-                const u32 idx = base + m * stride;
-                vx[m] = first ? __ldg(xrow + idx) : smx[px(idx)];
-                va[m] = first ? __ldg(arow + idx) : sma[px(idx)];
+                vx[m] = first ? fx[t * (1 << NS) + m] : smx[a0 + m * dsm];
+                va[m] = first ? fa[t * (1 << NS) + m] : sma[a0 + m * dsm];
             }
-            dif3<NS, LAST, false>(vx, s0, lo, stride, X.twC[j], p);
-            dif3<NS, LAST, false>(va, s0, lo, stride, X.twC[j], p);
+            const uint2 *rt = tw + lo * ((1u << NS) - 1);
+            dif3<NS, LAST, false>(vx, rt, p);
+            dif3<NS, LAST, false>(va, rt, p);
 #pragma unroll
             for (int m = 0; m < (1 << NS); m++) {
                 if (LAST) {
                     u32 &a = acc[t * (1 << NS) + m];
                     a = red2(a + mont(vx[m], va[m], p, pinv), 2 * p);
                 } else {
-                    const u32 idx = base + m * stride;
-                    smx[px(idx)] = vx[m];
-                    sma[px(idx)] = va[m];
+                    smx[a0 + m * dsm] = vx[m];
+                    sma[a0 + m * dsm] = va[m];
                 }
             }
         }
     }
 }
 
-template <int NS, int ACC, bool LAST>
+// The first round's inputs of one row pair (elements g + m C/2^NS of group g):
+// loaded into registers ahead of use.
+template <int NS, int ACC, int LL>
+__device__ __forceinline__ void row_load3(const Geo3 &X, const u32 *__restrict__ xrow, const u32 *__restrict__ arow,
+                                          u32 (&fx)[ACC], u32 (&fa)[ACC]) {
+    const u32 l = LL ? (u32)LL : X.logC, stride = 1u << (l - NS), ngroups = (1u << l) >> NS;
+#pragma unroll
+    for (int t = 0; t < (ACC >> NS); t++) {
+        const u32 g = threadIdx.x + t * blockDim.x;
+        if (g < ngroups) {
+#pragma unroll
+            for (int m = 0; m < (1 << NS); m++) {
+                fx[t * (1 << NS) + m] = __ldg(xrow + g + m * stride);
+                fa[t * (1 << NS) + m] = __ldg(arow + g + m * stride);
+            }
+        }
+    }
+}
+
+template <int NS, int ACC, bool LAST, int LL>
 __device__ __forceinline__ void row_inv3(const Geo3 &X, u32 j, u32 *__restrict__ sm, u32 *__restrict__ Srow, u32 row,
-                                         u32 s0, bool to_global, const u32 (&acc)[ACC]) {
-    const u32 l = X.logC, sh = l - s0 - NS, stride = 1u << sh, ngroups = X.C >> NS, p = X.p[j];
-    const uint2 *ictw = X.ictw[j] + (u64)row * X.C;
+                                         u32 s0, u32 rd, bool to_global, const u32 (&acc)[ACC]) {
+    const u32 l = LL ? (u32)LL : X.logC, sh = l - s0 - NS, stride = 1u << sh, ngroups = (1u << l) >> NS, p = X.p[j];
+    const u32 dsm = pstep(stride);
+    const uint2 *ictw = X.ictw[j] + ((u64)row << l);
+    const uint2 *itw = X.itwC[j] + X.rofC[rd];
 #pragma unroll
     for (int t = 0; t < (ACC >> NS); t++) {
         const u32 g = threadIdx.x + t * blockDim.x;
         if (g < ngroups) {
             const u32 lo = g & (stride - 1), base = ((g >> sh) << (l - s0)) + lo;
+            const u32 a0 = px(base);
             u32 v[8];
 #pragma unroll
-            for (int m = 0; m < (1 << NS); m++) v[m] = LAST ? acc[t * (1 << NS) + m] : sm[px(base + m * stride)];
-            dit3<NS, LAST, false>(v, s0, lo, stride, X.itwC[j], p);
+            for (int m = 0; m < (1 << NS); m++) v[m] = LAST ? acc[t * (1 << NS) + m] : sm[a0 + m * dsm];
+            dit3<NS, LAST, false>(v, itw + lo * ((1u << NS) - 1), p);
 #pragma unroll
             for (int m = 0; m < (1 << NS); m++) {
-                const u32 idx = base + m * stride;
-                if (to_global)
+                if (to_global) {
+                    const u32 idx = base + m * stride;
                     Srow[idx] = shoup(v[m], __ldg(ictw + idx), p);  // omega_T^(-c bitrev(row))
-                else
-                    sm[px(idx)] = v[m];
+                } else {
+                    sm[a0 + m * dsm] = v[m];
+                }
             }
         }
     }
 }
 
 // grid (R, 3 primes); blockDim = C / ACC threads, ACC accumulators each.
-template <int ACC>
-__global__ void __launch_bounds__(1024) k3_row_mac(Geo3 X, const u32 *__restrict__ Y, u32 *__restrict__ S3) {
+// PF: the next pair's first-round inputs are loaded while the current pair
+// is transformed (512 threads at most).
+template <int ACC, int LL, bool PF>
+__global__ void __launch_bounds__(PF ? 512 : 1024) k3_row_mac(Geo3 X, const u32 *__restrict__ Y, u32 *__restrict__ S3) {
     extern __shared__ u32 sm3[];
-    const u32 j = blockIdx.y, row = blockIdx.x, C = X.C, l = X.logC;
+    const u32 j = blockIdx.y, row = blockIdx.x, l = LL ? (u32)LL : X.logC, C = 1u << l;
     u32 *smx = sm3, *sma = sm3 + px(C);
-    u32 acc[ACC];
+    u32 acc[ACC], fx[ACC], fa[ACC];
 #pragma unroll
     for (int m = 0; m < ACC; m++) acc[m] = 0;
-    const u32 nr = (l + 2) / 3;
+    const u32 nr = (l + 2) / 3, ns0 = round_ns(l, 0);
+    auto rows = [&](u32 i, const u32 *&xr, const u32 *&ar) {
+        xr = Y + ((u64)j * 2 * X.K + i) * X.T + (u64)row * C;
+        ar = Y + ((u64)j * 2 * X.K + X.K + i) * X.T + (u64)row * C;
+    };
+#define P3_LOAD(NSV) row_load3<NSV, ACC, LL>(X, xr, ar, fx, fa)
+    if (PF) {
+        const u32 *xr, *ar;
+        rows(0, xr, ar);
+        P3_DISPATCH_NS(ns0, P3_LOAD);
+    }
     for (u32 i = 0; i < X.K; i++) {
-        const u32 *xrow = Y + ((u64)j * 2 * X.K + i) * X.T + (u64)row * C;
-        const u32 *arow = Y + ((u64)j * 2 * X.K + X.K + i) * X.T + (u64)row * C;
+        if (!PF) {  // load right before use: short register lifetimes
+            const u32 *xr, *ar;
+            rows(i, xr, ar);
+            P3_DISPATCH_NS(ns0, P3_LOAD);
+        }
+#pragma unroll(LL > 0 ? 8 : 1)
         for (u32 rd = 0; rd < nr; rd++) {
             const u32 s0 = round_s0(l, rd), ns = round_ns(l, rd);
             const bool first = rd == 0, last = rd == nr - 1;
 #define P3_ROWF(NSV)                                                                \
     do {                                                                            \
         if (last)                                                                   \
-            row_fwd3<NSV, ACC, true>(X, j, xrow, arow, smx, sma, s0, first, acc);   \
+            row_fwd3<NSV, ACC, true, LL>(X, j, fx, fa, smx, sma, s0, rd, first, acc);   \
         else                                                                        \
-            row_fwd3<NSV, ACC, false>(X, j, xrow, arow, smx, sma, s0, first, acc);  \
+            row_fwd3<NSV, ACC, false, LL>(X, j, fx, fa, smx, sma, s0, rd, first, acc);  \
     } while (0)
             P3_DISPATCH_NS(ns, P3_ROWF);
 #undef P3_ROWF
+            if (PF && first && i + 1 < X.K) {  // the next pair's inputs, in flight during this pair's rounds
+                const u32 *xr, *ar;
+                rows(i + 1, xr, ar);
+                P3_DISPATCH_NS(ns0, P3_LOAD);
+            }
             __syncthreads();
         }
     }
+#undef P3_LOAD
     u32 *Srow = S3 + (u64)j * X.T + (u64)row * C;
+#pragma unroll(LL > 0 ? 8 : 1)
     for (int rd = (int)nr - 1; rd >= 0; rd--) {
         const u32 s0 = round_s0(l, rd), ns = round_ns(l, rd);
         const bool from_acc = rd == (int)nr - 1, to_global = rd == 0;
 #define P3_ROWI(NSV)                                                          \
     do {                                                                      \
         if (from_acc)                                                         \
-            row_inv3<NSV, ACC, true>(X, j, smx, Srow, row, s0, to_global, acc);  \
+            row_inv3<NSV, ACC, true, LL>(X, j, smx, Srow, row, s0, rd, to_global, acc);  \
         else                                                                  \
-            row_inv3<NSV, ACC, false>(X, j, smx, Srow, row, s0, to_global, acc); \
+            row_inv3<NSV, ACC, false, LL>(X, j, smx, Srow, row, s0, rd, to_global, acc); \
     } while (0)
         P3_DISPATCH_NS(ns, P3_ROWI);
 #undef P3_ROWI
@@ -372,32 +530,33 @@ __global__ void __launch_bounds__(1024) k3_row_mac(Geo3 X, const u32 *__restrict
 
 // -------------------------------------------------------- inverse columns --
 
-template <int NS, bool FIRSTR, bool TOGLOBAL, bool HO>
+template <int NS, bool FIRSTR, bool TOGLOBAL, bool HO, int LL, int TC>
 __device__ __forceinline__ void inv3_round(const Geo3 &X, u32 j, u32 *__restrict__ S3, u32 *__restrict__ sm, u32 c0,
-                                           u32 s0) {
-    const u32 l = X.logR, tc = X.tc, p = X.p[j];
+                                           u32 s0, u32 rd) {
+    const u32 l = LL ? (u32)LL : X.logR, tc = TC ? (u32)TC : X.tc, p = X.p[j];
     const u32 sh = l - s0 - NS, stride = 1u << sh;
-    const u32 ntask = (X.R >> NS) * tc;
-    const u32 logtc = __ffs(tc) - 1;
+    const u32 ntask = ((1u << l) >> NS) * tc;
+    const u32 logtc = TC ? (u32)__builtin_ctz(TC) : (u32)(__ffs(tc) - 1);
+    const u32 dsm = pstep(stride * tc);
+    const u64 dY = (u64)stride * X.C;
+    const uint2 *itw = X.itwR[j] + X.rofR[rd];
     u32 *Sj = S3 + (u64)j * X.T;
     for (u32 task = threadIdx.x; task < ntask; task += blockDim.x) {
         const u32 c = task & (tc - 1), g = task >> logtc;
         const u32 lo = g & (stride - 1), base = ((g >> sh) << (l - s0)) + lo;
+        const u32 a0 = px(base * tc + c);
+        const u64 e0 = (u64)base * X.C + c0 + c;
         u32 v[8];
 #pragma unroll
-        for (int m = 0; m < (1 << NS); m++) {
-            const u32 r = base + m * stride;
-            v[m] = FIRSTR ? Sj[(u64)r * X.C + c0 + c] : sm[px(r * tc + c)];
-        }
-        dit3<NS, FIRSTR, HO>(v, s0, lo, stride, X.itwR[j], p);
+        for (int m = 0; m < (1 << NS); m++) v[m] = FIRSTR ? Sj[e0 + m * dY] : sm[a0 + m * dsm];
+        dit3<NS, FIRSTR, HO>(v, itw + lo * ((1u << NS) - 1), p);
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
-            const u32 r = base + m * stride;
             if (TOGLOBAL) {
                 if (HO && m >= (1 << (NS - 1))) continue;  // rows >= R/2: coefficients >= T/2, unused
-                Sj[(u64)r * X.C + c0 + c] = v[m];
+                Sj[e0 + m * dY] = v[m];
             } else {
-                sm[px(r * tc + c)] = v[m];
+                sm[a0 + m * dsm] = v[m];
             }
         }
     }
@@ -405,24 +564,26 @@ __device__ __forceinline__ void inv3_round(const Geo3 &X, u32 j, u32 *__restrict
 
 // grid (C / tc, 3 primes).  In place on S3: every CTA reads its own columns
 // completely (first round) before it writes them (last round).
+template <int LL, int TC>
 __global__ void __launch_bounds__(kColThreads) k3_inv_col(Geo3 X, u32 *__restrict__ S3) {
     extern __shared__ u32 sm3[];
-    const u32 j = blockIdx.y, tc = X.tc, c0 = blockIdx.x * tc;
-    const u32 l = X.logR, nr = (l + 2) / 3;
+    const u32 j = blockIdx.y, tc = TC ? (u32)TC : X.tc, c0 = blockIdx.x * tc;
+    const u32 l = LL ? (u32)LL : X.logR, nr = (l + 2) / 3;
     const bool ho = X.stage == 1;  // Eq. 4: only t mod 2^gamma, i.e. coefficients < T/2
+#pragma unroll(LL > 0 ? 8 : 1)
     for (int rd = (int)nr - 1; rd >= 0; rd--) {
         const u32 s0 = round_s0(l, rd), ns = round_ns(l, rd);
         const bool first = rd == (int)nr - 1, last = rd == 0;
 #define P3_INV(NSV)                                                       \
     do {                                                                  \
         if (first)                                                        \
-            inv3_round<NSV, true, false, false>(X, j, S3, sm3, c0, s0);   \
+            inv3_round<NSV, true, false, false, LL, TC>(X, j, S3, sm3, c0, s0, (u32)rd);   \
         else if (last && ho)                                              \
-            inv3_round<NSV, false, true, true>(X, j, S3, sm3, c0, s0);    \
+            inv3_round<NSV, false, true, true, LL, TC>(X, j, S3, sm3, c0, s0, (u32)rd);    \
         else if (last)                                                    \
-            inv3_round<NSV, false, true, false>(X, j, S3, sm3, c0, s0);   \
+            inv3_round<NSV, false, true, false, LL, TC>(X, j, S3, sm3, c0, s0, (u32)rd);   \
         else                                                              \
-            inv3_round<NSV, false, false, false>(X, j, S3, sm3, c0, s0);  \
+            inv3_round<NSV, false, false, false, LL, TC>(X, j, S3, sm3, c0, s0, (u32)rd);  \
     } while (0)
         P3_DISPATCH_NS(ns, P3_INV);
 #undef P3_INV
@@ -529,40 +690,71 @@ int p3_prepare_kernels() {
     if (done) return 0;
     const int big = 200 * 1024;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k3_fwd_col<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k3_fwd_col<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k3_row_mac<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k3_row_mac<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k3_inv_col, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+#define P3_ATTR(f) \
+    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    P3_ATTR((k3_fwd_col<true, 0, 0>))
+    P3_ATTR((k3_fwd_col_all<10, 8>))
+    P3_ATTR((k3_inv_col<0, 0>))
+    P3_ATTR((k3_inv_col<10, 8>))
+    P3_ATTR((k3_row_mac<8, 0, false>))
+    P3_ATTR((k3_row_mac<16, 0, false>))
+    P3_ATTR((k3_row_mac<8, 10, false>))
+    P3_ATTR((k3_row_mac<8, 11, false>))
+    P3_ATTR((k3_row_mac<8, 12, false>))
+    P3_ATTR((k3_row_mac<8, 13, false>))
+    P3_ATTR((k3_row_mac<16, 14, false>))
+#undef P3_ATTR
     done = true;
     return 0;
 }
 
+// Compile-time geometry for the production shapes (R = 2^10, 8-column tiles;
+// rows of 2^10 .. 2^14), runtime geometry otherwise.
 int p3_launch_fwd_col(const Geo3 &X, const Operands &S, int pairs, u32 *Y, void *stream) {
     if (int e = p3_prepare_kernels()) return e;
     const dim3 grid(X.C / X.tc, pairs, 3);
-    TRACED("p3_fwd_col", X.stage, stream,
-           (k3_fwd_col<true><<<grid, kColThreads, col_smem3(X, true), (cudaStream_t)stream>>>(X, S, Y)));
+    const size_t smem = col_smem3(X, true);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (X.logR == 10 && X.tc == 8)
+        TRACED("p3_fwd_col", X.stage, stream,
+               (k3_fwd_col_all<10, 8><<<dim3(X.C / X.tc, pairs), 512, smem, s>>>(X, S, Y)));
+    else
+        TRACED("p3_fwd_col", X.stage, stream, (k3_fwd_col<true, 0, 0><<<grid, kColThreads, smem, s>>>(X, S, Y)));
     return (int)cudaGetLastError();
 }
 
 int p3_launch_row_mac(const Geo3 &X, const u32 *Y, u32 *S3, void *stream) {
     if (int e = p3_prepare_kernels()) return e;
     const dim3 grid(X.R, 3);
-    if (X.C > 8192)
-        TRACED("p3_row_mac", X.stage, stream,
-               (k3_row_mac<16><<<grid, X.C / 16, row_smem3(X), (cudaStream_t)stream>>>(X, Y, S3)));
-    else
-        TRACED("p3_row_mac", X.stage, stream,
-               (k3_row_mac<8><<<grid, X.C / 8, row_smem3(X), (cudaStream_t)stream>>>(X, Y, S3)));
+    const size_t smem = row_smem3(X);
+    cudaStream_t s = (cudaStream_t)stream;
+#define P3_ROW(A, L, PF) \
+    TRACED("p3_row_mac", X.stage, stream, (k3_row_mac<A, L, PF><<<grid, X.C / A, smem, s>>>(X, Y, S3)))
+    switch (X.logC) {
+    case 10: P3_ROW(8, 10, false); break;
+    case 11: P3_ROW(8, 11, false); break;
+    case 12: P3_ROW(8, 12, false); break;
+    case 13: P3_ROW(8, 13, false); break;
+    case 14: P3_ROW(16, 14, false); break;
+    default:
+        if (X.C > 8192)
+            P3_ROW(16, 0, false);
+        else
+            P3_ROW(8, 0, false);
+    }
+#undef P3_ROW
     return (int)cudaGetLastError();
 }
 
 int p3_launch_inv_col(const Geo3 &X, u32 *S3, void *stream) {
     if (int e = p3_prepare_kernels()) return e;
     const dim3 grid(X.C / X.tc, 3);
-    TRACED("p3_inv_col", X.stage, stream,
-           (k3_inv_col<<<grid, kColThreads, col_smem3(X, false), (cudaStream_t)stream>>>(X, S3)));
+    const size_t smem = col_smem3(X, false);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (X.logR == 10 && X.tc == 8)
+        TRACED("p3_inv_col", X.stage, stream, (k3_inv_col<10, 8><<<grid, kColThreads, smem, s>>>(X, S3)));
+    else
+        TRACED("p3_inv_col", X.stage, stream, (k3_inv_col<0, 0><<<grid, kColThreads, smem, s>>>(X, S3)));
     return (int)cudaGetLastError();
 }
 
@@ -676,11 +868,32 @@ void geometry(Geo3 &X, const Choice &ch, uint64_t G, uint64_t K, u32 stage) {
     X.logC = l - X.logR;
     X.R = 1u << X.logR;
     X.C = 1u << X.logC;
+    // tile width: a multiple of 8 (32-byte row segments; linear padded addressing)
     u32 tc = std::min<u32>(16, 8192 / X.R);
     X.tc = std::min<u32>(tc, X.C);
 }
 
-uint64_t table_bytes(const Geo3 &X) { return 3ULL * (X.R + X.C + 2 * X.T) * sizeof(uint2); }
+// Round twiddle table of a length-2^l transform with root w (see Geo3).
+std::vector<uint2> round_table(u32 w, u32 l, u32 p, u32 *rof) {
+    std::vector<u32> pw(1u << l);
+    u64 a = 1;
+    for (size_t e = 0; e < pw.size(); e++, a = a * w % p) pw[e] = (u32)a;
+    std::vector<uint2> t;
+    const u32 nr = (l + 2) / 3, ns0 = l - 3 * (nr - 1);
+    u32 s0 = 0;
+    for (u32 rd = 0; rd < nr; rd++) {
+        const u32 ns = rd ? 3 : ns0, stride = 1u << (l - s0 - ns);
+        rof[rd] = (u32)t.size();
+        for (u32 lo = 0; lo < stride; lo++)
+            for (u32 sg = 0; sg < ns; sg++)
+                for (u32 jj = 0; jj < (1u << (ns - 1 - sg)); jj++)
+                    t.push_back(shoup_pair(pw[((lo + jj * stride) << (s0 + sg)) & ((1u << l) - 1)], p));
+        s0 += ns;
+    }
+    return t;
+}
+
+uint64_t table_bytes(const Geo3 &X) { return 3ULL * (4 * X.R + 4 * X.C + 2 * X.T) * sizeof(uint2); }
 
 }  // namespace
 
@@ -737,6 +950,10 @@ int build_tables(P3Plan *pl, Geo3 &X, const PrimeSet &ps, const Geo3 *other) {
             X.ctw[j] = other->ctw[j];
             X.ictw[j] = other->ictw[j];
         }
+        for (int rd = 0; rd < 6; rd++) {
+            X.rofR[rd] = other->rofR[rd];
+            X.rofC[rd] = other->rofC[rd];
+        }
         return PA_OK;
     }
     int err = PA_OK;
@@ -749,11 +966,8 @@ int build_tables(P3Plan *pl, Geo3 &X, const PrimeSet &ps, const Geo3 *other) {
         for (int dir = 0; dir < 2 && !err; dir++) {
             const u32 w = dir ? invmod(wT, p) : wT;
             const u32 wR = powmod(w, X.C, p), wC = powmod(w, X.R, p);
-            std::vector<uint2> tR(X.R / 2), tC(X.C / 2);
+            std::vector<uint2> tR = round_table(wR, X.logR, p, X.rofR), tC = round_table(wC, X.logC, p, X.rofC);
             u64 a = 1;
-            for (u32 e = 0; e < X.R / 2; e++, a = a * wR % p) tR[e] = shoup_pair((u32)a, p);
-            a = 1;
-            for (u32 e = 0; e < X.C / 2; e++, a = a * wC % p) tC[e] = shoup_pair((u32)a, p);
             uint2 *dR = (uint2 *)pl->alloc(tR.size() * sizeof(uint2), &err);
             uint2 *dC = (uint2 *)pl->alloc(tC.size() * sizeof(uint2), &err);
             uint2 *dT = (uint2 *)pl->alloc(X.T * sizeof(uint2), &err);

@@ -88,7 +88,7 @@ def test_backend_parameter_and_estimates():
     g = _lib.plan_estimate_bytes(260_000_000, 26_000_000, backend=_lib.BACKEND_GOLDILOCKS)
     p3 = _lib.plan_estimate_bytes(260_000_000, 26_000_000, backend=_lib.BACKEND_P3)
     auto = _lib.plan_estimate_bytes(260_000_000, 26_000_000)
-    assert auto == g and p3 > 0
+    assert auto == p3 and p3 > 0  # PA_BACKEND_AUTO takes the three-prime plan at this size
     assert 3 * 2 * 9 * (1 << 21) * 4 < p3 < 3 * g
     with pytest.raises(_lib.PAError) as e:
         _lib.plan_estimate_bytes(1000, 10, backend=3)

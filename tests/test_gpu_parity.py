@@ -212,17 +212,24 @@ def test_host_async_stream_of_blocks(backend):
     plan.close()
 
 
-def test_backend_lengths():
-    """Transform lengths of both backends at the 2.6e8-bit block and the
-    1e9-bit block; PA_BACKEND_AUTO gives the Goldilocks plan."""
+def test_backend_lengths_and_auto_choice():
+    """Transform lengths of both backends at the 2.6e8-bit and 1e9-bit blocks;
+    PA_BACKEND_AUTO takes the three-prime plan where its Eq. 2 transform is no
+    longer (2.6e8) and the Goldilocks plan where it would be (1e9)."""
     from paper_2105_13678_gb300 import _lib
     a = _lib.Plan(260_000_000, 26_000_000, backend=P3)
     assert a.info.mmh_len == 1 << 21 and a.info.mh_len == 1 << 21
-    g = _lib.Plan(260_000_000, 26_000_000)
-    assert g.backend == GOLDILOCKS and g.info.mmh_len == 1 << 21 and g.info.mh_len == 1 << 22
+    g = _lib.Plan(260_000_000, 26_000_000, backend=GOLDILOCKS)
+    assert g.info.mmh_len == 1 << 21 and g.info.mh_len == 1 << 22
+    auto = _lib.Plan(260_000_000, 26_000_000)
+    assert auto.backend == P3
     b = _lib.Plan(1_000_000_000, 100_000_000, backend=P3)
     assert b.info.mmh_len == 1 << 24
-    for p in (a, g, b):
+    b2 = _lib.Plan(1_000_000_000, 100_000_000)
+    assert b2.backend == GOLDILOCKS and b2.info.mmh_len == 1 << 23
+    small = _lib.Plan(1 << 20, 104858)
+    assert small.backend == GOLDILOCKS
+    for p in (a, g, auto, b, b2, small):
         p.close()
 
 
