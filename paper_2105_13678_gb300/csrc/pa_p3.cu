@@ -303,7 +303,9 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
     constexpr u32 LOGTC = __builtin_ctz(TC);
     static_assert(NT * NTH == NTASK0, "first-round tasks must divide evenly");
     extern __shared__ u32 sm3[];
-    const u32 c0 = blockIdx.x * TC, i = blockIdx.y + S.pair0;
+    // pairs vary fastest across the grid, so the tile's inter-pass twiddles are
+    // reused from L2 by the CTAs of all pairs
+    const u32 i = blockIdx.x + S.pair0, c0 = blockIdx.y * TC;
     Desc dx, da;
     descs(S, i, dx, da);
     u32 *smx = sm3, *sma = sm3 + px((1u << LL) * TC);
@@ -365,7 +367,7 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
         const int all = __syncthreads_and(ones ? 1 : 0);
         if (threadIdx.x == 0 && all) {
             int *cnt = S.reload + 4 + i;
-            if (atomicAdd(cnt, 1) + 1 == (int)gridDim.x) atomicExch(S.reload, 1);
+            if (atomicAdd(cnt, 1) + 1 == (int)gridDim.y) atomicExch(S.reload, 1);
         }
     }
 }
@@ -717,7 +719,7 @@ int p3_launch_fwd_col(const Geo3 &X, const Operands &S, int pairs, u32 *Y, void 
     cudaStream_t s = (cudaStream_t)stream;
     if (X.logR == 10 && X.tc == 8)
         TRACED("p3_fwd_col", X.stage, stream,
-               (k3_fwd_col_all<10, 8><<<dim3(X.C / X.tc, pairs), 512, smem, s>>>(X, S, Y)));
+               (k3_fwd_col_all<10, 8><<<dim3(pairs, X.C / X.tc), 512, smem, s>>>(X, S, Y)));
     else
         TRACED("p3_fwd_col", X.stage, stream, (k3_fwd_col<true, 0, 0><<<grid, kColThreads, smem, s>>>(X, S, Y)));
     return (int)cudaGetLastError();
