@@ -122,6 +122,13 @@ __device__ __forceinline__ void dit3(u32 (&v)[8], const uint2 *__restrict__ rt, 
 // so elements m * d apart, d a multiple of 8, are px(i) + m * (d + d / 8)).
 __device__ __forceinline__ u32 pstep(u32 d) { return d + (d >> 3); }
 
+// Column tiles ([row][8 columns]) use 8 pad words per 64: a warp's 4 rows x 8
+// columns are 32 consecutive words of one 64-word block (no conflicts), and
+// the final round's 4 groups of 8 rows land in 4 different bank octets.
+// Steps of 8 words stay inside a block; steps of 64k words add 72k.
+__device__ __forceinline__ u32 pxc(u32 i) { return i + ((i >> 6) << 3); }
+__device__ __forceinline__ u32 pstepc(u32 d) { return d >= 64 ? d + (d >> 3) : d; }
+
 #define P3_DISPATCH_NS(ns, F) \
     do {                      \
         if ((ns) == 3)        \
@@ -207,14 +214,14 @@ __device__ __forceinline__ void fwd3_round(const Geo3 &X, u32 j, const Desc &dx,
     const u32 sh = l - s0 - NS, stride = 1u << sh;
     const u32 ntask = ((1u << l) >> NS) * tc;
     const u32 logtc = TC ? (u32)__builtin_ctz(TC) : (u32)(__ffs(tc) - 1);
-    const u32 dsm = pstep(stride * tc);  // tc is a multiple of 8
+    const u32 dsm = pstepc(stride * tc);  // tc = 8
     const u64 dY = (u64)stride * X.C;
     const uint2 red = X.red[j];
     const uint2 *tw = X.twR[j] + X.rofR[rd];
     for (u32 task = threadIdx.x; task < ntask; task += blockDim.x) {
         const u32 c = task & (tc - 1), g = task >> logtc;
         const u32 lo = g & (stride - 1), base = ((g >> sh) << (l - s0)) + lo;
-        const u32 a0 = px(base * tc + c);
+        const u32 a0 = pxc(base * tc + c);
         const u64 e0 = (u64)base * X.C + c0 + c;
         u32 vx[8], va[8];
 #pragma unroll
@@ -259,7 +266,7 @@ __global__ void __launch_bounds__(kColThreads) k3_fwd_col(Geo3 X, Operands S, u3
     descs(S, i, dx, da);
     if (j) dx.check_ones = 0;
     u32 *Yx = Y + ((u64)j * 2 * X.K + i) * X.T, *Ya = Y + ((u64)j * 2 * X.K + X.K + i) * X.T;
-    u32 *smx = sm3, *sma = sm3 + px(X.R * tc);
+    u32 *smx = sm3, *sma = sm3 + pxc(X.R * tc);
     bool ones = true;
     const u32 l = LL ? (u32)LL : X.logR, nr = (l + 2) / 3;
 #pragma unroll(LL > 0 ? 8 : 1)
@@ -308,7 +315,7 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
     const u32 i = blockIdx.x + S.pair0, c0 = blockIdx.y * TC;
     Desc dx, da;
     descs(S, i, dx, da);
-    u32 *smx = sm3, *sma = sm3 + px((1u << LL) * TC);
+    u32 *smx = sm3, *sma = sm3 + pxc((1u << LL) * TC);
     bool ones = true;
     u32 rx[NT][HALF0], ra[NT][HALF0];
 #pragma unroll
@@ -334,8 +341,8 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
         for (u32 t = 0; t < NT; t++) {
             const u32 task = threadIdx.x + t * NTH;
             const u32 c = task & (TC - 1), g = task >> LOGTC;
-            const u32 a0 = px(g * TC + c);
-            constexpr u32 dsm = ((1u << SH0) * TC) + (((1u << SH0) * TC) >> 3);
+            const u32 a0 = pxc(g * TC + c);
+            constexpr u32 dsm = ((1u << SH0) * TC) + (((1u << SH0) * TC) >> 3);  // a multiple of 64 words apart
             u32 vx[8], va[8];
 #pragma unroll
             for (u32 m = 0; m < (1u << NS0); m++) {
@@ -539,14 +546,14 @@ __device__ __forceinline__ void inv3_round(const Geo3 &X, u32 j, u32 *__restrict
     const u32 sh = l - s0 - NS, stride = 1u << sh;
     const u32 ntask = ((1u << l) >> NS) * tc;
     const u32 logtc = TC ? (u32)__builtin_ctz(TC) : (u32)(__ffs(tc) - 1);
-    const u32 dsm = pstep(stride * tc);
+    const u32 dsm = pstepc(stride * tc);
     const u64 dY = (u64)stride * X.C;
     const uint2 *itw = X.itwR[j] + X.rofR[rd];
     u32 *Sj = S3 + (u64)j * X.T;
     for (u32 task = threadIdx.x; task < ntask; task += blockDim.x) {
         const u32 c = task & (tc - 1), g = task >> logtc;
         const u32 lo = g & (stride - 1), base = ((g >> sh) << (l - s0)) + lo;
-        const u32 a0 = px(base * tc + c);
+        const u32 a0 = pxc(base * tc + c);
         const u64 e0 = (u64)base * X.C + c0 + c;
         u32 v[8];
 #pragma unroll
@@ -683,7 +690,7 @@ __global__ void k3_fill_ctw(u32 logR, u32 logC, u32 h, const u32 *__restrict__ l
 using namespace p3;
 
 static size_t col_smem3(const Geo3 &X, bool pair) {
-    return (size_t)(pair ? 2 : 1) * (X.R * X.tc + (X.R * X.tc >> 3) + 8) * sizeof(u32);
+    return (size_t)(pair ? 2 : 1) * (X.R * X.tc + ((X.R * X.tc >> 6) << 3) + 8) * sizeof(u32);
 }
 static size_t row_smem3(const Geo3 &X) { return (size_t)2 * (X.C + (X.C >> 3) + 8) * sizeof(u32); }
 
@@ -870,9 +877,8 @@ void geometry(Geo3 &X, const Choice &ch, uint64_t G, uint64_t K, u32 stage) {
     X.logC = l - X.logR;
     X.R = 1u << X.logR;
     X.C = 1u << X.logC;
-    // tile width: a multiple of 8 (32-byte row segments; linear padded addressing)
-    u32 tc = std::min<u32>(16, 8192 / X.R);
-    X.tc = std::min<u32>(tc, X.C);
+    // tile width 8: 32-byte row segments, and the padded addressing of pxc()
+    X.tc = 8;
 }
 
 // Round twiddle table of a length-2^l transform with root w (see Geo3).
