@@ -457,9 +457,10 @@ def roofline(info, trace, steps, peaks, peak_kind, step_ms, geometries=None):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     # integer ALU pipe: 16 lanes per SM sub-partition x 4 x 152 SMs at the
-    # maximum SM clock; F_q products: 64 IMAD/clk/SM, 8 IMAD issue slots each
+    # maximum SM clock; modular products: 64 IMAD/clk/SM, 8 IMAD issue slots per
+    # F_q product, 3 per 32-bit Shoup product (three-prime kernels)
     alu_peak = 152 * 64 * sm_mhz * 1e6
-    mul_peak = 152 * 64 * sm_mhz * 1e6 / 8
+    mul_peak = 152 * 64 * sm_mhz * 1e6 / (3 if kern.startswith("p3_") else 8)
     out = {"kernel": name, "launches": launches, "avg_us": round(avg_s * 1e6, 2),
            "share_of_step": round(tot / max(1e-9, sum(step_ms)), 3)}
     if bytes_ is None:
