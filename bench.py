@@ -257,10 +257,32 @@ def run_gb300(args):
         dist.barrier()
     torch.cuda.synchronize()
 
+    L = _lib.lib()
+
+    def traced_pass(steps):
+        """Every kernel bracketed by events (a separate loop: the events between
+        kernels cost a few percent of the step)."""
+        _lib.trace_select(None)
+        _lib.trace_enable(True)
+        for _ in range(steps):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize()
+        tr = _lib.trace_collect()
+        _lib.trace_enable(False)
+        return tr
+
+    # the dominant kernel, found on a short traced pass before the timed region
+    pre = traced_pass(2)
+    dominant = max(pre.items(), key=lambda kv: kv[1][1])[0]
+    torch.cuda.synchronize()
+
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    L = _lib.lib()
+    # timed region: only the dominant kernel is bracketed by events (its live
+    # duration for the roofline); nothing is recorded between the other kernels
+    _lib.trace_select(dominant)
     _lib.trace_enable(True)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     wall0 = time.perf_counter()
@@ -271,8 +293,9 @@ def run_gb300(args):
         e1.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
-    trace = _lib.trace_collect()
+    trace_dom = _lib.trace_collect()
     _lib.trace_enable(False)
+    _lib.trace_select(None)
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = reduce_max(sum(step_ms), dist, "cuda")
@@ -281,7 +304,8 @@ def run_gb300(args):
     torch.cuda.synchronize()
     status = int(dstat.item())
 
-    # per-kernel device time inside the timed region: `trace` (collected above)
+    # per-kernel device time of every kernel: a traced repeat of the timed loop
+    trace = traced_pass(args.steps)
     launches_per_step = sum(v[0] for v in trace.values()) / max(1, args.steps)
 
     # the other backend on the same block (same bits), and seed reuse, which
@@ -348,8 +372,10 @@ def run_gb300(args):
 
     value = job_mbps(n, args.steps, ws, total_ms)
     peaks, peak_kind = measured_peaks()
-    roof = roofline(info, trace, args.steps, peaks, peak_kind, step_ms,
+    roof = roofline(info, trace_dom, args.steps, peaks, peak_kind, step_ms,
                     {"mmh": plan.geometry(0), "mh": plan.geometry(1)})
+    if roof is not None:
+        roof["timing"] = "CUDA events around this kernel's launches inside the timed region (no other events there)"
 
     line = {
         "metric": METRIC,
@@ -382,6 +408,7 @@ def run_gb300(args):
         "backends": backends,
         "kernels": {k_: {"launches": v[0], "avg_us": round(1e3 * v[1] / max(1, v[0]), 2)}
                     for k_, v in sorted(trace.items(), key=lambda kv: -kv[1][1])},
+        "kernels_source": "traced repeat of the timed loop (events around every kernel)",
         "step_ms_p50": round(statistics.median(step_ms), 4),
         "step_ms_max": round(max(step_ms), 4),
         "paper_context": {"mbps": PAPER_MBPS, "hardware": "Intel i5-7300HQ, GMP (CPU)"},
@@ -519,19 +546,24 @@ def run_sweep(steps: int = 5):
         for _ in range(2):
             _lib.pa_hash(plan, dk.data_ptr(), ds.data_ptr(), do.data_ptr(), st.data_ptr(), stream.cuda_stream)
         torch.cuda.synchronize()
-        _lib.trace_enable(True)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        for e0, e1 in evs:
-            flush.zero_()
-            e0.record(stream)
-            _lib.pa_hash(plan, dk.data_ptr(), ds.data_ptr(), do.data_ptr(), st.data_ptr(), stream.cuda_stream)
-            e1.record(stream)
-        torch.cuda.synchronize()
-        trace = _lib.trace_collect()
-        _lib.trace_enable(False)
-        step_ms = [a.elapsed_time(b_) for a, b_ in evs]
+
+        def loop(traced):
+            _lib.trace_enable(traced)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for e0, e1 in evs:
+                flush.zero_()
+                e0.record(stream)
+                _lib.pa_hash(plan, dk.data_ptr(), ds.data_ptr(), do.data_ptr(), st.data_ptr(), stream.cuda_stream)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            tr = _lib.trace_collect() if traced else {}
+            _lib.trace_enable(False)
+            return [a.elapsed_time(b_) for a, b_ in evs], tr
+
+        step_ms, _ = loop(False)           # the block time: no events between kernels
         ms = sum(step_ms) / steps
-        roof = roofline(plan.info, trace, steps, peaks, peak_kind, step_ms,
+        tr_ms, trace = loop(True)          # per-kernel times: a traced repeat
+        roof = roofline(plan.info, trace, steps, peaks, peak_kind, tr_ms,
                         {"mmh": plan.geometry(0), "mh": plan.geometry(1)})
         out.append({"n_bits": n, "r_bits": r, "gamma": plan.gamma, "k": plan.k, "mmh_len": plan.info.mmh_len,
                     "mh_len": plan.info.mh_len, "ms_per_block": round(ms, 4), "mbps": round(n / ms / 1e3, 1),

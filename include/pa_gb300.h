@@ -220,6 +220,11 @@ typedef struct pa_trace_entry {
 } pa_trace_entry;
 int pa_trace_enable(int on);
 int pa_trace_collect(pa_trace_entry *out, int max_entries, int *count);
+/* Restrict tracing to the launches named `name` ("mmh.<kernel>" or
+ * "mh.<kernel>", as pa_trace_collect reports them), so that one kernel can
+ * be timed with two events per launch and nothing between the others;
+ * NULL or "" traces every launch again.  Host-only; never fails. */
+int pa_trace_select(const char *name);
 
 /* ---- diagnostics for host-side checks (no device work) --------------------
  * pa_plan_estimate_bytes: device bytes pa_plan would allocate for (n, r).

@@ -83,6 +83,7 @@ SIGNATURES = {
     "pa_serve_destroy": (ctypes.c_int, [_vp]),
     "pa_trace_enable": (ctypes.c_int, [ctypes.c_int]),
     "pa_trace_collect": (ctypes.c_int, [ctypes.POINTER(pa_trace_entry), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "pa_trace_select": (ctypes.c_int, [ctypes.c_char_p]),
     "pa_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pa_version": (ctypes.c_char_p, []),
     "pa_plan_estimate_bytes": (ctypes.c_int, [_u64, _u64, ctypes.POINTER(pa_params), ctypes.POINTER(_u64)]),
@@ -221,6 +222,11 @@ def pa_hash_batch(plans, key_ptrs, seed_ptrs, out_ptrs, statuses_ptr: int = 0, s
 
 def trace_enable(on: bool) -> None:
     check(lib().pa_trace_enable(1 if on else 0), "pa_trace_enable")
+
+
+def trace_select(name: str | None) -> None:
+    """Record only the launches called `name` (None: all)."""
+    check(lib().pa_trace_select(name.encode() if name else None), "pa_trace_select")
 
 
 def trace_collect() -> dict:

@@ -168,6 +168,33 @@ int choose_params(uint64_t n_bits, uint64_t r_bits, const struct pa_params *para
 void *trace_begin(const char *name, u32 stage, void *stream);
 void trace_end(void *token, void *stream);
 
+// Programmatic dependent launch.  Kernels of a stream sequence are launched
+// with programmatic stream serialization: the next grid may be scheduled while
+// the previous one drains (each CTA signals once its stores are issued), and
+// it waits at pdl_wait() -- before touching any memory -- until the previous
+// grid has completed and its writes are visible.  Launched without the
+// attribute, both are no-ops.
+#if defined(__CUDACC__)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+#endif
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<Args &&>(args)...);
+}
+
 // Every launch goes through TRACED(): when tracing is on (pa_trace_enable) and
 // the stream is not being captured, a CUDA event pair is recorded on the
 // launching stream around the kernel.
@@ -193,10 +220,10 @@ int launch_carry(const Xform &X, const CarryDev &cd, u64 *z, u64 *out_bits, u64 
 // digits for the single-thread path), ring or linear per cd.linear; parallel
 // when there are enough chunks and every chunk spans at least 64 bits.
 int launch_carry_chunks(const CarryDev &cd, u64 ndigits, bool wide_chunks, u32 stage, u64 *z, u64 *out_bits,
-                        u64 out_words, void *stream);
+                        u64 out_words, void *stream, bool zeroed = false, bool pdl = false);
 int launch_extract(const u64 *t, u64 gamma, u64 r, const int *reload, u64 k, u64 *out,
-                   int *status, void *stream);
-int launch_canonical_zero(const int *flag, u64 *y, u64 words, void *stream);
+                   int *status, void *stream, bool pdl = false);
+int launch_canonical_zero(const int *flag, u64 *y, u64 words, void *stream, bool pdl = false);
 int launch_selftest_field(const u64 *a, const u64 *b, u64 *out, u64 n, void *stream);
 int launch_fill_coltw(const Xform &X, u64 *coltw, void *stream);
 
@@ -205,7 +232,8 @@ int p3_prepare_kernels();
 int p3_launch_fwd_col(const Geo3 &X, const Operands &S, int pairs, u32 *Y, void *stream);
 int p3_launch_row_mac(const Geo3 &X, const u32 *Y, u32 *S3, void *stream);
 int p3_launch_inv_col(const Geo3 &X, u32 *S3, void *stream);
-int p3_launch_digits(const Geo3 &X, const u32 *S3, u64 *z, u64 npad, const u64 *c_src, u64 c_base, void *stream);
+int p3_launch_digits(const Geo3 &X, const u32 *S3, u64 *z, u64 npad, const u64 *c_src, u64 c_base, u64 *zero_out,
+                     u64 zero_words, void *stream);
 int p3_launch_fill_ctw(u32 logR, u32 logC, u32 h, const u32 *lo, const u32 *hi, u32 p, uint2 *out, void *stream);
 
 // Three-prime plans (pa_p3.cu).

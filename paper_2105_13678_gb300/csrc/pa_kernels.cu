@@ -623,6 +623,7 @@ __device__ __forceinline__ u64 chunk_carry_out(const CarryDev &cd, const u64 *__
 }
 
 __global__ void __launch_bounds__(PA_CARRY_T) k_carry_a(CarryDev cd, const u64 *__restrict__ z, u64 *__restrict__ y) {
+    pdl_wait();
     __shared__ u64 Hs[PA_CARRY_T];
     __shared__ u64 Hprev;
     __shared__ unsigned wg[PA_CARRY_T / 32], wp[PA_CARRY_T / 32];
@@ -708,6 +709,7 @@ __global__ void __launch_bounds__(PA_CARRY_T) k_carry_a(CarryDev cd, const u64 *
 // carry in) wraps to bit 0; if every range propagates, the value is all ones
 // and no carry is taken.
 __global__ void __launch_bounds__(1024) k_carry_b(CarryDev cd, u32 nctas) {
+    pdl_wait();
     __shared__ unsigned wG[32], wP[32], wcin[32];
     const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const u32 per = (nctas + 1023) / 1024;
@@ -743,6 +745,7 @@ __global__ void __launch_bounds__(1024) k_carry_b(CarryDev cd, u32 nctas) {
 }
 
 __global__ void __launch_bounds__(PA_CARRY_T) k_carry_c(CarryDev cd, u64 *__restrict__ y) {
+    pdl_wait();
     __shared__ unsigned wg[PA_CARRY_T / 32], wp[PA_CARRY_T / 32];
     const u64 t = (u64)blockIdx.x * PA_CARRY_T + threadIdx.x;
     const bool act = t < cd.nchunks;
@@ -790,6 +793,7 @@ __global__ void __launch_bounds__(PA_CARRY_T) k_carry_c(CarryDev cd, u64 *__rest
 // Small transforms: one thread resolves the digits sequentially (around the
 // ring, or linearly dropping the top carry).
 __global__ void k_carry_seq(CarryDev cd, u64 ndigits, u64 *__restrict__ z, u64 *__restrict__ y) {
+    pdl_wait();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     unsigned __int128 c = 0;
     for (int pass = 0; pass < 8; pass++) {
@@ -819,6 +823,7 @@ __global__ void k_carry_seq(CarryDev cd, u64 ndigits, u64 *__restrict__ z, u64 *
 // Eq. 4: out = bits [gamma - r, gamma) of t = b*y + c; zero on reload.
 __global__ void k_extract(const u64 *__restrict__ t, u64 gamma, u64 r, const int *__restrict__ reload,
                           u64 *__restrict__ out, int *status) {
+    pdl_wait();
     const u64 w = (u64)blockIdx.x * blockDim.x + threadIdx.x;
     const u64 nw = (r + 63) >> 6;
     const bool rl = *reload != 0;
@@ -840,6 +845,7 @@ __global__ void k_extract(const u64 *__restrict__ t, u64 gamma, u64 r, const int
 }
 
 __global__ void k_canonical_zero(const int *__restrict__ flag, u64 *__restrict__ y, u64 words) {
+    pdl_wait();
     if (*flag == 0) return;
     for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (u64)gridDim.x * blockDim.x) y[i] = 0;
 }
@@ -1002,21 +1008,32 @@ int launch_inv_col(const Xform &X, const u64 *S, u64 *Z, const u64 *add_src, u64
 }
 
 int launch_carry_chunks(const CarryDev &cd, u64 ndigits, bool wide_chunks, u32 stage, u64 *z, u64 *out_bits,
-                        u64 out_words, void *stream) {
+                        u64 out_words, void *stream, bool zeroed, bool pdl) {
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaMemsetAsync(out_bits, 0, out_words * sizeof(u64), s);
-    if (e) return e;
+    if (!zeroed) {
+        cudaError_t e = cudaMemsetAsync(out_bits, 0, out_words * sizeof(u64), s);
+        if (e) return e;
+    }
     // chunks of PA_CARRY_D digits must span >= 64 bits so that adding the
     // previous chunk's carry-out leaves a 1-bit carry
     const bool parallel = cd.nchunks >= PA_CARRY_T && wide_chunks;
     if (!parallel) {
-        TRACED("carry_seq", stage, stream, (k_carry_seq<<<1, 32, 0, s>>>(cd, ndigits, z, out_bits)));
+        if (pdl)
+            TRACED("carry_seq", stage, stream, (launch_pdl(k_carry_seq, dim3(1), dim3(32), 0, s, cd, ndigits, z, out_bits)));
+        else
+            TRACED("carry_seq", stage, stream, (k_carry_seq<<<1, 32, 0, s>>>(cd, ndigits, z, out_bits)));
         return (int)cudaGetLastError();
     }
     const u32 nctas = (u32)((cd.nchunks + PA_CARRY_T - 1) / PA_CARRY_T);
-    TRACED("carry_a", stage, stream, (k_carry_a<<<nctas, PA_CARRY_T, 0, s>>>(cd, z, out_bits)));
-    TRACED("carry_b", stage, stream, (k_carry_b<<<1, 1024, 0, s>>>(cd, nctas)));
-    TRACED("carry_c", stage, stream, (k_carry_c<<<nctas, PA_CARRY_T, 0, s>>>(cd, out_bits)));
+    if (pdl) {
+        TRACED("carry_a", stage, stream, (launch_pdl(k_carry_a, dim3(nctas), dim3(PA_CARRY_T), 0, s, cd, (const u64 *)z, out_bits)));
+        TRACED("carry_b", stage, stream, (launch_pdl(k_carry_b, dim3(1), dim3(1024), 0, s, cd, nctas)));
+        TRACED("carry_c", stage, stream, (launch_pdl(k_carry_c, dim3(nctas), dim3(PA_CARRY_T), 0, s, cd, out_bits)));
+    } else {
+        TRACED("carry_a", stage, stream, (k_carry_a<<<nctas, PA_CARRY_T, 0, s>>>(cd, z, out_bits)));
+        TRACED("carry_b", stage, stream, (k_carry_b<<<1, 1024, 0, s>>>(cd, nctas)));
+        TRACED("carry_c", stage, stream, (k_carry_c<<<nctas, PA_CARRY_T, 0, s>>>(cd, out_bits)));
+    }
     return (int)cudaGetLastError();
 }
 
@@ -1030,17 +1047,27 @@ int launch_carry(const Xform &X, const CarryDev &cd_in, u64 *z, u64 *out_bits, u
     return launch_carry_chunks(cd, ndigits, (X.G >> X.logN) * PA_CARRY_D >= 64, X.stage, z, out_bits, out_words, stream);
 }
 
-int launch_extract(const u64 *t, u64 gamma, u64 r, const int *reload, u64 k, u64 *out, int *status, void *stream) {
+int launch_extract(const u64 *t, u64 gamma, u64 r, const int *reload, u64 k, u64 *out, int *status, void *stream,
+                   bool pdl) {
     (void)k;
     const u64 nw = (r + 63) >> 6;
     const u32 threads = 256;
     const u64 blocks = (nw + threads - 1) / threads;
-    TRACED("extract", 1, stream, (k_extract<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(t, gamma, r, reload, out, status)));
+    if (pdl)
+        TRACED("extract", 1, stream,
+               (launch_pdl(k_extract, dim3((unsigned)blocks), dim3(threads), 0, (cudaStream_t)stream, t, gamma, r,
+                           reload, out, status)));
+    else
+        TRACED("extract", 1, stream, (k_extract<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(t, gamma, r, reload, out, status)));
     return (int)cudaGetLastError();
 }
 
-int launch_canonical_zero(const int *flag, u64 *y, u64 words, void *stream) {
-    TRACED("canonical_zero", 0, stream, (k_canonical_zero<<<64, 256, 0, (cudaStream_t)stream>>>(flag, y, words)));
+int launch_canonical_zero(const int *flag, u64 *y, u64 words, void *stream, bool pdl) {
+    if (pdl)
+        TRACED("canonical_zero", 0, stream,
+               (launch_pdl(k_canonical_zero, dim3(64), dim3(256), 0, (cudaStream_t)stream, flag, y, words)));
+    else
+        TRACED("canonical_zero", 0, stream, (k_canonical_zero<<<64, 256, 0, (cudaStream_t)stream>>>(flag, y, words)));
     return (int)cudaGetLastError();
 }
 

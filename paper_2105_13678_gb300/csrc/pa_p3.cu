@@ -224,6 +224,11 @@ __device__ __forceinline__ void fwd3_round(const Geo3 &X, u32 j, const Desc &dx,
         const u32 a0 = pxc(base * tc + c);
         const u64 e0 = (u64)base * X.C + c0 + c;
         u32 vx[8], va[8];
+        uint2 ct[LAST ? 8 : 1];
+        if (LAST) {  // inter-pass twiddles first: their L2 latency overlaps the round's arithmetic
+#pragma unroll
+            for (int m = 0; m < (1 << NS); m++) ct[LAST ? m : 0] = __ldg(X.ctw[j] + e0 + m * dY);
+        }
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
             if (FIRST && m >= (1 << (NS - 1))) {  // rows >= R/2: digit slots >= T/2 are zero
@@ -246,7 +251,7 @@ __device__ __forceinline__ void fwd3_round(const Geo3 &X, u32 j, const Desc &dx,
             if (LAST) {
                 // position r holds column frequency bitrev(r): times omega_T^(c bitrev(r))
                 const u64 e = e0 + m * dY;
-                const uint2 t = __ldg(X.ctw[j] + e);
+                const uint2 t = ct[LAST ? m : 0];
                 Yx[e] = shoup(vx[m], t, p);
                 if (PAIR) Ya[e] = shoup(va[m], t, p);
             } else {
@@ -260,6 +265,7 @@ __device__ __forceinline__ void fwd3_round(const Geo3 &X, u32 j, const Desc &dx,
 // grid (C / tc, pairs, 3 primes): a tile of tc columns of pair blockIdx.y + pair0.
 template <bool PAIR, int LL, int TC>
 __global__ void __launch_bounds__(kColThreads) k3_fwd_col(Geo3 X, Operands S, u32 *__restrict__ Y) {
+    pdl_wait();
     extern __shared__ u32 sm3[];
     const u32 j = blockIdx.z, tc = TC ? (u32)TC : X.tc, c0 = blockIdx.x * tc, i = blockIdx.y + S.pair0;
     Desc dx, da;
@@ -286,6 +292,7 @@ __global__ void __launch_bounds__(kColThreads) k3_fwd_col(Geo3 X, Operands S, u3
 #undef P3_FWD
         __syncthreads();
     }
+    pdl_trigger();
     if (dx.check_ones) {
         // Algorithm 1 reload rule: slice i is all ones iff every CTA of the slice saw only ones
         const int all = __syncthreads_and(ones ? 1 : 0);
@@ -301,6 +308,7 @@ __global__ void __launch_bounds__(kColThreads) k3_fwd_col(Geo3 X, Operands S, u3
 // each prime runs its column transform through the same shared tile.
 template <int LL, int TC>
 __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32 *__restrict__ Y) {
+    pdl_wait();
     constexpr u32 NTH = 512;
     constexpr u32 NS0 = LL - 3 * ((LL + 2) / 3 - 1);
     constexpr u32 HALF0 = 1u << (NS0 - 1);
@@ -369,6 +377,7 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
             __syncthreads();
         }
     }
+    pdl_trigger();
     if (dx.check_ones) {
         // Algorithm 1 reload rule: slice i is all ones iff every CTA of the slice saw only ones
         const int all = __syncthreads_and(ones ? 1 : 0);
@@ -474,6 +483,7 @@ __device__ __forceinline__ void row_inv3(const Geo3 &X, u32 j, u32 *__restrict__
 // is transformed (512 threads at most).
 template <int ACC, int LL, bool PF>
 __global__ void __launch_bounds__(PF ? 512 : 1024) k3_row_mac(Geo3 X, const u32 *__restrict__ Y, u32 *__restrict__ S3) {
+    pdl_wait();
     extern __shared__ u32 sm3[];
     const u32 j = blockIdx.y, row = blockIdx.x, l = LL ? (u32)LL : X.logC, C = 1u << l;
     u32 *smx = sm3, *sma = sm3 + px(C);
@@ -535,6 +545,7 @@ __global__ void __launch_bounds__(PF ? 512 : 1024) k3_row_mac(Geo3 X, const u32 
 #undef P3_ROWI
         __syncthreads();
     }
+    pdl_trigger();
 }
 
 // -------------------------------------------------------- inverse columns --
@@ -575,6 +586,7 @@ __device__ __forceinline__ void inv3_round(const Geo3 &X, u32 j, u32 *__restrict
 // completely (first round) before it writes them (last round).
 template <int LL, int TC>
 __global__ void __launch_bounds__(kColThreads) k3_inv_col(Geo3 X, u32 *__restrict__ S3) {
+    pdl_wait();
     extern __shared__ u32 sm3[];
     const u32 j = blockIdx.y, tc = TC ? (u32)TC : X.tc, c0 = blockIdx.x * tc;
     const u32 l = LL ? (u32)LL : X.logR, nr = (l + 2) / 3;
@@ -598,6 +610,7 @@ __global__ void __launch_bounds__(kColThreads) k3_inv_col(Geo3 X, u32 *__restric
 #undef P3_INV
         __syncthreads();
     }
+    pdl_trigger();
 }
 
 // ------------------------------------------------------ CRT and Mersenne fold --
@@ -642,8 +655,10 @@ __device__ __forceinline__ u64 position_sum(const Geo3 &X, const u32 *__restrict
 // c (bits [c_base, c_base + gamma) of c_src).
 template <bool RING>
 __global__ void k3_digits(Geo3 X, const u32 *__restrict__ S3, u64 *__restrict__ z, u64 npad, const u64 *__restrict__ c_src,
-                          u64 c_base) {
+                          u64 c_base, u64 *__restrict__ zero_out, u64 zero_words) {
+    pdl_wait();
     const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < zero_words) zero_out[t] = 0;  // the carry kernels OR their bits into it
     if (t >= npad) return;
     if (t >= X.nd) {
         z[t] = 0;
@@ -726,9 +741,10 @@ int p3_launch_fwd_col(const Geo3 &X, const Operands &S, int pairs, u32 *Y, void 
     cudaStream_t s = (cudaStream_t)stream;
     if (X.logR == 10 && X.tc == 8)
         TRACED("p3_fwd_col", X.stage, stream,
-               (k3_fwd_col_all<10, 8><<<dim3(pairs, X.C / X.tc), 512, smem, s>>>(X, S, Y)));
+               (launch_pdl(k3_fwd_col_all<10, 8>, dim3(pairs, X.C / X.tc), dim3(512), smem, s, X, S, Y)));
     else
-        TRACED("p3_fwd_col", X.stage, stream, (k3_fwd_col<true, 0, 0><<<grid, kColThreads, smem, s>>>(X, S, Y)));
+        TRACED("p3_fwd_col", X.stage, stream,
+               (launch_pdl(k3_fwd_col<true, 0, 0>, grid, dim3(kColThreads), smem, s, X, S, Y)));
     return (int)cudaGetLastError();
 }
 
@@ -737,8 +753,9 @@ int p3_launch_row_mac(const Geo3 &X, const u32 *Y, u32 *S3, void *stream) {
     const dim3 grid(X.R, 3);
     const size_t smem = row_smem3(X);
     cudaStream_t s = (cudaStream_t)stream;
-#define P3_ROW(A, L, PF) \
-    TRACED("p3_row_mac", X.stage, stream, (k3_row_mac<A, L, PF><<<grid, X.C / A, smem, s>>>(X, Y, S3)))
+#define P3_ROW(A, L, PF)                     \
+    TRACED("p3_row_mac", X.stage, stream,      \
+           (launch_pdl(k3_row_mac<A, L, PF>, grid, dim3(X.C / A), smem, s, X, Y, S3)))
     switch (X.logC) {
     case 10: P3_ROW(8, 10, false); break;
     case 11: P3_ROW(8, 11, false); break;
@@ -761,21 +778,25 @@ int p3_launch_inv_col(const Geo3 &X, u32 *S3, void *stream) {
     const size_t smem = col_smem3(X, false);
     cudaStream_t s = (cudaStream_t)stream;
     if (X.logR == 10 && X.tc == 8)
-        TRACED("p3_inv_col", X.stage, stream, (k3_inv_col<10, 8><<<grid, kColThreads, smem, s>>>(X, S3)));
+        TRACED("p3_inv_col", X.stage, stream, (launch_pdl(k3_inv_col<10, 8>, grid, dim3(kColThreads), smem, s, X, S3)));
     else
-        TRACED("p3_inv_col", X.stage, stream, (k3_inv_col<0, 0><<<grid, kColThreads, smem, s>>>(X, S3)));
+        TRACED("p3_inv_col", X.stage, stream, (launch_pdl(k3_inv_col<0, 0>, grid, dim3(kColThreads), smem, s, X, S3)));
     return (int)cudaGetLastError();
 }
 
-int p3_launch_digits(const Geo3 &X, const u32 *S3, u64 *z, u64 npad, const u64 *c_src, u64 c_base, void *stream) {
+int p3_launch_digits(const Geo3 &X, const u32 *S3, u64 *z, u64 npad, const u64 *c_src, u64 c_base, u64 *zero_out,
+                     u64 zero_words, void *stream) {
     const u32 threads = 256;
-    const u64 blocks = (npad + threads - 1) / threads;
+    const u64 blocks = (std::max(npad, zero_words) + threads - 1) / threads;
+    cudaStream_t s = (cudaStream_t)stream;
     if (X.stage == 0)
         TRACED("p3_digits", X.stage, stream,
-               (k3_digits<true><<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(X, S3, z, npad, c_src, c_base)));
+               (launch_pdl(k3_digits<true>, dim3((unsigned)blocks), dim3(threads), 0, s, X, S3, z, npad, c_src, c_base,
+                           zero_out, zero_words)));
     else
         TRACED("p3_digits", X.stage, stream,
-               (k3_digits<false><<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(X, S3, z, npad, c_src, c_base)));
+               (launch_pdl(k3_digits<false>, dim3((unsigned)blocks), dim3(threads), 0, s, X, S3, z, npad, c_src, c_base,
+                           zero_out, zero_words)));
     return (int)cudaGetLastError();
 }
 
@@ -1123,10 +1144,10 @@ int p3_enqueue_mmh(P3Plan *pl, const u64 *key, const u64 *seed, u64 *y, bool can
     const CarryDev cd = p3_carry_dev(pl, X, true, pl->flags + 1);
     u64 *z = (u64 *)pl->Y;
     const u64 npad = cd.nchunks * PA_CARRY_D;
-    if ((e = p3_launch_digits(X, pl->S3, z, npad, nullptr, 0, stream))) return e;
     const u64 ywords = (pl->gamma + 63) / 64;
-    if ((e = launch_carry_chunks(cd, npad, X.b * PA_CARRY_D >= 64, 0, z, y, ywords, stream))) return e;
-    if (canonical && (e = launch_canonical_zero(pl->flags + 1, y, ywords, stream))) return e;
+    if ((e = p3_launch_digits(X, pl->S3, z, npad, nullptr, 0, y, ywords, stream))) return e;
+    if ((e = launch_carry_chunks(cd, npad, X.b * PA_CARRY_D >= 64, 0, z, y, ywords, stream, true, true))) return e;
+    if (canonical && (e = launch_canonical_zero(pl->flags + 1, y, ywords, stream, true))) return e;
     return 0;
 }
 
@@ -1151,10 +1172,12 @@ int p3_enqueue_mh(P3Plan *pl, const u64 *seed, u64 *out, int *status, void *stre
     const CarryDev cd = p3_carry_dev(pl, X, false, pl->flags + 2);
     u64 *z = (u64 *)pl->Y;
     const u64 npad = cd.nchunks * PA_CARRY_D;
-    if ((e = p3_launch_digits(X, pl->S3, z, npad, seed, (pl->k + 1) * (u64)pl->gamma, stream))) return e;
     const u64 twords = (pl->gamma + 63) / 64;
-    if ((e = launch_carry_chunks(cd, npad, X.b * PA_CARRY_D >= 64, 1, z, pl->tbuf, twords, stream))) return e;
-    if ((e = launch_extract(pl->tbuf, pl->gamma, pl->r, pl->flags, pl->k, out, status, stream))) return e;
+    if ((e = p3_launch_digits(X, pl->S3, z, npad, seed, (pl->k + 1) * (u64)pl->gamma, pl->tbuf, twords, stream)))
+        return e;
+    if ((e = launch_carry_chunks(cd, npad, X.b * PA_CARRY_D >= 64, 1, z, pl->tbuf, twords, stream, true, true)))
+        return e;
+    if ((e = launch_extract(pl->tbuf, pl->gamma, pl->r, pl->flags, pl->k, out, status, stream, true))) return e;
     return 0;
 }
 

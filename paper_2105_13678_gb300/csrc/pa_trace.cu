@@ -25,6 +25,7 @@ struct Rec {
 
 std::mutex g_mu;
 bool g_on = false;
+std::string g_only;  // non-empty: record only launches with this name
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
 
@@ -51,6 +52,7 @@ void *trace_begin(const char *name, u32 stage, void *stream) {
         return nullptr;
     Rec r;
     r.name = std::string(stage == 0 ? "mmh." : "mh.") + name;
+    if (!g_only.empty() && r.name != g_only) return nullptr;
     r.a = take_event();
     r.b = take_event();
     cudaEventRecord(r.a, (cudaStream_t)stream);
@@ -68,6 +70,12 @@ void trace_end(void *token, void *stream) {
 }  // namespace pa
 
 extern "C" {
+
+int pa_trace_select(const char *name) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_only = name ? std::string(name) : std::string();
+    return PA_OK;
+}
 
 int pa_trace_enable(int on) {
     std::lock_guard<std::mutex> lk(g_mu);
