@@ -298,6 +298,7 @@ __device__ __forceinline__ void fwd_col_round(const Xform &X, const OpDesc &dx, 
 // Y[i] and Y[K + i], or of the single operand blockIdx.y, written to Y[i].
 template <bool PAIR, int LL, int TC>
 __global__ void __launch_bounds__(PA_COL_T, 3) k_fwd_col(Xform X, Operands S, u64 *__restrict__ Y) {
+    pdl_wait();
     extern __shared__ u64 sm[];
     const u32 tc = TC ? (u32)TC : X.tc, c0 = blockIdx.x * tc, i = blockIdx.y + S.pair0;
     OpDesc dx, da;
@@ -345,6 +346,7 @@ __global__ void __launch_bounds__(PA_COL_T, 3) k_fwd_col(Xform X, Operands S, u6
             __syncthreads();
         }
     }
+    pdl_trigger();
     if (dx.check_ones) {
         // Algorithm 1 reload rule: slice i is all ones iff every CTA of the slice saw only ones.
         const int all = __syncthreads_and(ones ? 1 : 0);
@@ -439,6 +441,7 @@ __device__ __forceinline__ void row_inv_round(const Xform &X, u64 *__restrict__ 
 template <int ACC, int MODE, int LL>
 __global__ void __launch_bounds__(512, ACC == 8 ? 2 : 1)
     k_row_mac(Xform X, const u64 *__restrict__ Y, u64 *__restrict__ Spec, u64 *__restrict__ S) {
+    pdl_wait();
     extern __shared__ u64 sm[];
     const u32 l = LL ? (u32)LL : X.logC, C = 1u << l, row = blockIdx.x;
     const u64 N = X.N;
@@ -497,6 +500,7 @@ __global__ void __launch_bounds__(512, ACC == 8 ? 2 : 1)
 #undef PA_ROW_INV
         __syncthreads();
     }
+    pdl_trigger();
 }
 
 // ------------------------------------------------------ inverse columns --
@@ -544,6 +548,7 @@ __device__ __forceinline__ void inv_col_round(const Xform &X, const u64 *__restr
 template <int LL, int TC>
 __global__ void __launch_bounds__(PA_COL_T) k_inv_col(Xform X, const u64 *__restrict__ Sg, u64 *__restrict__ Z,
                                                       const u64 *__restrict__ add_src, u64 add_base, u64 add_len) {
+    pdl_wait();
     extern __shared__ u64 sm[];
     const u32 tc = TC ? (u32)TC : X.tc, c0 = blockIdx.x * tc;
     const u32 l = LL ? (u32)LL : X.logR;
@@ -588,6 +593,7 @@ __global__ void __launch_bounds__(PA_COL_T) k_inv_col(Xform X, const u64 *__rest
 #undef PA_INV_COL
         __syncthreads();
     }
+    pdl_trigger();
 }
 
 // ---------------------------------------------------------------- carry --
@@ -935,7 +941,7 @@ static int launch_cols(const char *name, const Xform &X, const Operands &S, int 
     cudaStream_t s = (cudaStream_t)stream;
 #define PA_LAUNCH_COL(LLV, TCV)                                                                \
     if ((LLV == 0 && TCV == 0) || (X.logR == (u32)LLV && X.tc == (u32)TCV)) {                  \
-        TRACED(name, X.stage, stream, (k_fwd_col<PAIR, LLV, TCV><<<grid, PA_COL_T, smem, s>>>(X, S, Y))); \
+        TRACED(name, X.stage, stream, (launch_pdl(k_fwd_col<PAIR, LLV, TCV>, grid, dim3(PA_COL_T), smem, s, X, S, Y))); \
         return (int)cudaGetLastError();                                                        \
     }
     PA_LAUNCH_COL(10, 4)
@@ -959,20 +965,20 @@ static int launch_rows(const char *name, const Xform &X, const u64 *Y, u64 *Spec
     cudaStream_t s = (cudaStream_t)stream;
     if (X.C > 4096) {
         if (X.logC == 13)
-            TRACED(name, X.stage, stream, (k_row_mac<16, MODE, 13><<<X.R, X.C / 16, row_smem(X), s>>>(X, Y, Spec, S)));
+            TRACED(name, X.stage, stream, (launch_pdl(k_row_mac<16, MODE, 13>, dim3(X.R), dim3(X.C / 16), row_smem(X), s, X, Y, Spec, S)));
         else
-            TRACED(name, X.stage, stream, (k_row_mac<16, MODE, 0><<<X.R, X.C / 16, row_smem(X), s>>>(X, Y, Spec, S)));
+            TRACED(name, X.stage, stream, (launch_pdl(k_row_mac<16, MODE, 0>, dim3(X.R), dim3(X.C / 16), row_smem(X), s, X, Y, Spec, S)));
     } else {
         u32 threads = X.C / 8;
         if (threads < 32) threads = 32;
         if (X.logC == 11)
-            TRACED(name, X.stage, stream, (k_row_mac<8, MODE, 11><<<X.R, threads, row_smem(X), s>>>(X, Y, Spec, S)));
+            TRACED(name, X.stage, stream, (launch_pdl(k_row_mac<8, MODE, 11>, dim3(X.R), dim3(threads), row_smem(X), s, X, Y, Spec, S)));
         else if (X.logC == 12)
-            TRACED(name, X.stage, stream, (k_row_mac<8, MODE, 12><<<X.R, threads, row_smem(X), s>>>(X, Y, Spec, S)));
+            TRACED(name, X.stage, stream, (launch_pdl(k_row_mac<8, MODE, 12>, dim3(X.R), dim3(threads), row_smem(X), s, X, Y, Spec, S)));
         else if (X.logC == 10)
-            TRACED(name, X.stage, stream, (k_row_mac<8, MODE, 10><<<X.R, threads, row_smem(X), s>>>(X, Y, Spec, S)));
+            TRACED(name, X.stage, stream, (launch_pdl(k_row_mac<8, MODE, 10>, dim3(X.R), dim3(threads), row_smem(X), s, X, Y, Spec, S)));
         else
-            TRACED(name, X.stage, stream, (k_row_mac<8, MODE, 0><<<X.R, threads, row_smem(X), s>>>(X, Y, Spec, S)));
+            TRACED(name, X.stage, stream, (launch_pdl(k_row_mac<8, MODE, 0>, dim3(X.R), dim3(threads), row_smem(X), s, X, Y, Spec, S)));
     }
     return (int)cudaGetLastError();
 }
@@ -997,7 +1003,7 @@ int launch_inv_col(const Xform &X, const u64 *S, u64 *Z, const u64 *add_src, u64
 #define PA_LAUNCH_INV(LLV, TCV)                                                                          \
     if ((LLV == 0 && TCV == 0) || (X.logR == (u32)LLV && X.tc == (u32)TCV)) {                            \
         TRACED("inv_col", X.stage, stream,                                                               \
-               (k_inv_col<LLV, TCV><<<grid, PA_COL_T, col_smem(X), s>>>(X, S, Z, add_src, add_base, add_len))); \
+               (launch_pdl(k_inv_col<LLV, TCV>, grid, dim3(PA_COL_T), col_smem(X), s, X, S, Z, add_src, add_base, add_len))); \
         return (int)cudaGetLastError();                                                                  \
     }
     PA_LAUNCH_INV(10, 4)
