@@ -632,55 +632,62 @@ __device__ __forceinline__ unsigned __int128 crt_value(const Geo3 &X, const u32 
     return (unsigned __int128)x1 + (unsigned __int128)((u64)p0 * x2) + (unsigned __int128)X.p01 * x3;
 }
 
-// Sum of the b-bit pieces that land on digit position P: piece k of
-// coefficient P - k (k = 0, 1, 2), for coefficients below ncoef.
-__device__ __forceinline__ u64 position_sum(const Geo3 &X, const u32 *__restrict__ S3, u64 P, u64 ncoef) {
-    const u32 b = X.b;
-    const u64 mask = (1ULL << b) - 1;
-    u64 s = 0;
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        if (P < (u64)k) break;
-        const u64 e = P - k;
-        if (e >= ncoef) continue;
-        const unsigned __int128 v = crt_value(X, S3, e);
-        s += k < 2 ? (u64)(v >> (k * b)) & mask : (u64)(v >> (2 * b));
-    }
-    return s;
-}
-
-// Digit t (bit offset t b) of the value to resolve.  Eq. 2 (RING): every
-// position P whose offset P b is congruent mod gamma to a bit of digit t,
-// shifted by its distance from t b.  Eq. 4: position t only, plus digit t of
-// c (bits [c_base, c_base + gamma) of c_src).
+// Digit t (bit offset t b) of the value to resolve.  Coefficient e's value V_e
+// sits at bit offset e b; its b-bit pieces (V_e, V_e >> b, V_e >> 2b) land on
+// positions e, e+1, e+2.  Eq. 2 (RING): position P's offset P b is taken mod
+// gamma; position t + nd (nd = ceil(gamma / b)) lands on digit t shifted by
+// D1 = nd b - gamma, position t + n2 (n2 = ceil(2 gamma / b)) by
+// D2 = n2 b - 2 gamma, as long as t b + D < gamma (the top digit is short:
+// larger offsets belong to a lower digit of the next wrap).  Eq. 4: position t
+// only, plus digit t of c (bits [c_base, c_base + gamma) of c_src).  A CTA of
+// 256 digits computes each coefficient it needs once (258 per wrap), shares
+// the pieces through shared memory, and zeroes the carry output first.
 template <bool RING>
-__global__ void k3_digits(Geo3 X, const u32 *__restrict__ S3, u64 *__restrict__ z, u64 npad, const u64 *__restrict__ c_src,
-                          u64 c_base, u64 *__restrict__ zero_out, u64 zero_words) {
+__global__ void __launch_bounds__(256) k3_digits(Geo3 X, const u32 *__restrict__ S3, u64 *__restrict__ z, u64 npad,
+                                                 const u64 *__restrict__ c_src, u64 c_base, u64 *__restrict__ zero_out,
+                                                 u64 zero_words) {
     pdl_wait();
-    const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ u64 pc[3][258];
+    const u64 t0 = (u64)blockIdx.x * 256, t = t0 + threadIdx.x;
     if (t < zero_words) zero_out[t] = 0;  // the carry kernels OR their bits into it
-    if (t >= npad) return;
-    if (t >= X.nd) {
-        z[t] = 0;
-        return;
-    }
-    const u64 b = X.b, G = X.G;
+    const u64 b = X.b, G = X.G, mask = (1ULL << b) - 1;
     const u64 ncoef = RING ? 2 * X.M - 1 : X.M;
-    u64 acc = position_sum(X, S3, t, ncoef);
-    if (RING) {
-#pragma unroll
-        for (u64 w = 1; w <= 2; w++) {
-            const u64 P = (w * G + t * b + b - 1) / b;  // first position at or above offset w G + t b
-            const u64 sh = P * b - w * G - t * b;      // < b
-            // offsets t b + sh >= G belong to digit 0.. of the next wrap (the top digit is short)
-            if (P <= 2 * X.M && t * b + sh < G) acc += position_sum(X, S3, P, ncoef) << sh;
+    const u64 nd = X.nd, n2 = (2 * G + b - 1) / b;
+    u64 acc = 0;
+#pragma unroll 1
+    for (u32 w = 0; w < (RING ? 3u : 1u); w++) {
+        const u64 off = w == 0 ? 0 : (w == 1 ? nd : n2);
+        const u64 D = w == 0 ? 0 : (w == 1 ? nd * b - G : n2 * b - 2 * G);
+        // the block's first digit has the smallest offset: if it cannot take wrap w, none can
+        if (w > 0 && (t0 * b + D >= G || t0 + off > 2 * X.M)) break;
+        const u64 P0 = t0 + off;  // position of this block's first digit
+        for (u32 i = threadIdx.x; i < 258; i += 256) {
+            const u64 e = P0 + i - 2;  // wraps below 0 when P0 < 2: skipped by the range check
+            u64 v0 = 0, v1 = 0, v2 = 0;
+            if (P0 + i >= 2 && e < ncoef) {
+                const unsigned __int128 V = crt_value(X, S3, e);
+                v0 = (u64)V & mask;
+                v1 = (u64)(V >> b) & mask;
+                v2 = (u64)(V >> (2 * b));
+            }
+            pc[0][i] = v0;
+            pc[1][i] = v1;
+            pc[2][i] = v2;
         }
-    } else if (c_src) {
+        __syncthreads();
+        if (t < nd && (w == 0 || (t * b + D < G && t + off <= 2 * X.M))) {
+            const u32 i = threadIdx.x + 2;
+            acc += (pc[0][i] + pc[1][i - 1] + pc[2][i - 2]) << D;
+        }
+        __syncthreads();
+    }
+    if (!RING && c_src && t < nd) {
         const u64 pos = t * b;
         const u32 nb = (u32)min(b, G - pos);
         acc += rd32(c_src, c_base + pos, nb);
     }
-    z[t] = acc;
+    if (t < npad) z[t] = t < nd ? acc : 0;
+    pdl_trigger();
 }
 
 // ------------------------------------------------------------------ tables --
