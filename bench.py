@@ -742,7 +742,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / len(times), 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic uniform random bits (splitmix64 seed 2)",
-        "config": {"workload": f"plain single block n={n:.3g} bits, r={args.ratio:g}n={r} (seed 2)", "sample": sample},
+        "config": {"workload": f"plain single block n={n_full:.3g} bits, r={RATIO:g}n={r} (seed 2)",
+                   "n_bits": n_full, "r_bits": r, "gamma": g, "sample": sample},
         "cpu_baseline": {"value": round(value, 3), "unit": "Mbps", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 3), "unit": "Mbps", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
