@@ -73,9 +73,9 @@ typedef struct pa_params {
  *               coefficients recovered by the Chinese remainder theorem
  *               (about half the integer work per transformed element);
  *               not available with pa_seed_prepare (PA_ERR_UNSUPPORTED);
- *   AUTO        P3 when it is feasible, its Eq. 2 transform is no longer
- *               than the Goldilocks one and at least 2^20 long; else
- *               GOLDILOCKS. */
+ *   AUTO        P3 when it is feasible and its Eq. 2 transform is no longer
+ *               than the Goldilocks one, or twice as long but at most 2^20
+ *               (where P3 was measured faster); else GOLDILOCKS. */
 #define PA_BACKEND_AUTO 0u
 #define PA_BACKEND_GOLDILOCKS 1u
 #define PA_BACKEND_P3 2u

@@ -215,7 +215,7 @@ def test_host_async_stream_of_blocks(backend):
 def test_backend_lengths_and_auto_choice():
     """Transform lengths of both backends at the 2.6e8-bit and 1e9-bit blocks;
     PA_BACKEND_AUTO takes the three-prime plan where its Eq. 2 transform is no
-    longer (2.6e8) and the Goldilocks plan where it would be (1e9)."""
+    longer (2.6e8, 2^20) and the Goldilocks plan where it would be (1e9, tiny)."""
     from paper_2105_13678_gb300 import _lib
     a = _lib.Plan(260_000_000, 26_000_000, backend=P3)
     assert a.info.mmh_len == 1 << 21 and a.info.mh_len == 1 << 21
@@ -228,8 +228,12 @@ def test_backend_lengths_and_auto_choice():
     b2 = _lib.Plan(1_000_000_000, 100_000_000)
     assert b2.backend == GOLDILOCKS and b2.info.mmh_len == 1 << 23
     small = _lib.Plan(1 << 20, 104858)
-    assert small.backend == GOLDILOCKS
-    for p in (a, g, auto, b, b2, small):
+    assert small.backend == P3 and small.info.mmh_len == 1 << 13
+    tiny = _lib.Plan(600, 10, gamma=61)  # the three-prime transforms start at 2^8
+    assert tiny.backend == GOLDILOCKS
+    mid = _lib.Plan(10_000_000, 1_000_000)  # T = 2^17 against N = 2^16
+    assert mid.backend == P3 and mid.info.mmh_len == 1 << 17
+    for p in (a, g, auto, b, b2, small, tiny, mid):
         p.close()
 
 
