@@ -71,7 +71,11 @@ __device__ __forceinline__ u32 round_s0(u32 l, u32 rd) { return rd ? round_ns(l,
 // group is zero on entry.  In the final round (LAST) the twiddles of the
 // pairs with i mod L/2^(s+1) = 0 are 1.
 // rt: the task's round twiddles, stage sg's pair jj at q = 2^NS - 2^(NS-sg) + jj.
-template <int NS, bool LAST, bool HZ>
+// TS: the round table is in shared memory (plain loads) rather than global (read-only path).
+template <bool TS>
+__device__ __forceinline__ uint2 twl(const uint2 *__restrict__ p) { return TS ? *p : __ldg(p); }
+
+template <int NS, bool LAST, bool HZ, bool TS = false>
 __device__ __forceinline__ void dif3(u32 (&v)[8], const uint2 *__restrict__ rt, u32 p) {
     const u32 p2 = 2 * p;
 #pragma unroll
@@ -85,12 +89,12 @@ __device__ __forceinline__ void dif3(u32 (&v)[8], const uint2 *__restrict__ rt, 
             const int q = (1 << NS) - (1 << (NS - sg)) + jj;
             const u32 a = v[m], b = v[m + half];
             if (HZ && sg == 0) {
-                v[m + half] = one ? a : shoup(a, __ldg(rt + q), p);
+                v[m + half] = one ? a : shoup(a, twl<TS>(rt + q), p);
                 continue;
             }
             v[m] = red2(a + b, p2);
             const u32 d = a - b + p2;
-            v[m + half] = one ? red2(d, p2) : shoup(d, __ldg(rt + q), p);
+            v[m + half] = one ? red2(d, p2) : shoup(d, twl<TS>(rt + q), p);
         }
     }
 }
@@ -206,10 +210,10 @@ __device__ __forceinline__ u32 digit_raw(const Geo3 &X, const Desc &d, u64 pos, 
 // ------------------------------------------------------------ column pass --
 
 // LL, TC: log2 R and the tile width when fixed at compile time (0: from X).
-template <int NS, bool PAIR, bool FIRST, bool LAST, int LL, int TC>
+template <int NS, bool PAIR, bool FIRST, bool LAST, int LL, int TC, bool TS = false>
 __device__ __forceinline__ void fwd3_round(const Geo3 &X, u32 j, const Desc &dx, const Desc &da, u32 *__restrict__ smx,
                                            u32 *__restrict__ sma, u32 *__restrict__ Yx, u32 *__restrict__ Ya, u32 c0,
-                                           u32 s0, u32 rd, bool &ones) {
+                                           u32 s0, u32 rd, bool &ones, const uint2 *__restrict__ stw = nullptr) {
     const u32 l = LL ? (u32)LL : X.logR, tc = TC ? (u32)TC : X.tc, p = X.p[j];
     const u32 sh = l - s0 - NS, stride = 1u << sh;
     const u32 ntask = ((1u << l) >> NS) * tc;
@@ -217,7 +221,7 @@ __device__ __forceinline__ void fwd3_round(const Geo3 &X, u32 j, const Desc &dx,
     const u32 dsm = pstepc(stride * tc);  // tc = 8
     const u64 dY = (u64)stride * X.C;
     const uint2 red = X.red[j];
-    const uint2 *tw = X.twR[j] + X.rofR[rd];
+    const uint2 *tw = (TS ? stw : X.twR[j]) + X.rofR[rd];
     for (u32 task = threadIdx.x; task < ntask; task += blockDim.x) {
         const u32 c = task & (tc - 1), g = task >> logtc;
         const u32 lo = g & (stride - 1), base = ((g >> sh) << (l - s0)) + lo;
@@ -244,8 +248,8 @@ __device__ __forceinline__ void fwd3_round(const Geo3 &X, u32 j, const Desc &dx,
             }
         }
         const uint2 *rt = tw + lo * ((1u << NS) - 1);
-        dif3<NS, LAST, FIRST>(vx, rt, p);
-        if (PAIR) dif3<NS, LAST, FIRST>(va, rt, p);
+        dif3<NS, LAST, FIRST, TS>(vx, rt, p);
+        if (PAIR) dif3<NS, LAST, FIRST, TS>(va, rt, p);
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
             if (LAST) {
@@ -324,6 +328,7 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
     Desc dx, da;
     descs(S, i, dx, da);
     u32 *smx = sm3, *sma = sm3 + pxc((1u << LL) * TC);
+    uint2 *stw = reinterpret_cast<uint2 *>(sm3 + 2 * pxc((1u << LL) * TC));  // this prime's round tables
     bool ones = true;
     u32 rx[NT][HALF0], ra[NT][HALF0];
 #pragma unroll
@@ -344,7 +349,12 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
         const u32 p = X.p[j];
         const uint2 red = X.red[j];
         u32 *Yx = Y + ((u64)j * 2 * X.K + i) * X.T, *Ya = Y + ((u64)j * 2 * X.K + X.K + i) * X.T;
-        const uint2 *tw = X.twR[j] + X.rofR[0];
+        {
+            const u32 ntw = X.rofR[nr - 1] + 7;  // the final round's table ends 7 entries on
+            for (u32 q = threadIdx.x; q < ntw; q += NTH) stw[q] = __ldg(X.twR[j] + q);
+            __syncthreads();
+        }
+        const uint2 *tw = stw + X.rofR[0];
 #pragma unroll
         for (u32 t = 0; t < NT; t++) {
             const u32 task = threadIdx.x + t * NTH;
@@ -358,8 +368,8 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
                 va[m] = m < HALF0 ? shoup(ra[t][m], red, p) : 0u;
             }
             const uint2 *rt = tw + g * ((1u << NS0) - 1);
-            dif3<NS0, false, true>(vx, rt, p);
-            dif3<NS0, false, true>(va, rt, p);
+            dif3<NS0, false, true, true>(vx, rt, p);
+            dif3<NS0, false, true, true>(va, rt, p);
 #pragma unroll
             for (u32 m = 0; m < (1u << NS0); m++) {
                 smx[a0 + m * dsm] = vx[m];
@@ -371,9 +381,9 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
         for (u32 rd = 1; rd < nr; rd++) {
             const u32 s0 = NS0 + 3 * (rd - 1);
             if (rd == nr - 1)
-                fwd3_round<3, true, false, true, LL, TC>(X, j, dx, da, smx, sma, Yx, Ya, c0, s0, rd, ones);
+                fwd3_round<3, true, false, true, LL, TC, true>(X, j, dx, da, smx, sma, Yx, Ya, c0, s0, rd, ones, stw);
             else
-                fwd3_round<3, true, false, false, LL, TC>(X, j, dx, da, smx, sma, Yx, Ya, c0, s0, rd, ones);
+                fwd3_round<3, true, false, false, LL, TC, true>(X, j, dx, da, smx, sma, Yx, Ya, c0, s0, rd, ones, stw);
             __syncthreads();
         }
     }
@@ -748,7 +758,8 @@ int p3_launch_fwd_col(const Geo3 &X, const Operands &S, int pairs, u32 *Y, void 
     cudaStream_t s = (cudaStream_t)stream;
     if (X.logR == 10 && X.tc == 8)
         TRACED("p3_fwd_col", X.stage, stream,
-               (launch_pdl(k3_fwd_col_all<10, 8>, dim3(pairs, X.C / X.tc), dim3(512), smem, s, X, S, Y)));
+               (launch_pdl(k3_fwd_col_all<10, 8>, dim3(pairs, X.C / X.tc), dim3(512), smem + X.R * sizeof(uint2), s,
+                           X, S, Y)));
     else
         TRACED("p3_fwd_col", X.stage, stream,
                (launch_pdl(k3_fwd_col<true, 0, 0>, grid, dim3(kColThreads), smem, s, X, S, Y)));
