@@ -151,6 +151,7 @@ struct Geo3 {
     const uint2 *twR[3], *itwR[3];
     const uint2 *twC[3], *itwC[3];
     u32 rofR[6], rofC[6];
+    u32 rof4R;      // forward R table: offset of the 4-stage first round (15 twiddles per lo), 0: none
     const uint2 *ctw[3], *ictw[3];  // T entries, [r][c]: omega_T^(+-c bitrev_R(r))
 };
 

@@ -122,6 +122,30 @@ __device__ __forceinline__ void dit3(u32 (&v)[8], const uint2 *__restrict__ rt, 
     }
 }
 
+// Stages 0..3 of a length-L transform on 16 elements lo + m L/16 whose upper
+// 8 are zero on entry (the zero-padded half), twiddles rt[16 - 2^(4-sg) + jj]
+// = omega_L^((lo + jj L/16) 2^sg); the round table is in shared memory.
+__device__ __forceinline__ void dif16_hz(u32 (&v)[16], const uint2 *__restrict__ rt, u32 p) {
+    const u32 p2 = 2 * p;
+#pragma unroll
+    for (int sg = 0; sg < 4; sg++) {
+        const int half = 8 >> sg;
+#pragma unroll
+        for (int m = 0; m < 16; m++) {
+            if (m & half) continue;
+            const int q = 16 - (16 >> sg) + (m & (half - 1));
+            const u32 a = v[m];
+            if (sg == 0) {
+                v[m + half] = shoup(a, rt[q], p);  // (a, 0) -> (a, a w)
+                continue;
+            }
+            const u32 b = v[m + half];
+            v[m] = red2(a + b, p2);
+            v[m + half] = shoup(a - b + p2, rt[q], p);
+        }
+    }
+}
+
 // Shared-memory word of element i: one pad word per 8 (px(i + 8k) = px(i) + 9k,
 // so elements m * d apart, d a multiple of 8, are px(i) + m * (d + d / 8)).
 __device__ __forceinline__ u32 pstep(u32 d) { return d + (d >> 3); }
@@ -307,20 +331,17 @@ __global__ void __launch_bounds__(kColThreads) k3_fwd_col(Geo3 X, Operands S, u3
     }
 }
 
-// All three primes in one CTA (compile-time geometry, 512 threads): the
-// digits of the first round's nonzero half are read once into registers, then
-// each prime runs its column transform through the same shared tile.
+// All three primes in one CTA (R = 2^10, 8-column tiles, 512 threads): each
+// thread reads the 8 nonzero digits of its first-round group once into
+// registers; each prime then runs its column transform through the same
+// shared tile in three rounds -- stages 0-3 in registers on 16 elements
+// (upper half zero), then 4-6 and 7-9 -- with its round twiddles staged in
+// shared memory.
 template <int LL, int TC>
 __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32 *__restrict__ Y) {
     pdl_wait();
+    static_assert(LL == 10 && TC == 8, "one task per thread: R/16 x 8 columns = 512");
     constexpr u32 NTH = 512;
-    constexpr u32 NS0 = LL - 3 * ((LL + 2) / 3 - 1);
-    constexpr u32 HALF0 = 1u << (NS0 - 1);
-    constexpr u32 SH0 = LL - NS0;                 // first-round stride 2^SH0 rows
-    constexpr u32 NTASK0 = ((1u << LL) >> NS0) * TC;
-    constexpr u32 NT = NTASK0 / NTH;
-    constexpr u32 LOGTC = __builtin_ctz(TC);
-    static_assert(NT * NTH == NTASK0, "first-round tasks must divide evenly");
     extern __shared__ u32 sm3[];
     // pairs vary fastest across the grid, so the tile's inter-pass twiddles are
     // reused from L2 by the CTAs of all pairs
@@ -330,62 +351,53 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
     u32 *smx = sm3, *sma = sm3 + pxc((1u << LL) * TC);
     uint2 *stw = reinterpret_cast<uint2 *>(sm3 + 2 * pxc((1u << LL) * TC));  // this prime's round tables
     bool ones = true;
-    u32 rx[NT][HALF0], ra[NT][HALF0];
+    const u32 c = threadIdx.x & (TC - 1), lo = threadIdx.x >> 3;  // group lo: rows lo + 64 m
+    constexpr u32 D64 = 64;
+    u32 rx[8], ra[8];
+    {
+        const u64 e0 = (u64)lo * X.C + c0 + c;
 #pragma unroll
-    for (u32 t = 0; t < NT; t++) {
-        const u32 task = threadIdx.x + t * NTH;
-        const u32 c = task & (TC - 1), g = task >> LOGTC;  // g < 2^SH0: base = g
-        const u64 e0 = (u64)g * X.C + c0 + c;
-#pragma unroll
-        for (u32 m = 0; m < HALF0; m++) {
-            const u64 pos = (e0 + ((u64)m << SH0) * X.C) * X.b;
-            rx[t][m] = digit_raw(X, dx, pos, ones);
-            ra[t][m] = digit_raw(X, da, pos, ones);
+        for (u32 m = 0; m < 8; m++) {
+            const u64 pos = (e0 + (u64)(m * D64) * X.C) * X.b;
+            rx[m] = digit_raw(X, dx, pos, ones);
+            ra[m] = digit_raw(X, da, pos, ones);
         }
     }
-    constexpr u32 nr = (LL + 2) / 3;
+    const u32 a0 = pxc(lo * TC + c);
+    constexpr u32 dsm = D64 * TC + ((D64 * TC) >> 3);  // 64 rows = 512 words apart
 #pragma unroll 1
     for (u32 j = 0; j < 3; j++) {
         const u32 p = X.p[j];
         const uint2 red = X.red[j];
         u32 *Yx = Y + ((u64)j * 2 * X.K + i) * X.T, *Ya = Y + ((u64)j * 2 * X.K + X.K + i) * X.T;
         {
-            const u32 ntw = X.rofR[nr - 1] + 7;  // the final round's table ends 7 entries on
+            const u32 ntw = X.rof4R + 64 * 15;  // standard rounds, then the 4-stage first round
             for (u32 q = threadIdx.x; q < ntw; q += NTH) stw[q] = __ldg(X.twR[j] + q);
             __syncthreads();
         }
-        const uint2 *tw = stw + X.rofR[0];
+        const uint2 *rt = stw + X.rof4R + lo * 15;
+        {
+            u32 v[16];
 #pragma unroll
-        for (u32 t = 0; t < NT; t++) {
-            const u32 task = threadIdx.x + t * NTH;
-            const u32 c = task & (TC - 1), g = task >> LOGTC;
-            const u32 a0 = pxc(g * TC + c);
-            constexpr u32 dsm = ((1u << SH0) * TC) + (((1u << SH0) * TC) >> 3);  // a multiple of 64 words apart
-            u32 vx[8], va[8];
+            for (u32 m = 0; m < 16; m++) v[m] = m < 8 ? shoup(rx[m], red, p) : 0u;
+            dif16_hz(v, rt, p);
 #pragma unroll
-            for (u32 m = 0; m < (1u << NS0); m++) {
-                vx[m] = m < HALF0 ? shoup(rx[t][m], red, p) : 0u;
-                va[m] = m < HALF0 ? shoup(ra[t][m], red, p) : 0u;
-            }
-            const uint2 *rt = tw + g * ((1u << NS0) - 1);
-            dif3<NS0, false, true, true>(vx, rt, p);
-            dif3<NS0, false, true, true>(va, rt, p);
+            for (u32 m = 0; m < 16; m++) smx[a0 + m * dsm] = v[m];
+        }
+        {
+            u32 v[16];
 #pragma unroll
-            for (u32 m = 0; m < (1u << NS0); m++) {
-                smx[a0 + m * dsm] = vx[m];
-                sma[a0 + m * dsm] = va[m];
-            }
+            for (u32 m = 0; m < 16; m++) v[m] = m < 8 ? shoup(ra[m], red, p) : 0u;
+            dif16_hz(v, rt, p);
+#pragma unroll
+            for (u32 m = 0; m < 16; m++) sma[a0 + m * dsm] = v[m];
         }
         __syncthreads();
-#pragma unroll
-        for (u32 rd = 1; rd < nr; rd++) {
-            const u32 s0 = NS0 + 3 * (rd - 1);
-            if (rd == nr - 1)
-                fwd3_round<3, true, false, true, LL, TC, true>(X, j, dx, da, smx, sma, Yx, Ya, c0, s0, rd, ones, stw);
-            else
-                fwd3_round<3, true, false, false, LL, TC, true>(X, j, dx, da, smx, sma, Yx, Ya, c0, s0, rd, ones, stw);
-            __syncthreads();
-        }
+        // stages 4-6 and 7-9: the standard partition's rounds 2 and 3
+        fwd3_round<3, true, false, false, LL, TC, true>(X, j, dx, da, smx, sma, Yx, Ya, c0, 4, 2, ones, stw);
+        __syncthreads();
+        fwd3_round<3, true, false, true, LL, TC, true>(X, j, dx, da, smx, sma, Yx, Ya, c0, 7, 3, ones, stw);
+        __syncthreads();
     }
     pdl_trigger();
     if (dx.check_ones) {
@@ -756,10 +768,10 @@ int p3_launch_fwd_col(const Geo3 &X, const Operands &S, int pairs, u32 *Y, void 
     const dim3 grid(X.C / X.tc, pairs, 3);
     const size_t smem = col_smem3(X, true);
     cudaStream_t s = (cudaStream_t)stream;
-    if (X.logR == 10 && X.tc == 8)
+    if (X.logR == 10 && X.tc == 8 && X.rof4R)
         TRACED("p3_fwd_col", X.stage, stream,
-               (launch_pdl(k3_fwd_col_all<10, 8>, dim3(pairs, X.C / X.tc), dim3(512), smem + X.R * sizeof(uint2), s,
-                           X, S, Y)));
+               (launch_pdl(k3_fwd_col_all<10, 8>, dim3(pairs, X.C / X.tc), dim3(512),
+                           smem + (X.rof4R + 64 * 15) * sizeof(uint2), s, X, S, Y)));
     else
         TRACED("p3_fwd_col", X.stage, stream,
                (launch_pdl(k3_fwd_col<true, 0, 0>, grid, dim3(kColThreads), smem, s, X, S, Y)));
@@ -1001,6 +1013,7 @@ int build_tables(P3Plan *pl, Geo3 &X, const PrimeSet &ps, const Geo3 *other) {
             X.rofR[rd] = other->rofR[rd];
             X.rofC[rd] = other->rofC[rd];
         }
+        X.rof4R = other->rof4R;
         return PA_OK;
     }
     int err = PA_OK;
@@ -1014,6 +1027,17 @@ int build_tables(P3Plan *pl, Geo3 &X, const PrimeSet &ps, const Geo3 *other) {
             const u32 w = dir ? invmod(wT, p) : wT;
             const u32 wR = powmod(w, X.C, p), wC = powmod(w, X.R, p);
             std::vector<uint2> tR = round_table(wR, X.logR, p, X.rofR), tC = round_table(wC, X.logC, p, X.rofC);
+            if (dir == 0 && X.logR == 10) {
+                // 4-stage first round of the column kernel: per lo < 64, stage sg's twiddles
+                // omega_R^((lo + jj 64) 2^sg), jj < 2^(3 - sg)
+                X.rof4R = (u32)tR.size();
+                std::vector<u32> pw(X.R);
+                u64 a4 = 1;
+                for (u32 e = 0; e < X.R; e++, a4 = a4 * wR % p) pw[e] = (u32)a4;
+                for (u32 lo = 0; lo < 64; lo++)
+                    for (u32 sg = 0; sg < 4; sg++)
+                        for (u32 jj = 0; jj < (8u >> sg); jj++) tR.push_back(shoup_pair(pw[((lo + jj * 64) << sg) % X.R], p));
+            }
             u64 a = 1;
             uint2 *dR = (uint2 *)pl->alloc(tR.size() * sizeof(uint2), &err);
             uint2 *dC = (uint2 *)pl->alloc(tC.size() * sizeof(uint2), &err);
