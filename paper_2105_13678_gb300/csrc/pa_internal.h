@@ -152,6 +152,7 @@ struct Geo3 {
     const uint2 *twC[3], *itwC[3];
     u32 rofR[6], rofC[6];
     u32 rof4R;      // forward R table: offset of the 4-stage first round (15 twiddles per lo), 0: none
+    u32 rof4Ri;     // inverse R table: the same 4-stage round with inverse twiddles, 0: none
     const uint2 *ctw[3], *ictw[3];  // T entries, [r][c]: omega_T^(+-c bitrev_R(r))
 };
 

@@ -146,6 +146,26 @@ __device__ __forceinline__ void dif16_hz(u32 (&v)[16], const uint2 *__restrict__
     }
 }
 
+// Inverse of the 4-stage round (DIT, stages 3..0, inverse twiddles in the same
+// layout); HO: the upper 8 outputs are not needed.
+template <bool HO>
+__device__ __forceinline__ void dit16(u32 (&v)[16], const uint2 *__restrict__ rt, u32 p) {
+    const u32 p2 = 2 * p;
+#pragma unroll
+    for (int sg = 3; sg >= 0; sg--) {
+        const int half = 8 >> sg;
+#pragma unroll
+        for (int m = 0; m < 16; m++) {
+            if (m & half) continue;
+            const int q = 16 - (16 >> sg) + (m & (half - 1));
+            const u32 a = v[m];
+            const u32 t = shoup(v[m + half], __ldg(rt + q), p);
+            v[m] = red2(a + t, p2);
+            if (!(HO && sg == 0)) v[m + half] = red2(a - t + p2, p2);
+        }
+    }
+}
+
 // Shared-memory word of element i: one pad word per 8 (px(i + 8k) = px(i) + 9k,
 // so elements m * d apart, d a multiple of 8, are px(i) + m * (d + d / 8)).
 __device__ __forceinline__ u32 pstep(u32 d) { return d + (d >> 3); }
@@ -613,8 +633,11 @@ __global__ void __launch_bounds__(kColThreads) k3_inv_col(Geo3 X, u32 *__restric
     const u32 j = blockIdx.y, tc = TC ? (u32)TC : X.tc, c0 = blockIdx.x * tc;
     const u32 l = LL ? (u32)LL : X.logR, nr = (l + 2) / 3;
     const bool ho = X.stage == 1;  // Eq. 4: only t mod 2^gamma, i.e. coefficients < T/2
+    // R = 2^10 with the 4-stage table: stages 3..0 in one register round at the end
+    constexpr bool M4 = LL == 10 && TC == 8;
+    const int rlast = (M4 && X.rof4Ri) ? 2 : 0;
 #pragma unroll(LL > 0 ? 8 : 1)
-    for (int rd = (int)nr - 1; rd >= 0; rd--) {
+    for (int rd = (int)nr - 1; rd >= rlast; rd--) {
         const u32 s0 = round_s0(l, rd), ns = round_ns(l, rd);
         const bool first = rd == (int)nr - 1, last = rd == 0;
 #define P3_INV(NSV)                                                       \
@@ -631,6 +654,29 @@ __global__ void __launch_bounds__(kColThreads) k3_inv_col(Geo3 X, u32 *__restric
         P3_DISPATCH_NS(ns, P3_INV);
 #undef P3_INV
         __syncthreads();
+    }
+    if (M4 && rlast == 2) {
+        // stages 3..0: 16 rows lo + 64 m of one column per task, written to S3
+        const u32 p = X.p[j];
+        const uint2 *itw = X.itwR[j] + X.rof4Ri;
+        u32 *Sj = S3 + (u64)j * X.T;
+        for (u32 task = threadIdx.x; task < 64 * TC; task += blockDim.x) {
+            const u32 c = task & (TC - 1), lo = task >> 3;
+            const u32 a0 = pxc(lo * TC + c);
+            const u64 e0 = (u64)lo * X.C + c0 + c, dY = (u64)64 * X.C;
+            u32 v[16];
+#pragma unroll
+            for (u32 m = 0; m < 16; m++) v[m] = sm3[a0 + m * 576];  // 64 rows apart: pstepc(512)
+            if (ho) {
+                dit16<true>(v, itw + lo * 15, p);
+#pragma unroll
+                for (u32 m = 0; m < 8; m++) Sj[e0 + m * dY] = v[m];
+            } else {
+                dit16<false>(v, itw + lo * 15, p);
+#pragma unroll
+                for (u32 m = 0; m < 16; m++) Sj[e0 + m * dY] = v[m];
+            }
+        }
     }
     pdl_trigger();
 }
@@ -1014,6 +1060,7 @@ int build_tables(P3Plan *pl, Geo3 &X, const PrimeSet &ps, const Geo3 *other) {
             X.rofC[rd] = other->rofC[rd];
         }
         X.rof4R = other->rof4R;
+        X.rof4Ri = other->rof4Ri;
         return PA_OK;
     }
     int err = PA_OK;
@@ -1027,6 +1074,16 @@ int build_tables(P3Plan *pl, Geo3 &X, const PrimeSet &ps, const Geo3 *other) {
             const u32 w = dir ? invmod(wT, p) : wT;
             const u32 wR = powmod(w, X.C, p), wC = powmod(w, X.R, p);
             std::vector<uint2> tR = round_table(wR, X.logR, p, X.rofR), tC = round_table(wC, X.logC, p, X.rofC);
+            if (dir == 1 && X.logR == 10) {
+                // inverse of the 4-stage round (stages 0-3 of the inverse column pass)
+                X.rof4Ri = (u32)tR.size();
+                std::vector<u32> pw(X.R);
+                u64 a4 = 1;
+                for (u32 e = 0; e < X.R; e++, a4 = a4 * wR % p) pw[e] = (u32)a4;
+                for (u32 lo = 0; lo < 64; lo++)
+                    for (u32 sg = 0; sg < 4; sg++)
+                        for (u32 jj = 0; jj < (8u >> sg); jj++) tR.push_back(shoup_pair(pw[((lo + jj * 64) << sg) % X.R], p));
+            }
             if (dir == 0 && X.logR == 10) {
                 // 4-stage first round of the column kernel: per lo < 64, stage sg's twiddles
                 // omega_R^((lo + jj 64) 2^sg), jj < 2^(3 - sg)
