@@ -471,8 +471,7 @@ __device__ __forceinline__ void row_fwd3(const Geo3 &X, u32 j, const u32 (&fx)[A
     }
 }
 
-// The first round's inputs of one row pair (elements g + m C/2^NS of group g):
-// loaded into registers ahead of use.
+// The first round's inputs of one row pair (elements g + m C/2^NS of group g).
 template <int NS, int ACC, int LL>
 __device__ __forceinline__ void row_load3(const Geo3 &X, const u32 *__restrict__ xrow, const u32 *__restrict__ arow,
                                           u32 (&fx)[ACC], u32 (&fa)[ACC]) {
@@ -521,10 +520,9 @@ __device__ __forceinline__ void row_inv3(const Geo3 &X, u32 j, u32 *__restrict__
 }
 
 // grid (R, 3 primes); blockDim = C / ACC threads, ACC accumulators each.
-// PF: the next pair's first-round inputs are loaded while the current pair
-// is transformed (512 threads at most).
-template <int ACC, int LL, bool PF>
-__global__ void __launch_bounds__(PF ? 512 : 1024) k3_row_mac(Geo3 X, const u32 *__restrict__ Y, u32 *__restrict__ S3) {
+// grid (R, 3 primes); blockDim = C / ACC threads, ACC accumulators each.
+template <int ACC, int LL>
+__global__ void __launch_bounds__(1024) k3_row_mac(Geo3 X, const u32 *__restrict__ Y, u32 *__restrict__ S3) {
     pdl_wait();
     extern __shared__ u32 sm3[];
     const u32 j = blockIdx.y, row = blockIdx.x, l = LL ? (u32)LL : X.logC, C = 1u << l;
@@ -533,21 +531,13 @@ __global__ void __launch_bounds__(PF ? 512 : 1024) k3_row_mac(Geo3 X, const u32 
 #pragma unroll
     for (int m = 0; m < ACC; m++) acc[m] = 0;
     const u32 nr = (l + 2) / 3, ns0 = round_ns(l, 0);
-    auto rows = [&](u32 i, const u32 *&xr, const u32 *&ar) {
-        xr = Y + ((u64)j * 2 * X.K + i) * X.T + (u64)row * C;
-        ar = Y + ((u64)j * 2 * X.K + X.K + i) * X.T + (u64)row * C;
-    };
-#define P3_LOAD(NSV) row_load3<NSV, ACC, LL>(X, xr, ar, fx, fa)
-    if (PF) {
-        const u32 *xr, *ar;
-        rows(0, xr, ar);
-        P3_DISPATCH_NS(ns0, P3_LOAD);
-    }
     for (u32 i = 0; i < X.K; i++) {
-        if (!PF) {  // load right before use: short register lifetimes
-            const u32 *xr, *ar;
-            rows(i, xr, ar);
+        {  // the first round's inputs, loaded right before use (short register lifetimes)
+            const u32 *xr = Y + ((u64)j * 2 * X.K + i) * X.T + (u64)row * C;
+            const u32 *ar = Y + ((u64)j * 2 * X.K + X.K + i) * X.T + (u64)row * C;
+#define P3_LOAD(NSV) row_load3<NSV, ACC, LL>(X, xr, ar, fx, fa)
             P3_DISPATCH_NS(ns0, P3_LOAD);
+#undef P3_LOAD
         }
 #pragma unroll(LL > 0 ? 8 : 1)
         for (u32 rd = 0; rd < nr; rd++) {
@@ -562,15 +552,9 @@ __global__ void __launch_bounds__(PF ? 512 : 1024) k3_row_mac(Geo3 X, const u32 
     } while (0)
             P3_DISPATCH_NS(ns, P3_ROWF);
 #undef P3_ROWF
-            if (PF && first && i + 1 < X.K) {  // the next pair's inputs, in flight during this pair's rounds
-                const u32 *xr, *ar;
-                rows(i + 1, xr, ar);
-                P3_DISPATCH_NS(ns0, P3_LOAD);
-            }
             __syncthreads();
         }
     }
-#undef P3_LOAD
     u32 *Srow = S3 + (u64)j * X.T + (u64)row * C;
 #pragma unroll(LL > 0 ? 8 : 1)
     for (int rd = (int)nr - 1; rd >= 0; rd--) {
@@ -795,13 +779,13 @@ int p3_prepare_kernels() {
     P3_ATTR((k3_fwd_col_all<10, 8>))
     P3_ATTR((k3_inv_col<0, 0>))
     P3_ATTR((k3_inv_col<10, 8>))
-    P3_ATTR((k3_row_mac<8, 0, false>))
-    P3_ATTR((k3_row_mac<16, 0, false>))
-    P3_ATTR((k3_row_mac<8, 10, false>))
-    P3_ATTR((k3_row_mac<8, 11, false>))
-    P3_ATTR((k3_row_mac<8, 12, false>))
-    P3_ATTR((k3_row_mac<8, 13, false>))
-    P3_ATTR((k3_row_mac<16, 14, false>))
+    P3_ATTR((k3_row_mac<8, 0>))
+    P3_ATTR((k3_row_mac<16, 0>))
+    P3_ATTR((k3_row_mac<8, 10>))
+    P3_ATTR((k3_row_mac<8, 11>))
+    P3_ATTR((k3_row_mac<8, 12>))
+    P3_ATTR((k3_row_mac<8, 13>))
+    P3_ATTR((k3_row_mac<16, 14>))
 #undef P3_ATTR
     done = true;
     return 0;
@@ -829,20 +813,19 @@ int p3_launch_row_mac(const Geo3 &X, const u32 *Y, u32 *S3, void *stream) {
     const dim3 grid(X.R, 3);
     const size_t smem = row_smem3(X);
     cudaStream_t s = (cudaStream_t)stream;
-#define P3_ROW(A, L, PF)                     \
-    TRACED("p3_row_mac", X.stage, stream,      \
-           (launch_pdl(k3_row_mac<A, L, PF>, grid, dim3(X.C / A), smem, s, X, Y, S3)))
+#define P3_ROW(A, L) \
+    TRACED("p3_row_mac", X.stage, stream, (launch_pdl(k3_row_mac<A, L>, grid, dim3(X.C / A), smem, s, X, Y, S3)))
     switch (X.logC) {
-    case 10: P3_ROW(8, 10, false); break;
-    case 11: P3_ROW(8, 11, false); break;
-    case 12: P3_ROW(8, 12, false); break;
-    case 13: P3_ROW(8, 13, false); break;
-    case 14: P3_ROW(16, 14, false); break;
+    case 10: P3_ROW(8, 10); break;
+    case 11: P3_ROW(8, 11); break;
+    case 12: P3_ROW(8, 12); break;
+    case 13: P3_ROW(8, 13); break;
+    case 14: P3_ROW(16, 14); break;
     default:
         if (X.C > 8192)
-            P3_ROW(16, 0, false);
+            P3_ROW(16, 0);
         else
-            P3_ROW(8, 0, false);
+            P3_ROW(8, 0);
     }
 #undef P3_ROW
     return (int)cudaGetLastError();
