@@ -96,6 +96,27 @@ def test_reload_on_all_ones_slice(backend):
     assert st == oracle.ORA_RELOAD and not gout.any()
 
 
+@pytest.mark.parametrize("backend", [GOLDILOCKS, P3])
+def test_reload_on_all_ones_slice_1024_row_columns(backend):
+    """The reload rule where the three-prime column pass runs on 1024-row tiles
+    (transform of 2^20 points, one CTA walking several tiles): a random key
+    hashes normally, and an all-ones slice in the middle or as the last slice
+    gives the reload status and a zero output."""
+    gamma = 13466917
+    n, r = 4 * gamma, 1000
+    plan = _plan(n, r, gamma, backend=backend)
+    if backend == P3:
+        assert plan.geometry(0)[0] == 10
+    key, hseed = synthetic.block_inputs(6, n, (plan.k + 2) * gamma)
+    st, _, _, _ = gpu_hash(plan, key, hseed)
+    assert st == oracle.ORA_OK
+    kv = oracle.words_to_int(key)
+    for sl in (1, plan.k - 1):
+        kv2 = kv | (((1 << gamma) - 1) << (sl * gamma))
+        st, out, _, _ = gpu_hash(plan, oracle.int_to_words(kv2, key.size), hseed)
+        assert st == oracle.ORA_RELOAD and not out.any()
+
+
 def test_zero_mmh_value_and_all_ones_representation():
     """Seeds that make y = 0: a = 0, and a pair with a_2 = -a_1, x_2 = x_1 (the
     carry ring may land on the all-ones representation of 0)."""
