@@ -72,7 +72,6 @@ typedef struct pa_params {
  *   P3          zero-padded transforms over three 30-bit primes, the
  *               coefficients recovered by the Chinese remainder theorem
  *               (about half the integer work per transformed element);
- *               not available with pa_seed_prepare (PA_ERR_UNSUPPORTED);
  *   AUTO        P3 when it is feasible and its Eq. 2 transform is no longer
  *               than the Goldilocks one, or twice as long but at most 2^20
  *               (where P3 was measured faster); else GOLDILOCKS. */
@@ -138,8 +137,9 @@ int pa_mh_plan(uint64_t n_bits, uint64_t r_bits, pa_plan_t **out);
 
 /* Seed reuse.  When the same hash seed (a, b, c) serves many blocks,
  * pa_seed_prepare transforms a_1..a_k and b once and keeps their spectra (and
- * a copy of the seed) in the plan: k N_mmh + N_mh words plus the seed, allocated
- * on the first call (blocking).  pa_hash_prepared then runs Algorithm 1 on a
+ * a copy of the seed) in the plan: k N_mmh + N_mh 64-bit words (GOLDILOCKS) or
+ * 3 (k N_mmh + N_mh) 32-bit words (P3) plus the seed, allocated on the first
+ * call (blocking).  pa_hash_prepared then runs Algorithm 1 on a
  * key with that seed, transforming only the key slices and y: k + 3 transforms
  * instead of 2k + 4, same output bits as pa_hash with the same seed.  Returns
  * PA_ERR_INVALID if the plan has no prepared seed.  Both are asynchronous on

@@ -691,7 +691,10 @@ int pa_hash_host(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint6
 int pa_seed_prepare(pa_plan_t *pl, const uint64_t *seed, void *stream) {
     if (!pl || !seed) return PA_ERR_INVALID;
     if (pl->mh_only) return PA_ERR_INVALID;
-    if (pl->p3) return PA_ERR_UNSUPPORTED;
+    if (pl->p3) {
+        const int e = p3_seed_prepare(pl->p3, (const u64 *)seed, stream);  // PA_ERR_* (< 0) or a CUDA error
+        return e < 0 ? e : cuda_rc(e);
+    }
     cudaStream_t s = (cudaStream_t)stream;
     const uint64_t sw = ((pl->k + 2) * pl->gamma + 63) / 64;
     if (!pl->spec_a) {
@@ -725,7 +728,12 @@ int pa_seed_prepare(pa_plan_t *pl, const uint64_t *seed, void *stream) {
 }
 
 int pa_hash_prepared(pa_plan_t *pl, const uint64_t *key, uint64_t *out, int *status, void *stream) {
-    if (!pl || !key || !out || !pl->prepared) return PA_ERR_INVALID;
+    if (!pl || !key || !out) return PA_ERR_INVALID;
+    if (pl->p3) {
+        if (!p3_prepared(pl->p3)) return PA_ERR_INVALID;
+        return cuda_rc(p3_hash_prepared(pl->p3, (const u64 *)key, (u64 *)out, status, stream));
+    }
+    if (!pl->prepared) return PA_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     int e = cudaMemsetAsync(pl->flags, 0, pl->flags_bytes, s);
     Operands ops;

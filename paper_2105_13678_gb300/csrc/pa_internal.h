@@ -231,8 +231,8 @@ int launch_fill_coltw(const Xform &X, u64 *coltw, void *stream);
 
 // Three-prime backend launchers (pa_p3.cu).
 int p3_prepare_kernels();
-int p3_launch_fwd_col(const Geo3 &X, const Operands &S, int pairs, u32 *Y, void *stream);
-int p3_launch_row_mac(const Geo3 &X, const u32 *Y, u32 *S3, void *stream);
+int p3_launch_fwd_col(const Geo3 &X, const Operands &S, int pairs, u32 *Y, void *stream, bool pair = true);
+int p3_launch_row_mac(const Geo3 &X, const u32 *Y, u32 *S3, void *stream, int mode = 0, u32 *spec = nullptr);
 int p3_launch_inv_col(const Geo3 &X, u32 *S3, void *stream);
 int p3_launch_digits(const Geo3 &X, const u32 *S3, u64 *z, u64 npad, const u64 *c_src, u64 c_base, u64 *zero_out,
                      u64 zero_words, void *stream);
@@ -248,6 +248,10 @@ void p3_plan_query(const P3Plan *pl, uint64_t *len_mmh, uint64_t *len_mh, uint64
 const Geo3 *p3_stage(const P3Plan *pl, int stage);
 int p3_enqueue_mmh(P3Plan *pl, const u64 *key, const u64 *seed, u64 *y, bool canonical, void *stream);
 int p3_enqueue_mh(P3Plan *pl, const u64 *seed, u64 *out, int *status, void *stream);
+// Seed reuse: spectra of a_1..a_k and b (and a seed copy) kept in the plan.
+int p3_seed_prepare(P3Plan *pl, const u64 *seed, void *stream);
+int p3_hash_prepared(P3Plan *pl, const u64 *key, u64 *out, int *status, void *stream);
+bool p3_prepared(const P3Plan *pl);
 u64 *p3_ybuf(P3Plan *pl);
 int *p3_flags(P3Plan *pl);
 size_t p3_flags_bytes(const P3Plan *pl);

@@ -196,11 +196,29 @@ struct Desc {
 };
 
 // Algorithm 1 slices: pair i of Eq. 2 is (x_{i+1}, a_{i+1}); the pair of
-// Eq. 4 is (y, b) with b forced odd.
+// Eq. 4 is (y, b) with b forced odd.  Single operands (seed preparation and
+// prepared hashing) come in dx: mode 2 = a_{i+1}, 3 = x_{i+1}, 4 = b, 5 = y.
 __device__ __forceinline__ void descs(const Operands &S, u32 i, Desc &dx, Desc &da) {
     dx.force_odd = da.force_odd = 0;
     dx.check_ones = da.check_ones = 0;
     dx.zero = da.zero = 0;
+    if (S.mode >= 2) {
+        da.src = S.seed;
+        da.base = 0;
+        da.len = 0;
+        da.zero = 1;
+        dx.src = S.mode == 3 ? S.key : S.mode == 5 ? S.y : S.seed;
+        dx.base = S.mode == 4 ? S.k * S.gamma : S.mode == 5 ? 0 : (u64)i * S.gamma;
+        dx.len = S.gamma;
+        if (S.mode == 3) {
+            const u64 rem = S.n - dx.base;
+            dx.len = rem < S.gamma ? rem : S.gamma;
+            dx.check_ones = 1;
+        }
+        dx.force_odd = S.mode == 4;
+        dx.zero = S.mode == 5 && *S.y_zero != 0;
+        return;
+    }
     if (S.mode == 0) {
         dx.src = S.key;
         dx.base = (u64)i * S.gamma;
@@ -356,8 +374,8 @@ __global__ void __launch_bounds__(kColThreads) k3_fwd_col(Geo3 X, Operands S, u3
 // registers; each prime then runs its column transform through the same
 // shared tile in three rounds -- stages 0-3 in registers on 16 elements
 // (upper half zero), then 4-6 and 7-9 -- with its round twiddles staged in
-// shared memory.
-template <int LL, int TC>
+// shared memory.  PAIR: both operands of pair i; else the single operand i.
+template <int LL, int TC, bool PAIR>
 __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32 *__restrict__ Y) {
     pdl_wait();
     static_assert(LL == 10 && TC == 8, "one task per thread: R/16 x 8 columns = 512");
@@ -369,7 +387,7 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
     Desc dx, da;
     descs(S, i, dx, da);
     u32 *smx = sm3, *sma = sm3 + pxc((1u << LL) * TC);
-    uint2 *stw = reinterpret_cast<uint2 *>(sm3 + 2 * pxc((1u << LL) * TC));  // this prime's round tables
+    uint2 *stw = reinterpret_cast<uint2 *>(sm3 + (PAIR ? 2 : 1) * pxc((1u << LL) * TC));  // this prime's round tables
     bool ones = true;
     const u32 c = threadIdx.x & (TC - 1), lo = threadIdx.x >> 3;  // group lo: rows lo + 64 m
     constexpr u32 D64 = 64;
@@ -380,7 +398,7 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
         for (u32 m = 0; m < 8; m++) {
             const u64 pos = (e0 + (u64)(m * D64) * X.C) * X.b;
             rx[m] = digit_raw(X, dx, pos, ones);
-            ra[m] = digit_raw(X, da, pos, ones);
+            if (PAIR) ra[m] = digit_raw(X, da, pos, ones);
         }
     }
     const u32 a0 = pxc(lo * TC + c);
@@ -404,7 +422,7 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
 #pragma unroll
             for (u32 m = 0; m < 16; m++) smx[a0 + m * dsm] = v[m];
         }
-        {
+        if (PAIR) {
             u32 v[16];
 #pragma unroll
             for (u32 m = 0; m < 16; m++) v[m] = m < 8 ? shoup(ra[m], red, p) : 0u;
@@ -414,9 +432,9 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
         }
         __syncthreads();
         // stages 4-6 and 7-9: the standard partition's rounds 2 and 3
-        fwd3_round<3, true, false, false, LL, TC, true>(X, j, dx, da, smx, sma, Yx, Ya, c0, 4, 2, ones, stw);
+        fwd3_round<3, PAIR, false, false, LL, TC, true>(X, j, dx, da, smx, sma, Yx, Ya, c0, 4, 2, ones, stw);
         __syncthreads();
-        fwd3_round<3, true, false, true, LL, TC, true>(X, j, dx, da, smx, sma, Yx, Ya, c0, 7, 3, ones, stw);
+        fwd3_round<3, PAIR, false, true, LL, TC, true>(X, j, dx, da, smx, sma, Yx, Ya, c0, 7, 3, ones, stw);
         __syncthreads();
     }
     pdl_trigger();
@@ -434,10 +452,13 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
 
 // Row rounds: elements base + m*stride with stride >= 8 or (stride = 1 and
 // base a multiple of 8), so their padded words are px(base) + m * pstep(stride).
-template <int NS, int ACC, bool LAST, int LL>
+// MODE 0: both rows of pair i, product into acc; 1: row x only, its spectrum
+// stored to spec; 2: row x only, times the stored spectrum held in fa.
+template <int NS, int ACC, bool LAST, int LL, int MODE>
 __device__ __forceinline__ void row_fwd3(const Geo3 &X, u32 j, const u32 (&fx)[ACC], const u32 (&fa)[ACC],
                                          u32 *__restrict__ smx, u32 *__restrict__ sma, u32 s0, u32 rd, bool first,
-                                         u32 (&acc)[ACC]) {
+                                         u32 (&acc)[ACC], u32 *__restrict__ spec) {
+    constexpr bool TWO = MODE == 0;
     const u32 l = LL ? (u32)LL : X.logC, sh = l - s0 - NS, stride = 1u << sh, ngroups = (1u << l) >> NS;
     const u32 p = X.p[j], pinv = X.pinv[j];
     const u32 dsm = pstep(stride);
@@ -452,19 +473,30 @@ __device__ __forceinline__ void row_fwd3(const Geo3 &X, u32 j, const u32 (&fx)[A
 #pragma unroll
             for (int m = 0; m < (1 << NS); m++) {
                 vx[m] = first ? fx[t * (1 << NS) + m] : smx[a0 + m * dsm];
-                va[m] = first ? fa[t * (1 << NS) + m] : sma[a0 + m * dsm];
+                if (TWO) va[m] = first ? fa[t * (1 << NS) + m] : sma[a0 + m * dsm];
             }
             const uint2 *rt = tw + lo * ((1u << NS) - 1);
             dif3<NS, LAST, false>(vx, rt, p);
-            dif3<NS, LAST, false>(va, rt, p);
+            if (TWO) dif3<NS, LAST, false>(va, rt, p);
+            if (LAST && MODE == 1) {  // the last round has stride 1: elements base + m
+                if constexpr (NS == 3) {
+                    uint4 *d = reinterpret_cast<uint4 *>(spec + base);
+                    d[0] = make_uint4(vx[0], vx[1], vx[2], vx[3]);
+                    d[1] = make_uint4(vx[4], vx[5], vx[6], vx[7]);
+                } else {
+#pragma unroll
+                    for (int m = 0; m < (1 << NS); m++) spec[base + m] = vx[m];
+                }
+                continue;
+            }
 #pragma unroll
             for (int m = 0; m < (1 << NS); m++) {
                 if (LAST) {
                     u32 &a = acc[t * (1 << NS) + m];
-                    a = red2(a + mont(vx[m], va[m], p, pinv), 2 * p);
+                    a = red2(a + mont(vx[m], TWO ? va[m] : fa[t * (1 << NS) + m], p, pinv), 2 * p);
                 } else {
                     smx[a0 + m * dsm] = vx[m];
-                    sma[a0 + m * dsm] = va[m];
+                    if (TWO) sma[a0 + m * dsm] = va[m];
                 }
             }
         }
@@ -472,7 +504,7 @@ __device__ __forceinline__ void row_fwd3(const Geo3 &X, u32 j, const u32 (&fx)[A
 }
 
 // The first round's inputs of one row pair (elements g + m C/2^NS of group g).
-template <int NS, int ACC, int LL>
+template <int NS, int ACC, int LL, bool TWO>
 __device__ __forceinline__ void row_load3(const Geo3 &X, const u32 *__restrict__ xrow, const u32 *__restrict__ arow,
                                           u32 (&fx)[ACC], u32 (&fa)[ACC]) {
     const u32 l = LL ? (u32)LL : X.logC, stride = 1u << (l - NS), ngroups = (1u << l) >> NS;
@@ -483,7 +515,7 @@ __device__ __forceinline__ void row_load3(const Geo3 &X, const u32 *__restrict__
 #pragma unroll
             for (int m = 0; m < (1 << NS); m++) {
                 fx[t * (1 << NS) + m] = __ldg(xrow + g + m * stride);
-                fa[t * (1 << NS) + m] = __ldg(arow + g + m * stride);
+                if (TWO) fa[t * (1 << NS) + m] = __ldg(arow + g + m * stride);
             }
         }
     }
@@ -519,10 +551,36 @@ __device__ __forceinline__ void row_inv3(const Geo3 &X, u32 j, u32 *__restrict__
     }
 }
 
+// A stored row spectrum in the last forward round's order: thread group g
+// holds elements g 2^NS + m, m < 2^NS.
+template <int NS, int ACC>
+__device__ __forceinline__ void row_load_spec(u32 ngroups, const u32 *__restrict__ srow, u32 (&f)[ACC]) {
+#pragma unroll
+    for (int t = 0; t < (ACC >> NS); t++) {
+        const u32 g = threadIdx.x + t * blockDim.x;
+        if (g < ngroups) {
+            if constexpr (NS == 3) {
+                const uint4 *q = reinterpret_cast<const uint4 *>(srow + (g << 3));
+                const uint4 u = __ldg(q), w = __ldg(q + 1);
+                f[t * 8 + 0] = u.x, f[t * 8 + 1] = u.y, f[t * 8 + 2] = u.z, f[t * 8 + 3] = u.w;
+                f[t * 8 + 4] = w.x, f[t * 8 + 5] = w.y, f[t * 8 + 6] = w.z, f[t * 8 + 7] = w.w;
+            } else {
+#pragma unroll
+                for (int m = 0; m < (1 << NS); m++) f[t * (1 << NS) + m] = __ldg(srow + (g << NS) + m);
+            }
+        }
+    }
+}
+
 // grid (R, 3 primes); blockDim = C / ACC threads, ACC accumulators each.
-// grid (R, 3 primes); blockDim = C / ACC threads, ACC accumulators each.
-template <int ACC, int LL>
-__global__ void __launch_bounds__(1024) k3_row_mac(Geo3 X, const u32 *__restrict__ Y, u32 *__restrict__ S3) {
+// MODE 0: Eq. 2 / Eq. 4 product of the pairs' rows, then the inverse rows;
+// 1 (seed preparation): forward rows of the single operands, spectra stored
+// to spec ([prime][operand][T], last-round order); 2 (prepared hashing):
+// forward rows of the single operands times the stored spectra, then the
+// inverse rows.
+template <int ACC, int LL, int MODE>
+__global__ void __launch_bounds__(1024) k3_row_mac(Geo3 X, const u32 *__restrict__ Y, u32 *__restrict__ S3,
+                                                   u32 *__restrict__ spec) {
     pdl_wait();
     extern __shared__ u32 sm3[];
     const u32 j = blockIdx.y, row = blockIdx.x, l = LL ? (u32)LL : X.logC, C = 1u << l;
@@ -530,30 +588,40 @@ __global__ void __launch_bounds__(1024) k3_row_mac(Geo3 X, const u32 *__restrict
     u32 acc[ACC], fx[ACC], fa[ACC];
 #pragma unroll
     for (int m = 0; m < ACC; m++) acc[m] = 0;
-    const u32 nr = (l + 2) / 3, ns0 = round_ns(l, 0);
+    const u32 nr = (l + 2) / 3, ns0 = round_ns(l, 0), nsl = round_ns(l, nr - 1);
     for (u32 i = 0; i < X.K; i++) {
+        u32 *srow = MODE ? spec + ((u64)j * X.K + i) * X.T + (u64)row * C : nullptr;
         {  // the first round's inputs, loaded right before use (short register lifetimes)
             const u32 *xr = Y + ((u64)j * 2 * X.K + i) * X.T + (u64)row * C;
-            const u32 *ar = Y + ((u64)j * 2 * X.K + X.K + i) * X.T + (u64)row * C;
-#define P3_LOAD(NSV) row_load3<NSV, ACC, LL>(X, xr, ar, fx, fa)
+            const u32 *ar = MODE ? xr : Y + ((u64)j * 2 * X.K + X.K + i) * X.T + (u64)row * C;
+#define P3_LOAD(NSV) row_load3<NSV, ACC, LL, MODE == 0>(X, xr, ar, fx, fa)
             P3_DISPATCH_NS(ns0, P3_LOAD);
 #undef P3_LOAD
+            if (MODE == 2) {
+#define P3_LOADS(NSV) row_load_spec<NSV, ACC>(C >> NSV, srow, fa)
+                P3_DISPATCH_NS(nsl, P3_LOADS);
+#undef P3_LOADS
+            }
         }
 #pragma unroll(LL > 0 ? 8 : 1)
         for (u32 rd = 0; rd < nr; rd++) {
             const u32 s0 = round_s0(l, rd), ns = round_ns(l, rd);
             const bool first = rd == 0, last = rd == nr - 1;
-#define P3_ROWF(NSV)                                                                \
-    do {                                                                            \
-        if (last)                                                                   \
-            row_fwd3<NSV, ACC, true, LL>(X, j, fx, fa, smx, sma, s0, rd, first, acc);   \
-        else                                                                        \
-            row_fwd3<NSV, ACC, false, LL>(X, j, fx, fa, smx, sma, s0, rd, first, acc);  \
+#define P3_ROWF(NSV)                                                                                  \
+    do {                                                                                              \
+        if (last)                                                                                     \
+            row_fwd3<NSV, ACC, true, LL, MODE>(X, j, fx, fa, smx, sma, s0, rd, first, acc, srow);     \
+        else                                                                                          \
+            row_fwd3<NSV, ACC, false, LL, MODE>(X, j, fx, fa, smx, sma, s0, rd, first, acc, srow);    \
     } while (0)
             P3_DISPATCH_NS(ns, P3_ROWF);
 #undef P3_ROWF
             __syncthreads();
         }
+    }
+    if (MODE == 1) {
+        pdl_trigger();
+        return;
     }
     u32 *Srow = S3 + (u64)j * X.T + (u64)row * C;
 #pragma unroll(LL > 0 ? 8 : 1)
@@ -768,6 +836,22 @@ static size_t col_smem3(const Geo3 &X, bool pair) {
 }
 static size_t row_smem3(const Geo3 &X) { return (size_t)2 * (X.C + (X.C >> 3) + 8) * sizeof(u32); }
 
+template <int MODE>
+static cudaError_t p3_row_attrs(int big) {
+    cudaError_t e;
+#define P3_ATTR(f) \
+    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    P3_ATTR((k3_row_mac<8, 0, MODE>))
+    P3_ATTR((k3_row_mac<16, 0, MODE>))
+    P3_ATTR((k3_row_mac<8, 10, MODE>))
+    P3_ATTR((k3_row_mac<8, 11, MODE>))
+    P3_ATTR((k3_row_mac<8, 12, MODE>))
+    P3_ATTR((k3_row_mac<8, 13, MODE>))
+    P3_ATTR((k3_row_mac<16, 14, MODE>))
+#undef P3_ATTR
+    return cudaSuccess;
+}
+
 int p3_prepare_kernels() {
     static bool done = false;
     if (done) return 0;
@@ -776,45 +860,50 @@ int p3_prepare_kernels() {
 #define P3_ATTR(f) \
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     P3_ATTR((k3_fwd_col<true, 0, 0>))
-    P3_ATTR((k3_fwd_col_all<10, 8>))
+    P3_ATTR((k3_fwd_col<false, 0, 0>))
+    P3_ATTR((k3_fwd_col_all<10, 8, true>))
+    P3_ATTR((k3_fwd_col_all<10, 8, false>))
     P3_ATTR((k3_inv_col<0, 0>))
     P3_ATTR((k3_inv_col<10, 8>))
-    P3_ATTR((k3_row_mac<8, 0>))
-    P3_ATTR((k3_row_mac<16, 0>))
-    P3_ATTR((k3_row_mac<8, 10>))
-    P3_ATTR((k3_row_mac<8, 11>))
-    P3_ATTR((k3_row_mac<8, 12>))
-    P3_ATTR((k3_row_mac<8, 13>))
-    P3_ATTR((k3_row_mac<16, 14>))
 #undef P3_ATTR
+    if ((e = p3_row_attrs<0>(big)) || (e = p3_row_attrs<1>(big)) || (e = p3_row_attrs<2>(big))) return e;
     done = true;
     return 0;
 }
 
 // Compile-time geometry for the production shapes (R = 2^10, 8-column tiles;
-// rows of 2^10 .. 2^14), runtime geometry otherwise.
-int p3_launch_fwd_col(const Geo3 &X, const Operands &S, int pairs, u32 *Y, void *stream) {
+// rows of 2^10 .. 2^14), runtime geometry otherwise.  pair: both operands of
+// each pair (Eq. 2 / Eq. 4), else the single operands of S.mode.
+int p3_launch_fwd_col(const Geo3 &X, const Operands &S, int pairs, u32 *Y, void *stream, bool pair) {
     if (int e = p3_prepare_kernels()) return e;
     const dim3 grid(X.C / X.tc, pairs, 3);
-    const size_t smem = col_smem3(X, true);
+    const size_t smem = col_smem3(X, pair);
     cudaStream_t s = (cudaStream_t)stream;
-    if (X.logR == 10 && X.tc == 8 && X.rof4R)
-        TRACED("p3_fwd_col", X.stage, stream,
-               (launch_pdl(k3_fwd_col_all<10, 8>, dim3(pairs, X.C / X.tc), dim3(512),
-                           smem + (X.rof4R + 64 * 15) * sizeof(uint2), s, X, S, Y)));
-    else
+    const size_t smem_all = smem + (X.rof4R + 64 * 15) * sizeof(uint2);
+    if (X.logR == 10 && X.tc == 8 && X.rof4R) {
+        if (pair)
+            TRACED("p3_fwd_col", X.stage, stream,
+                   (launch_pdl(k3_fwd_col_all<10, 8, true>, dim3(pairs, X.C / X.tc), dim3(512), smem_all, s, X, S, Y)));
+        else
+            TRACED("p3_fwd_col", X.stage, stream,
+                   (launch_pdl(k3_fwd_col_all<10, 8, false>, dim3(pairs, X.C / X.tc), dim3(512), smem_all, s, X, S, Y)));
+    } else if (pair) {
         TRACED("p3_fwd_col", X.stage, stream,
                (launch_pdl(k3_fwd_col<true, 0, 0>, grid, dim3(kColThreads), smem, s, X, S, Y)));
+    } else {
+        TRACED("p3_fwd_col", X.stage, stream,
+               (launch_pdl(k3_fwd_col<false, 0, 0>, grid, dim3(kColThreads), smem, s, X, S, Y)));
+    }
     return (int)cudaGetLastError();
 }
 
-int p3_launch_row_mac(const Geo3 &X, const u32 *Y, u32 *S3, void *stream) {
-    if (int e = p3_prepare_kernels()) return e;
+template <int MODE>
+static void p3_row_launch(const Geo3 &X, const u32 *Y, u32 *S3, u32 *spec, cudaStream_t s, void *stream) {
     const dim3 grid(X.R, 3);
     const size_t smem = row_smem3(X);
-    cudaStream_t s = (cudaStream_t)stream;
+    const char *name = MODE == 1 ? "p3_row_store" : "p3_row_mac";
 #define P3_ROW(A, L) \
-    TRACED("p3_row_mac", X.stage, stream, (launch_pdl(k3_row_mac<A, L>, grid, dim3(X.C / A), smem, s, X, Y, S3)))
+    TRACED(name, X.stage, stream, (launch_pdl(k3_row_mac<A, L, MODE>, grid, dim3(X.C / A), smem, s, X, Y, S3, spec)))
     switch (X.logC) {
     case 10: P3_ROW(8, 10); break;
     case 11: P3_ROW(8, 11); break;
@@ -828,6 +917,19 @@ int p3_launch_row_mac(const Geo3 &X, const u32 *Y, u32 *S3, void *stream) {
             P3_ROW(8, 0);
     }
 #undef P3_ROW
+}
+
+// mode 0: pairs (spec unused); 1: store the single operands' spectra to
+// spec; 2: single operands times the spectra stored in spec.
+int p3_launch_row_mac(const Geo3 &X, const u32 *Y, u32 *S3, void *stream, int mode, u32 *spec) {
+    if (int e = p3_prepare_kernels()) return e;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (mode == 0)
+        p3_row_launch<0>(X, Y, S3, spec, s, stream);
+    else if (mode == 1)
+        p3_row_launch<1>(X, Y, S3, spec, s, stream);
+    else
+        p3_row_launch<2>(X, Y, S3, spec, s, stream);
     return (int)cudaGetLastError();
 }
 
@@ -996,6 +1098,10 @@ struct P3Plan {
     unsigned char *cstate = nullptr, *cta_state = nullptr, *cta_cin = nullptr;
     int *flags = nullptr;
     size_t flags_bytes = 0;
+    // seed reuse: spectra of a_1..a_k ([prime][i][T]) and b ([prime][T]), seed copy
+    u32 *spec_a = nullptr, *spec_b = nullptr;
+    u64 *seed_copy = nullptr;
+    bool prepared = false;
     ~P3Plan() {
         for (void *p : allocs) cudaFree(p);
     }
@@ -1203,8 +1309,9 @@ static CarryDev p3_carry_dev(P3Plan *pl, const Geo3 &X, bool ring, int *allones)
     return cd;
 }
 
-// Eq. 2: y = sum_i a_i x_i mod 2^gamma - 1 into y (gamma bits).
-int p3_enqueue_mmh(P3Plan *pl, const u64 *key, const u64 *seed, u64 *y, bool canonical, void *stream) {
+// Eq. 2: y = sum_i a_i x_i mod 2^gamma - 1 into y (gamma bits).  prep: the
+// spectra of a_i come from the plan (seed reuse), only the x_i are transformed.
+static int mmh_impl(P3Plan *pl, const u64 *key, const u64 *seed, u64 *y, bool canonical, void *stream, bool prep) {
     cudaStream_t s = (cudaStream_t)stream;
     int e;
     if ((e = cudaMemsetAsync(pl->flags, 0, pl->flags_bytes, s))) return e;
@@ -1218,10 +1325,10 @@ int p3_enqueue_mmh(P3Plan *pl, const u64 *key, const u64 *seed, u64 *y, bool can
     ops.n = pl->n;
     ops.gamma = pl->gamma;
     ops.k = pl->k;
-    ops.mode = 0;
+    ops.mode = prep ? 3 : 0;
     const Geo3 &X = pl->mmh;
-    if ((e = p3_launch_fwd_col(X, ops, (int)pl->k, pl->Y, stream))) return e;
-    if ((e = p3_launch_row_mac(X, pl->Y, pl->S3, stream))) return e;
+    if ((e = p3_launch_fwd_col(X, ops, (int)pl->k, pl->Y, stream, !prep))) return e;
+    if ((e = p3_launch_row_mac(X, pl->Y, pl->S3, stream, prep ? 2 : 0, prep ? pl->spec_a : nullptr))) return e;
     if ((e = p3_launch_inv_col(X, pl->S3, stream))) return e;
     const CarryDev cd = p3_carry_dev(pl, X, true, pl->flags + 1);
     u64 *z = (u64 *)pl->Y;
@@ -1233,8 +1340,9 @@ int p3_enqueue_mmh(P3Plan *pl, const u64 *key, const u64 *seed, u64 *y, bool can
     return 0;
 }
 
-// Eq. 4: out = ((b y + c) mod 2^gamma) >> (gamma - r), y from the plan's buffer.
-int p3_enqueue_mh(P3Plan *pl, const u64 *seed, u64 *out, int *status, void *stream) {
+// Eq. 4: out = ((b y + c) mod 2^gamma) >> (gamma - r), y from the plan's
+// buffer.  prep: the spectrum of b comes from the plan, only y is transformed.
+static int mh_impl(P3Plan *pl, const u64 *seed, u64 *out, int *status, void *stream, bool prep) {
     int e;
     Operands ops;
     ops.pair0 = 0;
@@ -1246,10 +1354,10 @@ int p3_enqueue_mh(P3Plan *pl, const u64 *seed, u64 *out, int *status, void *stre
     ops.n = pl->n;
     ops.gamma = pl->gamma;
     ops.k = pl->k;
-    ops.mode = 1;
+    ops.mode = prep ? 5 : 1;
     const Geo3 &X = pl->mh;
-    if ((e = p3_launch_fwd_col(X, ops, 1, pl->Y, stream))) return e;
-    if ((e = p3_launch_row_mac(X, pl->Y, pl->S3, stream))) return e;
+    if ((e = p3_launch_fwd_col(X, ops, 1, pl->Y, stream, !prep))) return e;
+    if ((e = p3_launch_row_mac(X, pl->Y, pl->S3, stream, prep ? 2 : 0, prep ? pl->spec_b : nullptr))) return e;
     if ((e = p3_launch_inv_col(X, pl->S3, stream))) return e;
     const CarryDev cd = p3_carry_dev(pl, X, false, pl->flags + 2);
     u64 *z = (u64 *)pl->Y;
@@ -1262,6 +1370,57 @@ int p3_enqueue_mh(P3Plan *pl, const u64 *seed, u64 *out, int *status, void *stre
     if ((e = launch_extract(pl->tbuf, pl->gamma, pl->r, pl->flags, pl->k, out, status, stream, true))) return e;
     return 0;
 }
+
+int p3_enqueue_mmh(P3Plan *pl, const u64 *key, const u64 *seed, u64 *y, bool canonical, void *stream) {
+    return mmh_impl(pl, key, seed, y, canonical, stream, false);
+}
+
+int p3_enqueue_mh(P3Plan *pl, const u64 *seed, u64 *out, int *status, void *stream) {
+    return mh_impl(pl, seed, out, status, stream, false);
+}
+
+// Seed reuse: forward transforms (columns, then rows) of a_1..a_k and of b,
+// their spectra kept in the plan with a copy of the seed (c is read from it).
+int p3_seed_prepare(P3Plan *pl, const u64 *seed, void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t sw = ((pl->k + 2) * pl->gamma + 63) / 64;
+    if (!pl->spec_a) {
+        int err = PA_OK;
+        pl->spec_a = (u32 *)pl->alloc(3 * pl->k * pl->mmh.T * 4, &err);
+        pl->spec_b = (u32 *)pl->alloc(3 * pl->mh.T * 4, &err);
+        pl->seed_copy = (u64 *)pl->alloc(sw * 8, &err);
+        if (err) return err;
+    }
+    pl->prepared = false;
+    int e;
+    if ((e = cudaMemcpyAsync(pl->seed_copy, seed, sw * 8, cudaMemcpyDeviceToDevice, s))) return e;
+    Operands ops;
+    ops.pair0 = 0;
+    ops.key = nullptr;
+    ops.seed = pl->seed_copy;
+    ops.y = nullptr;
+    ops.y_zero = nullptr;
+    ops.reload = pl->flags;
+    ops.n = pl->n;
+    ops.gamma = pl->gamma;
+    ops.k = pl->k;
+    ops.mode = 2;  // a_i
+    if ((e = p3_launch_fwd_col(pl->mmh, ops, (int)pl->k, pl->Y, stream, false))) return e;
+    if ((e = p3_launch_row_mac(pl->mmh, pl->Y, pl->S3, stream, 1, pl->spec_a))) return e;
+    ops.mode = 4;  // b
+    if ((e = p3_launch_fwd_col(pl->mh, ops, 1, pl->Y, stream, false))) return e;
+    if ((e = p3_launch_row_mac(pl->mh, pl->Y, pl->S3, stream, 1, pl->spec_b))) return e;
+    pl->prepared = true;
+    return 0;
+}
+
+int p3_hash_prepared(P3Plan *pl, const u64 *key, u64 *out, int *status, void *stream) {
+    int e = mmh_impl(pl, key, pl->seed_copy, pl->ybuf, false, stream, true);
+    if (!e) e = mh_impl(pl, pl->seed_copy, out, status, stream, true);
+    return e;
+}
+
+bool p3_prepared(const P3Plan *pl) { return pl->prepared; }
 
 u64 *p3_ybuf(P3Plan *pl) { return pl->ybuf; }
 int *p3_flags(P3Plan *pl) { return pl->flags; }
