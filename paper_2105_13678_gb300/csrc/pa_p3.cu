@@ -478,7 +478,7 @@ __device__ __forceinline__ void row_fwd3(const Geo3 &X, u32 j, const u32 (&fx)[A
             const uint2 *rt = tw + lo * ((1u << NS) - 1);
             dif3<NS, LAST, false>(vx, rt, p);
             if (TWO) dif3<NS, LAST, false>(va, rt, p);
-            if (LAST && MODE == 1) {  // the last round has stride 1: elements base + m
+            if constexpr (LAST && MODE == 1) {  // the last round has stride 1: elements base + m
                 if constexpr (NS == 3) {
                     uint4 *d = reinterpret_cast<uint4 *>(spec + base);
                     d[0] = make_uint4(vx[0], vx[1], vx[2], vx[3]);
@@ -487,16 +487,16 @@ __device__ __forceinline__ void row_fwd3(const Geo3 &X, u32 j, const u32 (&fx)[A
 #pragma unroll
                     for (int m = 0; m < (1 << NS); m++) spec[base + m] = vx[m];
                 }
-                continue;
-            }
+            } else {
 #pragma unroll
-            for (int m = 0; m < (1 << NS); m++) {
-                if (LAST) {
-                    u32 &a = acc[t * (1 << NS) + m];
-                    a = red2(a + mont(vx[m], TWO ? va[m] : fa[t * (1 << NS) + m], p, pinv), 2 * p);
-                } else {
-                    smx[a0 + m * dsm] = vx[m];
-                    if (TWO) sma[a0 + m * dsm] = va[m];
+                for (int m = 0; m < (1 << NS); m++) {
+                    if (LAST) {
+                        u32 &a = acc[t * (1 << NS) + m];
+                        a = red2(a + mont(vx[m], TWO ? va[m] : fa[t * (1 << NS) + m], p, pinv), 2 * p);
+                    } else {
+                        smx[a0 + m * dsm] = vx[m];
+                        if (TWO) sma[a0 + m * dsm] = va[m];
+                    }
                 }
             }
         }
@@ -707,26 +707,28 @@ __global__ void __launch_bounds__(kColThreads) k3_inv_col(Geo3 X, u32 *__restric
 #undef P3_INV
         __syncthreads();
     }
-    if (M4 && rlast == 2) {
-        // stages 3..0: 16 rows lo + 64 m of one column per task, written to S3
-        const u32 p = X.p[j];
-        const uint2 *itw = X.itwR[j] + X.rof4Ri;
-        u32 *Sj = S3 + (u64)j * X.T;
-        for (u32 task = threadIdx.x; task < 64 * TC; task += blockDim.x) {
-            const u32 c = task & (TC - 1), lo = task >> 3;
-            const u32 a0 = pxc(lo * TC + c);
-            const u64 e0 = (u64)lo * X.C + c0 + c, dY = (u64)64 * X.C;
-            u32 v[16];
+    if constexpr (M4) {
+        if (rlast == 2) {
+            // stages 3..0: 16 rows lo + 64 m of one column per task, written to S3
+            const u32 p = X.p[j];
+            const uint2 *itw = X.itwR[j] + X.rof4Ri;
+            u32 *Sj = S3 + (u64)j * X.T;
+            for (u32 task = threadIdx.x; task < 64 * TC; task += blockDim.x) {
+                const u32 c = task & (TC - 1), lo = task >> 3;
+                const u32 a0 = pxc(lo * TC + c);
+                const u64 e0 = (u64)lo * X.C + c0 + c, dY = (u64)64 * X.C;
+                u32 v[16];
 #pragma unroll
-            for (u32 m = 0; m < 16; m++) v[m] = sm3[a0 + m * 576];  // 64 rows apart: pstepc(512)
-            if (ho) {
-                dit16<true>(v, itw + lo * 15, p);
+                for (u32 m = 0; m < 16; m++) v[m] = sm3[a0 + m * 576];  // 64 rows apart: pstepc(512)
+                if (ho) {
+                    dit16<true>(v, itw + lo * 15, p);
 #pragma unroll
-                for (u32 m = 0; m < 8; m++) Sj[e0 + m * dY] = v[m];
-            } else {
-                dit16<false>(v, itw + lo * 15, p);
+                    for (u32 m = 0; m < 8; m++) Sj[e0 + m * dY] = v[m];
+                } else {
+                    dit16<false>(v, itw + lo * 15, p);
 #pragma unroll
-                for (u32 m = 0; m < 16; m++) Sj[e0 + m * dY] = v[m];
+                    for (u32 m = 0; m < 16; m++) Sj[e0 + m * dY] = v[m];
+                }
             }
         }
     }
