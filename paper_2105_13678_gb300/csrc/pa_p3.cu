@@ -196,13 +196,15 @@ struct Desc {
 };
 
 // Algorithm 1 slices: pair i of Eq. 2 is (x_{i+1}, a_{i+1}); the pair of
-// Eq. 4 is (y, b) with b forced odd.  Single operands (seed preparation and
-// prepared hashing) come in dx: mode 2 = a_{i+1}, 3 = x_{i+1}, 4 = b, 5 = y.
+// Eq. 4 is (y, b) with b forced odd.  Single operands (PAIR false: seed
+// preparation and prepared hashing) come in dx: mode 2 = a_{i+1}, 3 = x_{i+1},
+// 4 = b, 5 = y.
+template <bool PAIR>
 __device__ __forceinline__ void descs(const Operands &S, u32 i, Desc &dx, Desc &da) {
     dx.force_odd = da.force_odd = 0;
     dx.check_ones = da.check_ones = 0;
     dx.zero = da.zero = 0;
-    if (S.mode >= 2) {
+    if constexpr (!PAIR) {
         da.src = S.seed;
         da.base = 0;
         da.len = 0;
@@ -335,7 +337,7 @@ __global__ void __launch_bounds__(kColThreads) k3_fwd_col(Geo3 X, Operands S, u3
     extern __shared__ u32 sm3[];
     const u32 j = blockIdx.z, tc = TC ? (u32)TC : X.tc, c0 = blockIdx.x * tc, i = blockIdx.y + S.pair0;
     Desc dx, da;
-    descs(S, i, dx, da);
+    descs<PAIR>(S, i, dx, da);
     if (j) dx.check_ones = 0;
     u32 *Yx = Y + ((u64)j * 2 * X.K + i) * X.T, *Ya = Y + ((u64)j * 2 * X.K + X.K + i) * X.T;
     u32 *smx = sm3, *sma = sm3 + pxc(X.R * tc);
@@ -385,7 +387,7 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
     // reused from L2 by the CTAs of all pairs
     const u32 i = blockIdx.x + S.pair0, c0 = blockIdx.y * TC;
     Desc dx, da;
-    descs(S, i, dx, da);
+    descs<PAIR>(S, i, dx, da);
     u32 *smx = sm3, *sma = sm3 + pxc((1u << LL) * TC);
     uint2 *stw = reinterpret_cast<uint2 *>(sm3 + (PAIR ? 2 : 1) * pxc((1u << LL) * TC));  // this prime's round tables
     bool ones = true;
