@@ -62,13 +62,18 @@ def test_prepared_matches_plain_for_several_keys(n, r, gamma, backend):
     plan.close()
 
 
-@pytest.mark.parametrize("backend", [GOLDILOCKS, P3])
-def test_prepared_at_paper_scale(backend):
-    """n = 2.6e8, r = 0.1 n (gamma = 30402457, k = 9): prepared output equals
-    the plain path's, whose parity with the oracle the paper-scale parity test
-    holds; a second seed replaces the first."""
-    n, r = 260_000_000, 26_000_000
+@pytest.mark.parametrize("backend,n,logc", [(GOLDILOCKS, 260_000_000, None), (P3, 260_000_000, 11),
+                                             (P3, 500_000_000, 12), (P3, 600_000_000, 13), (P3, 1_000_000_000, 14)])
+def test_prepared_at_paper_scale(backend, n, logc):
+    """r = 0.1 n (n = 2.6e8: gamma = 30402457, k = 9), and on the three-prime
+    plan row lengths 2^11 .. 2^14 (the 2^14 rows hold 16 accumulators per
+    thread): prepared output equals the plain path's, whose parity with the
+    oracle the paper-scale parity tests hold; a second seed replaces the
+    first."""
+    r = n // 10
     plan = _plan_or_skip(n, r, 0, backend)
+    if logc is not None:
+        assert plan.geometry(0)[1] == logc
     g, k = plan.gamma, plan.k
     key, seed = synthetic.block_inputs(2, n, (k + 2) * g)
     _, seed2 = synthetic.block_inputs(12, n, (k + 2) * g)
