@@ -134,7 +134,7 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# Algorithmic work of each kernel, per launch, for one plan (see DESIGN.md):
+# Algorithmic work of each kernel, per launch, for one plan:
 # bytes = compulsory global reads + writes; products = F_q multiplications;
 # alu = integer-ALU-pipe operations of the F_q arithmetic the kernel must do,
 # counted from the carry-chain sequences of the field code: add 6, sub 8,
