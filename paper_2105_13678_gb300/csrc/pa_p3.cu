@@ -409,6 +409,7 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
     for (u32 j = 0; j < 3; j++) {
         const u32 p = X.p[j];
         const uint2 red = X.red[j];
+        const bool raw = (1ULL << X.b) <= 2ULL * p;  // b-bit digits already lie in [0, 2p)
         u32 *Yx = Y + ((u64)j * 2 * X.K + i) * X.T, *Ya = Y + ((u64)j * 2 * X.K + X.K + i) * X.T;
         {
             const u32 ntw = X.rof4R + 64 * 15;  // standard rounds, then the 4-stage first round
@@ -419,7 +420,7 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
         {
             u32 v[16];
 #pragma unroll
-            for (u32 m = 0; m < 16; m++) v[m] = m < 8 ? shoup(rx[m], red, p) : 0u;
+            for (u32 m = 0; m < 16; m++) v[m] = m < 8 ? (raw ? rx[m] : shoup(rx[m], red, p)) : 0u;
             dif16_hz(v, rt, p);
 #pragma unroll
             for (u32 m = 0; m < 16; m++) smx[a0 + m * dsm] = v[m];
@@ -427,7 +428,7 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
         if (PAIR) {
             u32 v[16];
 #pragma unroll
-            for (u32 m = 0; m < 16; m++) v[m] = m < 8 ? shoup(ra[m], red, p) : 0u;
+            for (u32 m = 0; m < 16; m++) v[m] = m < 8 ? (raw ? ra[m] : shoup(ra[m], red, p)) : 0u;
             dif16_hz(v, rt, p);
 #pragma unroll
             for (u32 m = 0; m < 16; m++) sma[a0 + m * dsm] = v[m];
