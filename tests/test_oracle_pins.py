@@ -1,8 +1,9 @@
 """Pins for the CPU oracle (``oracle/``) against facts that do not come from
 the oracle's own code: library routines (CPython big-integer ``*`` and ``%``),
 closed forms (the exact MMH collision count of Eq. 2), invariants (MMH
-linearity, MH shift-equivariance in c), textbook primality tests of the
-Mersenne table, and the parameter points printed in the paper (Table 3).
+linearity, MH shift-equivariance in c), brute force of Algorithm 1 from Eq. 2
+and Eq. 4 on tiny inputs (every key at gamma <= 7), textbook primality tests of
+the Mersenne table, and the parameter points printed in the paper (Table 3).
 
 A plausible slip anywhere in the oracle (a dropped carry, a wrong bit offset,
 a transposed seed slice, a missing final reduction) fails at least one check.
@@ -300,6 +301,56 @@ def test_pa_hash_is_mh_of_mmh_and_ignores_bits_past_n():
     assert np.array_equal(oracle.pa_hash(dirty, n, seed, r, gamma, k)[1], out)
     assert out.size == (r + 63) // 64
     assert int(out[-1]) >> (r % 64) == 0       # bits past r are zero
+
+
+def _algorithm1_direct(key_int, n, seed_int, r, gamma, k):
+    """Algorithm 1 evaluated from Eq. 2 and Eq. 4 on Python integers, slice by
+    slice (brute force for tiny sizes)."""
+    mask, p = (1 << gamma) - 1, (1 << gamma) - 1
+    key_int &= (1 << n) - 1
+    xs = [(key_int >> (i * gamma)) & mask for i in range(k)]
+    if any(x == p for x in xs):
+        return oracle.ORA_RELOAD, 0
+    sl = [(seed_int >> (i * gamma)) & mask for i in range(k + 2)]
+    y = sum((a % p) * x for a, x in zip(sl[:k], xs)) % p
+    t = ((sl[k] | 1) * y + sl[k + 1]) % (1 << gamma)
+    return oracle.ORA_OK, t >> (gamma - r)
+
+
+@pytest.mark.parametrize("gamma,k", [(2, 1), (2, 2), (3, 1), (3, 2), (5, 1), (5, 2), (7, 1), (7, 2)])
+def test_algorithm1_exhaustive_over_keys_tiny(gamma, k):
+    """Brute force: every key of n = k gamma and n = k gamma - 1 bits, every
+    beta < gamma, three seeds; the oracle's status and output bits equal the
+    direct evaluation (reload included)."""
+    rng = random.Random(gamma * 31 + k)
+    for n in {k * gamma, k * gamma - 1} - {0}:
+        for _ in range(3):
+            seed_int = rng.getrandbits((k + 2) * gamma)
+            seed = oracle.int_to_words(seed_int, oracle.words((k + 2) * gamma) + 1)
+            for r in range(1, gamma):
+                for key_int in range(1 << n):
+                    key = oracle.int_to_words(key_int, oracle.words(n) + 1)
+                    rc, out, _ = oracle.pa_hash(key, n, seed, r, gamma, k)
+                    want_rc, want = _algorithm1_direct(key_int, n, seed_int, r, gamma, k)
+                    assert rc == want_rc
+                    assert oracle.words_to_int(out) == want
+
+
+@pytest.mark.parametrize("gamma,k", [(13, 16), (17, 5), (19, 9), (31, 16), (61, 12), (89, 3), (607, 7)])
+def test_algorithm1_random_keys_small(gamma, k):
+    """The same direct evaluation on random keys, seeds and output lengths at
+    the small Mersenne exponents, ragged n included."""
+    rng = random.Random(gamma + 1000 * k)
+    for _ in range(20):
+        n = rng.randrange((k - 1) * gamma + 1, k * gamma + 1)
+        r = rng.randrange(1, gamma)
+        key_int = rng.getrandbits(n)
+        seed_int = rng.getrandbits((k + 2) * gamma)
+        key = oracle.int_to_words(key_int, oracle.words(n) + 1)
+        seed = oracle.int_to_words(seed_int, oracle.words((k + 2) * gamma) + 1)
+        rc, out, _ = oracle.pa_hash(key, n, seed, r, gamma, k)
+        want_rc, want = _algorithm1_direct(key_int, n, seed_int, r, gamma, k)
+        assert rc == want_rc and oracle.words_to_int(out) == want
 
 
 def test_pa_hash_output_is_not_trivial():
