@@ -94,3 +94,25 @@ def test_backend_parameter_and_estimates():
         _lib.plan_estimate_bytes(1000, 10, backend=3)
     assert e.value.code == -1
     assert _lib.plan_estimate_bytes(61 * 3, 10, gamma=61, backend=_lib.BACKEND_P3) > 0
+    # n = 1e9 (gamma = 136279841): the three-prime Eq. 2 transform would be twice the Goldilocks one
+    g9 = _lib.plan_estimate_bytes(1_000_000_000, 100_000_000, backend=_lib.BACKEND_GOLDILOCKS)
+    assert _lib.plan_estimate_bytes(1_000_000_000, 100_000_000) == g9
+    assert _lib.plan_estimate_bytes(1_000_000_000, 100_000_000, backend=_lib.BACKEND_P3) > g9
+
+
+def test_oracle_and_library_share_no_code():
+    """The oracle includes only C standard headers and the package never names
+    the oracle: the two sides share no code, header or table, and only the
+    seeded input generator (which holds none of the hash arithmetic) serves
+    both."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with open(os.path.join(root, "oracle", "pa_oracle.c")) as f:
+        incs = re.findall(r'#include\s*[<"]([^>"]+)[>"]', f.read())
+    assert incs and all(h in ("stdint.h", "stdlib.h", "string.h", "stdio.h", "stddef.h") for h in incs), incs
+    pkg = os.path.join(root, "paper_2105_13678_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for name in files:
+            if name.endswith((".py", ".cu", ".cuh", ".h", ".cpp")) and name != "synthetic.py":
+                with open(os.path.join(dirpath, name)) as f:
+                    text = f.read()
+                assert not re.search(r"\bimport\s+oracle\b|\bfrom\s+oracle\b|pa_oracle|liboracle", text), name
