@@ -167,6 +167,7 @@ struct pa_plan_s {
     void *alloc(size_t bytes, int *err) {
         void *p = nullptr;
         if (cudaMalloc(&p, bytes ? bytes : 8) != cudaSuccess) {
+            cudaGetLastError();  // an allocation failure must not read as a later launch's error
             *err = PA_ERR_NOMEM;
             return nullptr;
         }
@@ -697,11 +698,11 @@ int pa_seed_prepare(pa_plan_t *pl, const uint64_t *seed, void *stream) {
     }
     cudaStream_t s = (cudaStream_t)stream;
     const uint64_t sw = ((pl->k + 2) * pl->gamma + 63) / 64;
-    if (!pl->spec_a) {
+    if (!pl->spec_a || !pl->spec_b || !pl->seed_copy) {  // first call, or a retry after a failed allocation
         int err = PA_OK;
-        pl->spec_a = (u64 *)pl->alloc(pl->k * pl->mmh.N * 8, &err);
-        pl->spec_b = (u64 *)pl->alloc(pl->mh.N * 8, &err);
-        pl->seed_copy = (u64 *)pl->alloc(sw * 8, &err);
+        if (!pl->spec_a) pl->spec_a = (u64 *)pl->alloc(pl->k * pl->mmh.N * 8, &err);
+        if (!pl->spec_b) pl->spec_b = (u64 *)pl->alloc(pl->mh.N * 8, &err);
+        if (!pl->seed_copy) pl->seed_copy = (u64 *)pl->alloc(sw * 8, &err);
         if (err) return err;
     }
     pl->prepared = false;

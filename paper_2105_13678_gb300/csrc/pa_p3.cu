@@ -1114,6 +1114,7 @@ struct P3Plan {
         void *p = nullptr;
         if (*err) return nullptr;
         if (cudaMalloc(&p, bytes ? bytes : 8) != cudaSuccess) {
+            cudaGetLastError();  // an allocation failure must not read as a later launch's error
             *err = PA_ERR_NOMEM;
             return nullptr;
         }
@@ -1389,11 +1390,11 @@ int p3_enqueue_mh(P3Plan *pl, const u64 *seed, u64 *out, int *status, void *stre
 int p3_seed_prepare(P3Plan *pl, const u64 *seed, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     const uint64_t sw = ((pl->k + 2) * pl->gamma + 63) / 64;
-    if (!pl->spec_a) {
+    if (!pl->spec_a || !pl->spec_b || !pl->seed_copy) {  // first call, or a retry after a failed allocation
         int err = PA_OK;
-        pl->spec_a = (u32 *)pl->alloc(3 * pl->k * pl->mmh.T * 4, &err);
-        pl->spec_b = (u32 *)pl->alloc(3 * pl->mh.T * 4, &err);
-        pl->seed_copy = (u64 *)pl->alloc(sw * 8, &err);
+        if (!pl->spec_a) pl->spec_a = (u32 *)pl->alloc(3 * pl->k * pl->mmh.T * 4, &err);
+        if (!pl->spec_b) pl->spec_b = (u32 *)pl->alloc(3 * pl->mh.T * 4, &err);
+        if (!pl->seed_copy) pl->seed_copy = (u64 *)pl->alloc(sw * 8, &err);
         if (err) return err;
     }
     pl->prepared = false;
