@@ -156,7 +156,8 @@ struct pa_plan_s {
     std::vector<void *> ws_allocs;
     ~pa_plan_s() {
         for (auto &st : stage) {
-            for (cudaEvent_t e : st.ready) cudaEventDestroy(e);
+            for (cudaEvent_t e : st.ready)
+                if (e) cudaEventDestroy(e);
             if (st.free_ev) cudaEventDestroy(st.free_ev);
             if (st.hstatus) cudaFreeHost(st.hstatus);
         }
@@ -604,18 +605,35 @@ int pa_hash_host_async(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed,
     auto &st = pl->stage[pl->next_stage];
     pl->next_stage ^= 1;
     if (!st.dkey) {
-        void *d = nullptr;
-        if (cudaMalloc(&d, (kw + sw + ow + 1) * 8) != cudaSuccess) return PA_ERR_NOMEM;
-        pl->ws_allocs.push_back(d);
-        st.dkey = (u64 *)d;
-        st.dseed = st.dkey + kw;
+        // each resource once; the slot counts as set up (dkey) only when all exist,
+        // so a call after a failed setup completes it instead of using a partial slot
+        if (!st.dseed) {
+            void *d = nullptr;
+            if (cudaMalloc(&d, (kw + sw + ow + 1) * 8) != cudaSuccess) {
+                cudaGetLastError();
+                return PA_ERR_NOMEM;
+            }
+            pl->ws_allocs.push_back(d);
+            st.dseed = (u64 *)d + kw;
+        }
+        if (!st.hstatus && cudaMallocHost(&st.hstatus, sizeof(int)) != cudaSuccess) {
+            st.hstatus = nullptr;
+            cudaGetLastError();
+            return PA_ERR_NOMEM;
+        }
+        st.ready.resize(ng + 1, nullptr);
+        for (auto &ev : st.ready)
+            if (!ev && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+                ev = nullptr;
+                return PA_ERR_CUDA;
+            }
+        if (!st.free_ev && cudaEventCreateWithFlags(&st.free_ev, cudaEventDisableTiming) != cudaSuccess) {
+            st.free_ev = nullptr;
+            return PA_ERR_CUDA;
+        }
         st.dout = st.dseed + sw;
         st.dstatus = (int *)(st.dout + ow);
-        if (cudaMallocHost(&st.hstatus, sizeof(int))) return PA_ERR_NOMEM;
-        st.ready.resize(ng + 1, nullptr);
-        for (auto &e : st.ready)
-            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming)) return PA_ERR_CUDA;
-        if (cudaEventCreateWithFlags(&st.free_ev, cudaEventDisableTiming)) return PA_ERR_CUDA;
+        st.dkey = st.dseed - kw;
     }
     int e = 0;
     // the slot's previous inputs must have been consumed before they are overwritten
