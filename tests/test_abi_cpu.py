@@ -116,3 +116,15 @@ def test_oracle_and_library_share_no_code():
                 with open(os.path.join(dirpath, name)) as f:
                     text = f.read()
                 assert not re.search(r"\bimport\s+oracle\b|\bfrom\s+oracle\b|pa_oracle|liboracle", text), name
+
+
+@pytest.mark.parametrize("n,r,gamma", [(0, 10, 0), (100, 0, 0), (1000, 10, 100), (1000, 200, 61), (1000, 10, 1),
+                                       (10**12, 10**11, 0)])
+def test_plan_rejects_invalid_arguments(n, r, gamma):
+    """n = 0, r = 0, a gamma outside the Mersenne exponent list, r >= gamma, and
+    r + margin above the largest listed exponent are PA_ERR_INVALID for both
+    backends (the plan rule runs on the host)."""
+    for backend in (_lib.BACKEND_AUTO, _lib.BACKEND_GOLDILOCKS, _lib.BACKEND_P3):
+        with pytest.raises(_lib.PAError) as e:
+            _lib.plan_estimate_bytes(n, r, gamma=gamma, backend=backend)
+        assert e.value.code == _lib.PA_ERR_INVALID
