@@ -157,7 +157,8 @@ int pa_hash_prepared(pa_plan_t *plan, const uint64_t *key, uint64_t *out, int *s
  * the process exits.  Blocks whose workspace does not fit (about n <= 1e7 key
  * bits at r = 0.1 n) return PA_ERR_UNSUPPORTED.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) and should be
- * made before any stream capture on that device.  Every call shares the array:
+ * made before any stream capture on that device; the lookup is repeated when
+ * the device's context has been re-created (after cudaDeviceReset).  Every call shares the array:
  * calls whose work overlaps on the GPU race, so order them (one stream, or
  * events).  key, seed, out and status are device pointers as for pa_hash.
  * Asynchronous.  This entry point has no counterpart in the paper. */

@@ -148,7 +148,8 @@ struct pa_plan_s {
         int *dstatus = nullptr;
         int *hstatus = nullptr;  // pinned
         std::vector<cudaEvent_t> ready;
-        cudaEvent_t free_ev = nullptr;
+        cudaEvent_t free_ev = nullptr;  // the slot's key and seed have been consumed
+        cudaEvent_t out_ev = nullptr;   // the slot's output and status have been copied out
         bool used = false;
     } stage[2];
     int next_stage = 0;
@@ -159,6 +160,7 @@ struct pa_plan_s {
             for (cudaEvent_t e : st.ready)
                 if (e) cudaEventDestroy(e);
             if (st.free_ev) cudaEventDestroy(st.free_ev);
+            if (st.out_ev) cudaEventDestroy(st.out_ev);
             if (st.hstatus) cudaFreeHost(st.hstatus);
         }
         if (copy_stream) cudaStreamDestroy(copy_stream);
@@ -631,13 +633,20 @@ int pa_hash_host_async(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed,
             st.free_ev = nullptr;
             return PA_ERR_CUDA;
         }
+        if (!st.out_ev && cudaEventCreateWithFlags(&st.out_ev, cudaEventDisableTiming) != cudaSuccess) {
+            st.out_ev = nullptr;
+            return PA_ERR_CUDA;
+        }
         st.dout = st.dseed + sw;
         st.dstatus = (int *)(st.dout + ow);
         st.dkey = st.dseed - kw;
     }
     int e = 0;
-    // the slot's previous inputs must have been consumed before they are overwritten
+    // the slot's previous inputs must have been consumed before they are
+    // overwritten, and its previous output and status copied out before the
+    // kernels (on `stream`, possibly another stream than last time) rewrite them
     if (st.used) e = cudaStreamWaitEvent(pl->copy_stream, st.free_ev, 0);
+    if (st.used && !e) e = cudaStreamWaitEvent(s, st.out_ev, 0);
     auto copy_words = [&](u64 *dst, const uint64_t *src, uint64_t w0, uint64_t w1) {
         if (w1 > w0 && !e)
             e = cudaMemcpyAsync(dst + w0, src + w0, (w1 - w0) * 8, cudaMemcpyHostToDevice, pl->copy_stream);
@@ -660,6 +669,7 @@ int pa_hash_host_async(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed,
         if (!e) e = cudaEventRecord(st.free_ev, s);
         if (!e) e = cudaMemcpyAsync(out, st.dout, ow * 8, cudaMemcpyDeviceToHost, s);
         if (!e) e = cudaMemcpyAsync(status ? status : st.hstatus, st.dstatus, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaEventRecord(st.out_ev, s);
         if (e) return PA_ERR_CUDA;
         st.used = true;
         return PA_OK;
@@ -690,6 +700,7 @@ int pa_hash_host_async(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed,
     if (!e) e = cudaEventRecord(st.free_ev, s);
     if (!e) e = cudaMemcpyAsync(out, st.dout, ow * 8, cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaMemcpyAsync(status ? status : st.hstatus, st.dstatus, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaEventRecord(st.out_ev, s);
     if (e) return PA_ERR_CUDA;
     st.used = true;
     return PA_OK;

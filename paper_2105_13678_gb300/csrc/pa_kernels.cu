@@ -12,6 +12,9 @@
 //   k_extract   z = bits [gamma - r, gamma) of b*y + c              (Eq. 4)
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <atomic>
+
 #include "gl_device.cuh"
 #include "pa_internal.h"
 
@@ -796,32 +799,108 @@ __global__ void __launch_bounds__(PA_CARRY_T) k_carry_c(CarryDev cd, u64 *__rest
     if (threadIdx.x == 0 && !all) *cd.allones = 0;
 }
 
-// Small transforms: one thread resolves the digits sequentially (around the
-// ring, or linearly dropping the top carry).
-__global__ void k_carry_seq(CarryDev cd, u64 ndigits, u64 *__restrict__ z, u64 *__restrict__ y) {
+// Small digit vectors: one CTA.  Thread t < runs owns the digits
+// [t D, (t + 1) D) (the top thread also the rest up to ndigits); the host
+// chooses D so that every run spans >= 64 bits.  Pass 1: each run's carry-out
+// H_t with zero carry-in.  Pass 2: run t with carry-in H_{t-1} (H of the top
+// run around the ring, 0 when linear) leaves a 1-bit carry at most (H < 2^64
+// <= 2^width), summarised as generate / propagate; a two-level ballot scan
+// gives every run its 1-bit carry-in (end-around for the ring).  Pass 3: each
+// run writes its bits with carry-in H_{t-1} + c_t.  runs == 1 (values of a
+// few dozen bits): thread 0 folds the carry around the ring until it is 0.
+__device__ __forceinline__ void run_bits(const CarryDev &cd, const u64 *__restrict__ z, u64 j0, u64 j1,
+                                         unsigned __int128 cin, bool write, u64 *__restrict__ y, u64 *cout,
+                                         bool *ones) {
+    unsigned __int128 acc = cin;
+    bool all = true;
+    u64 s = cd_start(cd, j0);
+    u64 wi = s >> 6, wv = 0;
+    u32 bo = (u32)(s & 63);
+    for (u64 j = j0; j < j1; j++) {
+        const u64 s1 = cd_start(cd, j + 1);
+        const u32 bd = (u32)(s1 - s);
+        s = s1;
+        acc += __ldg(z + j);
+        if (bd == 0) continue;
+        const u64 mask = bd >= 64 ? ~0ULL : (1ULL << bd) - 1;
+        const u64 bits = (u64)acc & mask;
+        all = all && (bits == mask);
+        acc >>= bd;
+        if (write) {
+            wv |= bits << bo;
+            const u32 nb = bo + bd;
+            if (nb >= 64) {
+                atomicOr(y + wi, wv);
+                wi++;
+                wv = (nb > 64) ? (bits >> (64 - bo)) : 0;
+                bo = nb - 64;
+            } else {
+                bo = nb;
+            }
+        }
+    }
+    if (write && bo) atomicOr(y + wi, wv);
+    *cout = (u64)acc;
+    *ones = all;
+}
+
+__global__ void __launch_bounds__(1024) k_carry_one(CarryDev cd, u64 ndigits, u64 D, u32 runs, const u64 *__restrict__ z,
+                                                    u64 *__restrict__ y) {
     pdl_wait();
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    unsigned __int128 c = 0;
-    for (int pass = 0; pass < 8; pass++) {
-        for (u64 j = 0; j < ndigits; j++) {
-            const u32 b = digit_bits(cd, j);
-            const unsigned __int128 v = (unsigned __int128)z[j] + c;
-            z[j] = (u64)v & ((1ULL << b) - 1);
-            c = v >> b;
+    __shared__ u64 Hs[1024];
+    __shared__ unsigned wG[32], wP[32], wcin[32];
+    const u32 t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const bool act = t < runs;
+    const u64 j0 = act ? (u64)t * D : 0, j1 = act ? (t + 1 == runs ? ndigits : j0 + D) : 0;
+    if (runs == 1) {
+        if (t != 0) return;
+        // the ring value is low(V + c) for the fixed point c = carry-out(V + c)
+        // (then V = low + c (2^G - 1)); c grows monotonically from 0 and each
+        // step shrinks the remaining difference by 2^width, so it settles fast
+        u64 c = 0, h = 0;
+        bool ones = true;
+        for (int pass = 0; pass < 80 && !cd.linear; pass++) {
+            run_bits(cd, z, 0, ndigits, c, false, y, &h, &ones);
+            if (h == c) break;
+            c = h;
         }
-        if (c == 0 || cd.linear) break;
+        run_bits(cd, z, 0, ndigits, c, true, y, &h, &ones);
+        *cd.allones = ones ? 1 : 0;
+        return;
     }
+    u64 H = 0;
     bool ones = true;
-    for (u64 j = 0; j < ndigits; j++) {
-        const u32 b = digit_bits(cd, j);
-        const u64 s = cd_start(cd, j);
-        ones = ones && z[j] == ((1ULL << b) - 1);
-        if (b) {
-            y[s >> 6] |= z[j] << (s & 63);
-            if ((s & 63) + b > 64) y[(s >> 6) + 1] |= z[j] >> (64 - (s & 63));
-        }
+    if (act) run_bits(cd, z, j0, j1, 0, false, y, &H, &ones);
+    Hs[t] = H;
+    __syncthreads();
+    const u64 Hin = !act ? 0 : (t ? Hs[t - 1] : (cd.linear ? 0 : Hs[runs - 1]));
+    u64 out = 0;
+    bool g = false, p = true;
+    if (act) {
+        run_bits(cd, z, j0, j1, Hin, false, y, &out, &ones);
+        g = out != H;  // out == H_t + (carry out of adding H_{t-1})
+        p = !g && ones;
     }
-    *cd.allones = ones ? 1 : 0;
+    const unsigned gm = __ballot_sync(0xFFFFFFFFu, g), pm = __ballot_sync(0xFFFFFFFFu, p);
+    if (lane == 0) {
+        wG[warp] = (unsigned)((((u64)(gm | pm)) + gm) >> 32);
+        wP[warp] = (pm == 0xFFFFFFFFu);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned g2 = __ballot_sync(0xFFFFFFFFu, wG[lane]), p2 = __ballot_sync(0xFFFFFFFFu, wP[lane]);
+        const u64 a = g2 | p2;
+        const unsigned ewrap = cd.linear ? 0u : (unsigned)((a + g2) >> 32);
+        const u64 sum = a + g2 + ewrap;
+        wcin[lane] = (unsigned)(((sum ^ a ^ g2) >> lane) & 1);
+    }
+    __syncthreads();
+    const u64 a = gm | pm, sum = a + gm + wcin[warp];
+    const unsigned c = (unsigned)(((sum ^ a ^ gm) >> lane) & 1);
+    bool fin = true;
+    if (act) run_bits(cd, z, j0, j1, (unsigned __int128)Hin + c, true, y, &out, &fin);
+    const int all = __syncthreads_and(fin ? 1 : 0);
+    if (t == 0) *cd.allones = all;
 }
 
 // -------------------------------------------------------------- extract --
@@ -903,8 +982,12 @@ static size_t row_smem(const Xform &X) { return (size_t)2 * pidx_host(X.C) * siz
 #define PA_FOR_ROW_SHAPES16(F) F(0) F(13)
 
 int prepare_kernels() {
-    static bool done = false;
-    if (done) return 0;
+    // kernel attributes are per device: set them once on each device used
+    static std::atomic<unsigned long long> done_mask{0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return (int)cudaErrorInvalidDevice;
+    const unsigned long long bit = dev < 64 ? 1ULL << dev : 0;  // devices >= 64: set every time
+    if (done_mask.load() & bit) return 0;
     cudaError_t e;
     const int big = 200 * 1024;
 #define PA_ATTR_COL(LLV, TCV)                                                                                   \
@@ -929,7 +1012,7 @@ int prepare_kernels() {
 #undef PA_ATTR_ROW8
 #undef PA_ATTR_ROW16
 #undef PA_ATTR_ROW
-    done = true;
+    done_mask.fetch_or(bit);
     return 0;
 }
 
@@ -1013,6 +1096,26 @@ int launch_inv_col(const Xform &X, const u64 *S, u64 *Z, const u64 *add_src, u64
     return (int)cudaErrorInvalidValue;
 }
 
+// Runs of the one-CTA carry: D digits per run (the top run takes the rest),
+// every run >= 64 bits wide so that a carry-in below 2^64 leaves a 1-bit
+// carry; a single run when the value is too short for two.
+void carry_runs(const CarryDev &cd, u64 ndigits, u64 *D_out, u32 *runs_out) {
+    auto start = [&](u64 j) -> u64 {
+        if (cd.ub) {
+            const u64 s = j * cd.ub;
+            return s < cd.G ? s : cd.G;
+        }
+        return (cd.G * j + cd.N - 1) >> cd.logN;
+    };
+    // narrowest run of D interior digits: D ub bits, or floor(D G / N) - 1
+    u64 D = cd.ub ? (64 + cd.ub - 1) / cd.ub : (65 * cd.N + cd.G - 1) / cd.G + 1;
+    D = std::max<u64>(D, (ndigits + 1023) / 1024);
+    u64 runs = ndigits ? (ndigits + D - 1) / D : 1;
+    while (runs > 1 && start(ndigits) - start((runs - 1) * D) < 64) runs--;
+    *D_out = D;
+    *runs_out = (u32)std::max<u64>(runs, 1);
+}
+
 int launch_carry_chunks(const CarryDev &cd, u64 ndigits, bool wide_chunks, u32 stage, u64 *z, u64 *out_bits,
                         u64 out_words, void *stream, bool zeroed, bool pdl) {
     cudaStream_t s = (cudaStream_t)stream;
@@ -1024,10 +1127,14 @@ int launch_carry_chunks(const CarryDev &cd, u64 ndigits, bool wide_chunks, u32 s
     // previous chunk's carry-out leaves a 1-bit carry
     const bool parallel = cd.nchunks >= PA_CARRY_T && wide_chunks;
     if (!parallel) {
+        u64 D = 0;
+        u32 runs = 0;
+        carry_runs(cd, ndigits, &D, &runs);
         if (pdl)
-            TRACED("carry_seq", stage, stream, (launch_pdl(k_carry_seq, dim3(1), dim3(32), 0, s, cd, ndigits, z, out_bits)));
+            TRACED("carry_one", stage, stream,
+                   (launch_pdl(k_carry_one, dim3(1), dim3(1024), 0, s, cd, ndigits, D, runs, (const u64 *)z, out_bits)));
         else
-            TRACED("carry_seq", stage, stream, (k_carry_seq<<<1, 32, 0, s>>>(cd, ndigits, z, out_bits)));
+            TRACED("carry_one", stage, stream, (k_carry_one<<<1, 1024, 0, s>>>(cd, ndigits, D, runs, z, out_bits)));
         return (int)cudaGetLastError();
     }
     const u32 nctas = (u32)((cd.nchunks + PA_CARRY_T - 1) / PA_CARRY_T);

@@ -12,9 +12,10 @@
 // it until the process exits.  The caller passes only the inputs and outputs.
 //
 // Host code never dereferences the array's name (on the host it is only a
-// stand-in for the symbol); the device address is obtained once per device
-// with cudaGetSymbolAddress, on the first call made while that device is
-// current, and cached.  Every call shares the array and leaves its contents
+// stand-in for the symbol); the device address is obtained with
+// cudaGetSymbolAddress on the first call made while that device is current
+// (and again after the device's context has been re-created, e.g. by
+// cudaDeviceReset), and cached.  Every call shares the array and leaves its contents
 // behind; the parts that must start at zero are cleared on the stream by each
 // call.  Calls whose work overlaps on the GPU (different streams without
 // ordering, or several host threads) race on the shared array.
@@ -41,16 +42,45 @@ namespace {
 
 constexpr int kMaxDevices = 128;
 std::mutex g_mu;
-unsigned long long *g_scratch_dev[kMaxDevices];  // device address of the array, per device
+// Per device: the array's device address and the context it was looked up
+// in.  A device reset (cudaDeviceReset) or a re-created primary context loads
+// a new copy of the module, so the address is looked up again whenever the
+// current context differs from the one recorded.
+unsigned long long *g_scratch_dev[kMaxDevices];
+void *g_scratch_ctx[kMaxDevices];
+
+typedef int (*CtxGetCurrentFn)(void **);
+
+void *current_context() {
+    static CtxGetCurrentFn fn = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (CtxGetCurrentFn)f;
+        cudaGetLastError();
+        looked_up = true;
+    }
+    void *ctx = nullptr;
+    if (fn && fn(&ctx) != 0) ctx = nullptr;
+    return ctx;
+}
 
 int scratch_address(unsigned long long **out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PA_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_dev[dev]) {
+    void *ctx = current_context();  // null until the runtime has bound a context to this thread
+    if (!g_scratch_dev[dev] || !ctx || ctx != g_scratch_ctx[dev]) {
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_pa_noalloc_scratch) != cudaSuccess || !p) return PA_ERR_CUDA;
+        if (cudaGetSymbolAddress(&p, g_pa_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return PA_ERR_CUDA;
+        }
         g_scratch_dev[dev] = (unsigned long long *)p;
+        g_scratch_ctx[dev] = current_context();
     }
     *out = g_scratch_dev[dev];
     return PA_OK;

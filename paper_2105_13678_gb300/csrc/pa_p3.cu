@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <vector>
 
@@ -858,8 +859,12 @@ static cudaError_t p3_row_attrs(int big) {
 }
 
 int p3_prepare_kernels() {
-    static bool done = false;
-    if (done) return 0;
+    // kernel attributes are per device: set them once on each device used
+    static std::atomic<unsigned long long> done_mask{0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return (int)cudaErrorInvalidDevice;
+    const unsigned long long bit = dev < 64 ? 1ULL << dev : 0;  // devices >= 64: set every time
+    if (done_mask.load() & bit) return 0;
     const int big = 200 * 1024;
     cudaError_t e;
 #define P3_ATTR(f) \
@@ -872,7 +877,7 @@ int p3_prepare_kernels() {
     P3_ATTR((k3_inv_col<10, 8>))
 #undef P3_ATTR
     if ((e = p3_row_attrs<0>(big)) || (e = p3_row_attrs<1>(big)) || (e = p3_row_attrs<2>(big))) return e;
-    done = true;
+    done_mask.fetch_or(bit);
     return 0;
 }
 

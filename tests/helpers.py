@@ -76,3 +76,46 @@ def oracle_hash_parallel(key, n, seed, r, gamma, k, workers: int | None = None):
     yw = oracle.int_to_words(y, oracle.words(gamma))
     out = oracle.mh(yw, seed, gamma, k, r)
     return oracle.ORA_OK, out, yw
+
+
+def oracle_hash_many(blocks, workers: int | None = None):
+    """Algorithm 1 by the oracle for many blocks at once.
+
+    ``blocks`` is a list of (key, n, seed, r, gamma, k).  Every block's k
+    segment products (Eq. 2, one per segment) go to one thread pool, then
+    every block's Eq. 4 product; the oracle's C code releases the GIL, so the
+    host's cores all work.  Returns [(status, out words)] in input order."""
+    workers = workers or (os.cpu_count() or 1)
+    p_of = [(1 << b[4]) - 1 for b in blocks]
+
+    def seg(job):
+        bi, i = job
+        key, n, seed, r, gamma, k = blocks[bi]
+        nn = min(n, (i + 1) * gamma) - i * gamma
+        sub_key = _slice_words(key, n, i * gamma, i * gamma + nn)
+        sub_seed = np.zeros(oracle.words(3 * gamma) + 1, dtype=np.uint64)
+        a = _slice_words(seed, (k + 2) * gamma, i * gamma, (i + 1) * gamma)
+        sub_seed[:a.size] = a[:sub_seed.size]
+        rc, y = oracle.mmh(sub_key, nn, sub_seed, gamma, 1)
+        return bi, rc, oracle.words_to_int(y)
+
+    jobs = [(bi, i) for bi, b in enumerate(blocks) for i in range(b[5])]
+    # largest products first so that the pool finishes together
+    jobs.sort(key=lambda j: -blocks[j[0]][4])
+    acc = [0] * len(blocks)
+    reload = [False] * len(blocks)
+    with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
+        for bi, rc, v in ex.map(seg, jobs):
+            reload[bi] = reload[bi] or rc == oracle.ORA_RELOAD
+            acc[bi] += v
+
+        def fin(bi):
+            key, n, seed, r, gamma, k = blocks[bi]
+            if reload[bi]:
+                return oracle.ORA_RELOAD, np.zeros(oracle.words(r), dtype=np.uint64)
+            yw = oracle.int_to_words(acc[bi] % p_of[bi], oracle.words(gamma))
+            return oracle.ORA_OK, oracle.mh(yw, seed, gamma, k, r)
+
+        order = sorted(range(len(blocks)), key=lambda b: -blocks[b][4])
+        res = dict(zip(order, ex.map(fin, order)))
+    return [res[i] for i in range(len(blocks))]

@@ -10,7 +10,7 @@ import pytest
 import oracle
 from paper_2105_13678_gb300 import synthetic
 
-from helpers import dev, gpu_hash, host, oracle_hash_parallel
+from helpers import dev, gpu_hash, host, oracle_hash_many, oracle_hash_parallel
 
 pytestmark = pytest.mark.gpu
 
@@ -72,19 +72,19 @@ def test_batch_replays_current_buffer_contents():
 
 def test_batch_config4_64_blocks():
     """64 blocks, n log-uniform in [2^20, 2^27], r/n in [0.05, 0.5] (seed 7):
-    the graph batch equals each block hashed alone; the 20 smallest also equal
-    the oracle."""
+    every block of the graph batch equals the oracle, and each block hashed
+    alone gives the same bits."""
     shapes = synthetic.batch_shapes(7)
     blocks = _blocks(shapes)
     st = _run_batch(blocks, reps=2)
     assert (st == 0).all()
     batch_out = [host(b["do"]).copy() for b in blocks]
+    ref = oracle_hash_many([(b["key"], b["n"], b["seed"], b["r"], b["plan"].gamma, b["plan"].k) for b in blocks])
+    for i, (b, bo, (rc, out)) in enumerate(zip(blocks, batch_out, ref)):
+        assert rc == 0 and np.array_equal(bo, out), f"block {i}: n={b['n']} r={b['r']} differs from the oracle"
     for b, bo in zip(blocks, batch_out):
         s, out, _, _ = gpu_hash(b["plan"], b["key"], b["seed"])
         assert s == 0 and np.array_equal(out, bo)
-    for b in sorted(blocks, key=lambda b: b["n"])[:20]:
-        rc, out, _ = oracle_hash_parallel(b["key"], b["n"], b["seed"], b["r"], b["plan"].gamma, b["plan"].k)
-        assert rc == 0 and np.array_equal(host(b["do"]), out)
     for b in blocks:
         b["plan"].close()
 
@@ -119,6 +119,33 @@ def test_serve_alone_equals_in_mix():
         g, k = oracle.plan(j["n"], j["r"])
         rc, out, _ = oracle_hash_parallel(j["key"], j["n"], j["seed"], j["r"], g, k)
         assert np.array_equal(out, host(j["do"]))
+
+
+def test_serve_paper_scale_jobs_in_mix_match_oracle():
+    """Served mix of the paper's sizes in flight together: 2.6e8-, 1e8- and
+    1e7-bit jobs (r = 0.1 n) submitted at once onto 6 slots under a 16 GB
+    budget; every result, taken from the mix, equals the oracle."""
+    import torch
+    from paper_2105_13678_gb300 import _lib
+    sizes = [260_000_000, 10_000_000, 100_000_000, 10_000_000, 260_000_000, 100_000_000,
+             10_000_000, 100_000_000, 10_000_000, 10_000_000]
+    jobs = []
+    for i, n in enumerate(sizes):
+        r = int(math.ceil(0.1 * n))
+        g, k = oracle.plan(n, r)
+        key, seed = synthetic.block_inputs((8 << 32) + 7000 + i, n, (k + 2) * g)
+        jobs.append(dict(n=n, r=r, g=g, k=k, key=key, seed=seed, dk=dev(key), ds=dev(seed),
+                         do=torch.full(((r + 63) // 64,), -1, dtype=torch.int64, device="cuda")))
+    srv = _lib.Server(16 << 30, slots=6)
+    tickets = [srv.submit(j["n"], j["r"], j["dk"].data_ptr(), j["ds"].data_ptr(), j["do"].data_ptr()) for j in jobs]
+    sts = [srv.wait(t, 300.0) for t in tickets]
+    stats = srv.stats()
+    srv.close()
+    assert all(s == 0 for s in sts)
+    assert stats["completed"] == len(jobs) and stats["peak_budget_bytes"] <= 16 << 30
+    ref = oracle_hash_many([(j["key"], j["n"], j["seed"], j["r"], j["g"], j["k"]) for j in jobs])
+    for i, (j, (rc, out)) in enumerate(zip(jobs, ref)):
+        assert rc == 0 and np.array_equal(out, host(j["do"])), f"job {i} (n={j['n']}) differs from the oracle"
 
 
 def test_serve_budget_admission():

@@ -9,6 +9,7 @@ file is collected last so that a failure here does not hide the other tests."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2105_13678_gb300 import synthetic
 
 pytestmark = pytest.mark.gpu
@@ -59,3 +60,28 @@ def test_noalloc_rejects_blocks_beyond_the_static_scratch():
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     rc = _noalloc(n, r, dummy, dummy, dummy, st, torch.cuda.current_stream().cuda_stream)
     assert rc == _lib.PA_ERR_UNSUPPORTED
+
+
+def test_noalloc_matches_oracle_and_reports_reload():
+    """The same entry point against the oracle directly, at a ragged size, and
+    on a key whose second slice is all ones (Algorithm 1's reload rule: status
+    1 and a zero-filled output), on two calls in a row each."""
+    import torch
+    from paper_2105_13678_gb300 import _lib
+    stream = torch.cuda.current_stream().cuda_stream
+    n, r = 1_234_567, 99_999
+    g, k = oracle.plan(n, r)
+    key, seed = synthetic.block_inputs(31, n, (k + 2) * g)
+    reload_key = oracle.int_to_words(oracle.words_to_int(key) | (((1 << g) - 1) << g), key.size)
+    for kw, want_rc in ((key, oracle.ORA_OK), (reload_key, oracle.ORA_RELOAD)):
+        rc, ref, _ = oracle.pa_hash(kw, n, seed, r, g, k)
+        assert rc == want_rc
+        dk = torch.from_numpy(kw.view(np.int64)).cuda()
+        ds = torch.from_numpy(seed.view(np.int64)).cuda()
+        for call in range(2):
+            out = torch.full((oracle.words(r),), -1, dtype=torch.int64, device="cuda")
+            st = torch.full((1,), -9, dtype=torch.int32, device="cuda")
+            assert _noalloc(n, r, dk, ds, out, st, stream) == _lib.PA_OK
+            torch.cuda.synchronize()
+            assert int(st.item()) == rc, f"call {call}: status {int(st.item())}, oracle {rc}"
+            assert np.array_equal(out.cpu().numpy().view(np.uint64), ref), f"call {call}: output differs from the oracle"
