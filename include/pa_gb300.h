@@ -183,7 +183,10 @@ int pa_batch_cache_clear(void);
  * Jobs are admitted while their device bytes (plan workspace) fit in the HBM
  * budget; admitted jobs run concurrently on `slots` streams; others wait in a
  * FIFO.  key/seed/out are DEVICE pointers owned by the caller and must stay
- * valid until the job completes. */
+ * valid until the job completes.  The server's plans use stream-ordered
+ * device memory (cudaMallocAsync from the device's default pool), so building
+ * and dropping them does not synchronise the device.  Latency is measured
+ * from submit to a host function that runs when the job's work is done. */
 typedef struct pa_server_s pa_server_t;
 typedef struct pa_serve_config {
     uint64_t hbm_budget_bytes; /* admission budget for plan workspaces         */
@@ -205,7 +208,15 @@ int pa_serve_submit(pa_server_t *srv, uint64_t n_bits, uint64_t r_bits, const ui
 int pa_serve_poll(pa_server_t *srv, uint64_t ticket, int *status);  /* PA_OK if done, PA_ERR_BUSY if not */
 int pa_serve_wait(pa_server_t *srv, uint64_t ticket, uint64_t timeout_ns, int *status);
 int pa_serve_stats_get(pa_server_t *srv, pa_serve_stats *stats);
-int pa_serve_destroy(pa_server_t *srv); /* cancels queued jobs, waits for running ones */
+/* Start the statistics afresh (counters, latencies, busy time; the peak
+ * budget restarts at what is held now).  Jobs in flight are counted when they
+ * complete. */
+int pa_serve_stats_reset(pa_server_t *srv);
+/* Stop the server: later submits return PA_ERR_CANCELLED, queued jobs finish
+ * with status PA_ERR_CANCELLED, running jobs complete; returns when none is
+ * running.  poll, wait and stats keep working until pa_serve_destroy. */
+int pa_serve_shutdown(pa_server_t *srv);
+int pa_serve_destroy(pa_server_t *srv); /* pa_serve_shutdown, then frees the server */
 
 /* ---- tracing: per-kernel device time ---------------------------------------
  * pa_trace_enable(1) clears earlier records and brackets every later kernel
@@ -245,6 +256,13 @@ int pa_plan_geometry(const pa_plan_t *plan, int stage, uint32_t *log_r, uint32_t
  * mod q, canonical; a, b, out (4n words) are device arrays, any 64-bit inputs.
  * Asynchronous. */
 int pa_selftest_field(const uint64_t *a, const uint64_t *b, uint64_t *out, uint64_t n, void *stream);
+
+/* Failure injection for tests of the error paths (host side only; no device
+ * work fails): of the library's next device and pinned host allocations,
+ * `skip` succeed and the following `count` fail as if the memory were
+ * exhausted (the call returns PA_ERR_NOMEM).  pa_debug_fail_allocs(0, 0)
+ * switches it off.  Not thread-safe; for tests. */
+int pa_debug_fail_allocs(uint32_t skip, uint32_t count);
 
 /* Human-readable name of a return code (static string). */
 const char *pa_status_string(int code);

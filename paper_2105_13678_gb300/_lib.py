@@ -80,10 +80,13 @@ SIGNATURES = {
     "pa_serve_poll": (ctypes.c_int, [_vp, _u64, ctypes.POINTER(ctypes.c_int)]),
     "pa_serve_wait": (ctypes.c_int, [_vp, _u64, _u64, ctypes.POINTER(ctypes.c_int)]),
     "pa_serve_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(pa_serve_stats)]),
+    "pa_serve_stats_reset": (ctypes.c_int, [_vp]),
+    "pa_serve_shutdown": (ctypes.c_int, [_vp]),
     "pa_serve_destroy": (ctypes.c_int, [_vp]),
     "pa_trace_enable": (ctypes.c_int, [ctypes.c_int]),
     "pa_trace_collect": (ctypes.c_int, [ctypes.POINTER(pa_trace_entry), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "pa_trace_select": (ctypes.c_int, [ctypes.c_char_p]),
+    "pa_debug_fail_allocs": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32]),
     "pa_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pa_version": (ctypes.c_char_p, []),
     "pa_plan_estimate_bytes": (ctypes.c_int, [_u64, _u64, ctypes.POINTER(pa_params), ctypes.POINTER(_u64)]),
@@ -293,6 +296,14 @@ class Server:
         s = pa_serve_stats()
         check(lib().pa_serve_stats_get(self.handle, ctypes.byref(s)), "pa_serve_stats_get")
         return {name: getattr(s, name) for name, _ in pa_serve_stats._fields_}
+
+    def stats_reset(self):
+        check(lib().pa_serve_stats_reset(self.handle), "pa_serve_stats_reset")
+
+    def shutdown(self):
+        """Cancel the queued jobs and wait for the running ones; poll, wait and
+        stats keep working until close()."""
+        check(lib().pa_serve_shutdown(self.handle), "pa_serve_shutdown")
 
     def close(self):
         if self.handle:

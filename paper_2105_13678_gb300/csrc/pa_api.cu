@@ -12,9 +12,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <map>
-#include <tuple>
 #include <mutex>
+#include <tuple>
 #include <new>
 #include <vector>
 
@@ -68,24 +69,71 @@ static int choose_len(uint64_t G, uint64_t K, uint32_t *logN) {
     return PA_ERR_UNSUPPORTED;
 }
 
-namespace {
+// ------------------------------------------------------- device memory --
 
-struct DevTables {
-    std::vector<void *> allocs;
-    ~DevTables() {
-        for (void *p : allocs) cudaFree(p);
+static std::atomic<long long> g_fail_skip{0}, g_fail_count{0};
+
+bool pa::alloc_fail_injected() {
+    if (g_fail_count.load() <= 0) return false;
+    if (g_fail_skip.load() > 0) {
+        g_fail_skip--;
+        return false;
     }
-    const u64 *upload(const std::vector<u64> &h, int *err) {
-        void *d = nullptr;
-        if (cudaMalloc(&d, h.size() * sizeof(u64)) != cudaSuccess) {
-            *err = PA_ERR_NOMEM;
-            return nullptr;
-        }
-        allocs.push_back(d);
-        if (cudaMemcpy(d, h.data(), h.size() * sizeof(u64), cudaMemcpyHostToDevice) != cudaSuccess) *err = PA_ERR_CUDA;
-        return (const u64 *)d;
+    g_fail_count--;
+    return true;
+}
+
+int DevAlloc::init(bool stream_ordered) {
+    async = stream_ordered;
+    if (!stream && cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) {
+        stream = nullptr;
+        cudaGetLastError();
+        return PA_ERR_CUDA;
     }
-};
+    return PA_OK;
+}
+
+void *DevAlloc::take(size_t b, int *err) {
+    if (*err) return nullptr;
+    void *p = nullptr;
+    const size_t nb = b ? b : 8;
+    // stream-ordered: the allocation is waited for on the private stream, so the
+    // buffer is usable from any stream when take() returns
+    const bool fail = alloc_fail_injected() ||
+                      (async ? (cudaMallocAsync(&p, nb, stream) != cudaSuccess ||
+                                cudaStreamSynchronize(stream) != cudaSuccess)
+                             : cudaMalloc(&p, nb) != cudaSuccess);
+    if (fail) {
+        cudaGetLastError();  // an allocation failure must not read as a later launch's error
+        *err = PA_ERR_NOMEM;
+        return nullptr;
+    }
+    ptrs.push_back(p);
+    bytes += b;
+    return p;
+}
+
+void DevAlloc::upload(void *dst, const void *src, size_t b, int *err) {
+    if (*err || !b) return;
+    if (cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, stream) != cudaSuccess) *err = PA_ERR_CUDA;
+}
+
+int DevAlloc::sync() { return cudaStreamSynchronize(stream) == cudaSuccess ? PA_OK : PA_ERR_CUDA; }
+
+void DevAlloc::release() {
+    for (void *p : ptrs) {
+        if (async)
+            cudaFreeAsync(p, stream);
+        else
+            cudaFree(p);
+    }
+    ptrs.clear();
+    bytes = 0;
+    if (stream) cudaStreamDestroy(stream);  // resources go once its pending frees have run
+    stream = nullptr;
+}
+
+namespace {
 
 // F_q has generator 7; omega_N = 7^((q-1)/N).  2 has order 192, so
 // 2 = rho^u with rho = 7^((q-1)/192); theta_N = 7^(u (q-1)/(192 N)) then
@@ -127,7 +175,7 @@ struct pa_plan_s {
     bool mh_only = false;   // modular-arithmetic hash over the whole key (gamma = n, k = 0)
     P3Plan *p3 = nullptr;   // three-prime backend (pa_p3.cu): owns its own workspace
     Xform mmh, mh;
-    DevTables tables;
+    DevAlloc mem;           // every device buffer and table of the plan
     // workspace
     u64 *Y = nullptr;       // operand spectra (and the un-weighted coefficients)
     u64 *S = nullptr;       // accumulated spectra
@@ -154,7 +202,6 @@ struct pa_plan_s {
     } stage[2];
     int next_stage = 0;
     cudaStream_t copy_stream = nullptr;
-    std::vector<void *> ws_allocs;
     ~pa_plan_s() {
         for (auto &st : stage) {
             for (cudaEvent_t e : st.ready)
@@ -164,18 +211,12 @@ struct pa_plan_s {
             if (st.hstatus) cudaFreeHost(st.hstatus);
         }
         if (copy_stream) cudaStreamDestroy(copy_stream);
-        for (void *p : ws_allocs) cudaFree(p);
         if (p3) p3_plan_destroy(p3);
+        mem.release();
     }
     void *alloc(size_t bytes, int *err) {
-        void *p = nullptr;
-        if (cudaMalloc(&p, bytes ? bytes : 8) != cudaSuccess) {
-            cudaGetLastError();  // an allocation failure must not read as a later launch's error
-            *err = PA_ERR_NOMEM;
-            return nullptr;
-        }
-        ws_allocs.push_back(p);
-        ws_bytes += bytes;
+        void *p = mem.take(bytes, err);
+        if (p) ws_bytes += bytes;
         return p;
     }
 };
@@ -198,7 +239,7 @@ static bool geometry_ok(uint32_t l, u32 logR, u32 tc) {
 }
 
 static int build_xform(pa_plan_t *pl, Xform &X, uint64_t G, uint64_t K, u32 logR_sel = ~0u, u32 tc_sel = 0,
-                       DevTables *sink = nullptr) {
+                       DevAlloc *sink = nullptr) {
     uint32_t l;
     int rc = choose_len(G, K, &l);
     if (rc) return rc;
@@ -209,7 +250,7 @@ static int build_xform(pa_plan_t *pl, Xform &X, uint64_t G, uint64_t K, u32 logR
         logR = logR_sel;
         tc = tc_sel;
     }
-    DevTables &tabs = sink ? *sink : pl->tables;
+    DevAlloc &tabs = sink ? *sink : pl->mem;
     X.N = 1ULL << l;
     X.G = G;
     X.K = (u32)K;
@@ -225,7 +266,11 @@ static int build_xform(pa_plan_t *pl, Xform &X, uint64_t G, uint64_t K, u32 logR
     const u64 ninv = gl_inv(X.N % GL_Q);
     const u64 wR = gl_pow(w, X.C), wC = gl_pow(w, X.R);
     int err = PA_OK;
-    auto up = [&](const std::vector<u64> &v) { return tabs.upload(v, &err); };
+    auto up = [&](const std::vector<u64> &v) -> const u64 * {
+        void *d = tabs.take(v.size() * sizeof(u64), &err);
+        tabs.upload(d, v.data(), v.size() * sizeof(u64), &err);
+        return (const u64 *)d;
+    };
     X.twR = up(powers(wR, X.R));
     X.itwR = up(powers(gl_inv(wR), X.R));
     X.twC = up(powers(wC, X.C));
@@ -252,11 +297,11 @@ static int build_xform(pa_plan_t *pl, Xform &X, uint64_t G, uint64_t K, u32 logR
     }
     if (err) return err;
     {
-        void *d = nullptr;
-        if (cudaMalloc(&d, X.N * sizeof(u64)) != cudaSuccess) return PA_ERR_NOMEM;
-        tabs.allocs.push_back(d);
+        void *d = tabs.take(X.N * sizeof(u64), &err);
+        if (err) return err;
         X.coltw = (const u64 *)d;
-        if (launch_fill_coltw(X, (u64 *)d, nullptr) || cudaDeviceSynchronize() != cudaSuccess) return PA_ERR_CUDA;
+        // on the plan's private stream: building a plan waits for nothing else on the device
+        if (launch_fill_coltw(X, (u64 *)d, tabs.stream) || tabs.sync() != PA_OK) return PA_ERR_CUDA;
     }
     return err;
 }
@@ -289,7 +334,16 @@ static WsSizes ws_sizes(uint32_t gamma, uint64_t k, uint64_t N1, uint64_t N2) {
     z.cstate = nch;
     z.cta = nch / PA_CARRY_T + 1;
     z.flags = (4 + k) * sizeof(int);
-    z.tables = (N1 + N2) * 8;  // full column-pass twiddle tables
+    // tables of both transforms: a bound for every geometry the tuner may pick
+    auto table_words = [](uint64_t N) {
+        uint32_t l = 0;
+        while ((1ULL << l) < N) l++;
+        const uint64_t Rmax = 1ULL << std::min<uint32_t>(l / 2 + 1, PA_MAX_LOGR);
+        const uint64_t Cmax = N >> (std::min<uint32_t>(l / 2, PA_MAX_LOGR) > 0 ? std::min<uint32_t>(l / 2, PA_MAX_LOGR) - 1 : 0);
+        const uint32_t hb = (l + 1) / 2;
+        return 4 * Rmax + 2 * Cmax + 4 * ((1ULL << hb) + (N >> hb)) + N;
+    };
+    z.tables = (table_words(N1) + table_words(N2)) * 8;
     return z;
 }
 
@@ -315,9 +369,10 @@ static int choose_backend(uint32_t gamma, uint64_t k, const pa_params *params, u
     return PA_OK;
 }
 
-extern "C" {
-
-int pa_plan(uint64_t n_bits, uint64_t r_bits, const pa_params *params, pa_plan_t **out) {
+// Step 0 and the plan's device memory; stream_ordered: every allocation and
+// table fill on the plan's private stream with cudaMallocAsync (server plans).
+int pa::plan_create(uint64_t n_bits, uint64_t r_bits, const pa_params *params, bool stream_ordered,
+                    pa_plan_t **out) {
     if (!out || n_bits == 0 || r_bits == 0) return PA_ERR_INVALID;
     *out = nullptr;
     if (params) {
@@ -330,6 +385,10 @@ int pa_plan(uint64_t n_bits, uint64_t r_bits, const pa_params *params, pa_plan_t
     if (prepare_kernels()) return PA_ERR_CUDA;
     pa_plan_t *pl = new (std::nothrow) pa_plan_s();
     if (!pl) return PA_ERR_NOMEM;
+    if ((rc = pl->mem.init(stream_ordered))) {
+        delete pl;
+        return rc;
+    }
     pl->n = n_bits;
     pl->r = r_bits;
     pl->gamma = gamma;
@@ -349,7 +408,7 @@ int pa_plan(uint64_t n_bits, uint64_t r_bits, const pa_params *params, pa_plan_t
         return rc;
     }
     if (backend == PA_BACKEND_P3) {
-        if ((rc = p3_plan_create(n_bits, r_bits, gamma, pl->k, &pl->p3))) {
+        if ((rc = p3_plan_create(n_bits, r_bits, gamma, pl->k, stream_ordered, &pl->p3))) {
             delete pl;
             return rc;
         }
@@ -390,8 +449,15 @@ int pa_plan(uint64_t n_bits, uint64_t r_bits, const pa_params *params, pa_plan_t
         delete pl;
         return rc;
     }
+    pl->ws_bytes = pl->mem.bytes;  // workspace and tables
     *out = pl;
     return PA_OK;
+}
+
+extern "C" {
+
+int pa_plan(uint64_t n_bits, uint64_t r_bits, const pa_params *params, pa_plan_t **out) {
+    return pa::plan_create(n_bits, r_bits, params, false, out);
 }
 
 // Comparison scheme: the modular-arithmetic hash over the whole key (Eq. 4
@@ -405,6 +471,10 @@ int pa_mh_plan(uint64_t n_bits, uint64_t r_bits, pa_plan_t **out) {
     if (prepare_kernels()) return PA_ERR_CUDA;
     pa_plan_t *pl = new (std::nothrow) pa_plan_s();
     if (!pl) return PA_ERR_NOMEM;
+    if ((rc = pl->mem.init(false))) {
+        delete pl;
+        return rc;
+    }
     pl->mh_only = true;
     pl->n = n_bits;
     pl->r = r_bits;
@@ -430,6 +500,7 @@ int pa_mh_plan(uint64_t n_bits, uint64_t r_bits, pa_plan_t **out) {
         delete pl;
         return err;
     }
+    pl->ws_bytes = pl->mem.bytes;
     *out = pl;
     return PA_OK;
 }
@@ -462,6 +533,12 @@ int pa_plan_destroy(pa_plan_t *pl) {
 }
 
 }  // extern "C"
+
+void pa::plan_destroy_idle(pa_plan_t *pl) {
+    if (!pl) return;
+    pa_batch_drop_plan(pl);
+    delete pl;
+}
 
 // Eq. 2 (MMH): y = sum_i a_i x_i mod 2^gamma - 1, written to y (canonical after
 // the optional zero fix-up when `canonical` is set).
@@ -610,15 +687,12 @@ int pa_hash_host_async(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed,
         // each resource once; the slot counts as set up (dkey) only when all exist,
         // so a call after a failed setup completes it instead of using a partial slot
         if (!st.dseed) {
-            void *d = nullptr;
-            if (cudaMalloc(&d, (kw + sw + ow + 1) * 8) != cudaSuccess) {
-                cudaGetLastError();
-                return PA_ERR_NOMEM;
-            }
-            pl->ws_allocs.push_back(d);
+            int err = PA_OK;
+            void *d = pl->alloc((kw + sw + ow + 1) * 8, &err);
+            if (err) return err;
             st.dseed = (u64 *)d + kw;
         }
-        if (!st.hstatus && cudaMallocHost(&st.hstatus, sizeof(int)) != cudaSuccess) {
+        if (!st.hstatus && (alloc_fail_injected() || cudaMallocHost(&st.hstatus, sizeof(int)) != cudaSuccess)) {
             st.hstatus = nullptr;
             cudaGetLastError();
             return PA_ERR_NOMEM;
@@ -827,13 +901,15 @@ static int tune_geometry(pa_plan_t *pl, int stage, uint64_t G, uint64_t K, uint3
     default_geometry(l, &dR, &dtc);
     // synthetic operands: a fixed bit pattern as key and seed
     const uint64_t words = std::max<uint64_t>((pl->n + 63) / 64, ((pl->k + 2) * pl->gamma + 63) / 64) + 2;
-    void *src = nullptr;
-    if (cudaMalloc(&src, words * 8) != cudaSuccess) return PA_ERR_NOMEM;
-    cudaStream_t s = nullptr;
+    DevAlloc scratch;
+    int aerr = scratch.init(pl->mem.async);
+    void *src = scratch.take(words * 8, &aerr);
+    if (aerr) return aerr;
+    cudaStream_t s = scratch.stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int rc = PA_OK;
-    if (cudaMemset(src, 0xA5, words * 8) || cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) ||
-        cudaEventCreate(&e0) || cudaEventCreate(&e1) || cudaMemset(pl->flags, 0, pl->flags_bytes))
+    if (cudaMemsetAsync(src, 0xA5, words * 8, s) || cudaEventCreate(&e0) || cudaEventCreate(&e1) ||
+        cudaMemsetAsync(pl->flags, 0, pl->flags_bytes, s))
         rc = PA_ERR_CUDA;
     float best = 1e30f;
     u32 bestR = dR, besttc = dtc;
@@ -842,9 +918,9 @@ static int tune_geometry(pa_plan_t *pl, int stage, uint64_t G, uint64_t K, uint3
         const u32 logR = (u32)((int)dR + dr);
         for (u32 tc : {1u, 2u, 4u, 8u}) {
             if (!geometry_ok(l, logR, tc)) continue;
-            DevTables tmp;
+            DevAlloc tmp;
             Xform X;
-            if (build_xform(pl, X, G, K, logR, tc, &tmp)) continue;
+            if (tmp.init(pl->mem.async) || build_xform(pl, X, G, K, logR, tc, &tmp)) continue;
             X.stage = (u32)stage;
             Operands ops;
             ops.pair0 = 0;
@@ -879,8 +955,8 @@ static int tune_geometry(pa_plan_t *pl, int stage, uint64_t G, uint64_t K, uint3
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    if (s) cudaStreamDestroy(s);
-    cudaFree(src);
+    if (!rc && scratch.sync()) rc = PA_ERR_CUDA;
+    scratch.release();
     if (rc) return rc;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -946,6 +1022,14 @@ int pa_plan_geometry(const pa_plan_t *pl, int stage, uint32_t *log_r, uint32_t *
     *log_r = X.logR;
     *log_c = X.logC;
     *tile_cols = X.tc;
+    return PA_OK;
+}
+
+// Failure injection for tests: of the library's next device (and pinned host)
+// allocations, let `skip` succeed, then fail `count` with PA_ERR_NOMEM.
+int pa_debug_fail_allocs(uint32_t skip, uint32_t count) {
+    g_fail_skip = skip;
+    g_fail_count = count;
     return PA_OK;
 }
 

@@ -16,7 +16,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 struct pa_params;
+struct pa_plan_s;
 
 #if defined(__CUDACC__)
 #define PA_HD __host__ __device__ __forceinline__
@@ -80,6 +83,27 @@ inline u64 gl_pow(u64 b, u64 e) {
 inline u64 gl_inv(u64 a) { return gl_pow(a, GL_Q - 2); }
 
 // ------------------------------------------------------------------ plans --
+
+// Device memory of one plan (pa_api.cu).  Plans made by pa_plan allocate with
+// cudaMalloc; plans made by the server allocate stream-ordered
+// (cudaMallocAsync / cudaFreeAsync on the plan's private stream), so that
+// building or dropping one never waits for other work on the device.  Table
+// uploads and fills run on the private stream and are waited for on it alone.
+struct DevAlloc {
+    cudaStream_t stream = nullptr;  // private, non-blocking
+    bool async = false;
+    std::vector<void *> ptrs;
+    uint64_t bytes = 0;
+    int init(bool stream_ordered);                            // PA_OK or PA_ERR_CUDA
+    void *take(size_t b, int *err);                           // sets *err = PA_ERR_NOMEM on failure
+    void upload(void *dst, const void *src, size_t b, int *err);  // host -> device on `stream`
+    int sync();                                               // wait for `stream`; PA_OK or PA_ERR_CUDA
+    void release();                                           // free every allocation
+    ~DevAlloc() { release(); }
+};
+// Host-side failure injection for tests (pa_debug_fail_allocs): true when the
+// allocation about to be made must fail.
+bool alloc_fail_injected();
 
 // One weighted cyclic transform of length N = R * C over F_q.  All tables are
 // device pointers owned by the plan.
@@ -162,6 +186,13 @@ constexpr u32 PA_COL_T = 256;      // threads per CTA in the column passes
 constexpr u32 PA_MAX_LOGN = 24;    // largest transform the kernels implement
 constexpr u32 PA_MAX_LOGR = 11;    // column length cap (smem tile R x tc)
 
+// Plans (pa_api.cu).  stream_ordered: allocations and table fills on the
+// plan's private stream (cudaMallocAsync), for the server.
+int plan_create(uint64_t n_bits, uint64_t r_bits, const ::pa_params *params, bool stream_ordered,
+                ::pa_plan_s **out);
+// Destroy a plan none of whose work is pending (no device synchronisation).
+void plan_destroy_idle(::pa_plan_s *pl);
+
 // Step-0 parameters (pa_api.cu): gamma, k and log2 of both transform lengths.
 int choose_params(uint64_t n_bits, uint64_t r_bits, const struct pa_params *params, uint32_t *gamma, uint64_t *k,
                   uint32_t *log_mmh, uint32_t *log_mh);
@@ -242,7 +273,7 @@ int p3_launch_fill_ctw(u32 logR, u32 logC, u32 h, const u32 *lo, const u32 *hi, 
 struct P3Plan;
 int p3_feasible(uint32_t gamma, uint64_t k, uint32_t *logT_mmh, uint32_t *logT_mh);
 uint64_t p3_plan_bytes(uint32_t gamma, uint64_t k);
-int p3_plan_create(uint64_t n, uint64_t r, uint32_t gamma, uint64_t k, P3Plan **out);
+int p3_plan_create(uint64_t n, uint64_t r, uint32_t gamma, uint64_t k, bool stream_ordered, P3Plan **out);
 void p3_plan_destroy(P3Plan *pl);
 void p3_plan_query(const P3Plan *pl, uint64_t *len_mmh, uint64_t *len_mh, uint64_t *ws_bytes);
 const Geo3 *p3_stage(const P3Plan *pl, int stage);

@@ -1101,7 +1101,7 @@ struct P3Plan {
     uint64_t n = 0, r = 0, k = 0;
     uint32_t gamma = 0;
     Geo3 mmh{}, mh{};
-    std::vector<void *> allocs;
+    DevAlloc mem;  // every device buffer and table of the plan
     uint64_t ws_bytes = 0;
     u32 *Y = nullptr, *S3 = nullptr;
     u64 *ybuf = nullptr, *tbuf = nullptr, *H = nullptr;
@@ -1112,19 +1112,10 @@ struct P3Plan {
     u32 *spec_a = nullptr, *spec_b = nullptr;
     u64 *seed_copy = nullptr;
     bool prepared = false;
-    ~P3Plan() {
-        for (void *p : allocs) cudaFree(p);
-    }
+    ~P3Plan() { mem.release(); }
     void *alloc(size_t bytes, int *err) {
-        void *p = nullptr;
-        if (*err) return nullptr;
-        if (cudaMalloc(&p, bytes ? bytes : 8) != cudaSuccess) {
-            cudaGetLastError();  // an allocation failure must not read as a later launch's error
-            *err = PA_ERR_NOMEM;
-            return nullptr;
-        }
-        allocs.push_back(p);
-        ws_bytes += bytes;
+        void *p = mem.take(bytes, err);
+        if (p) ws_bytes += bytes;
         return p;
     }
 };
@@ -1200,22 +1191,20 @@ int build_tables(P3Plan *pl, Geo3 &X, const PrimeSet &ps, const Geo3 *other) {
             uint2 *dC = (uint2 *)pl->alloc(tC.size() * sizeof(uint2), &err);
             uint2 *dT = (uint2 *)pl->alloc(X.T * sizeof(uint2), &err);
             if (err) break;
-            if (cudaMemcpy(dR, tR.data(), tR.size() * sizeof(uint2), cudaMemcpyHostToDevice) ||
-                cudaMemcpy(dC, tC.data(), tC.size() * sizeof(uint2), cudaMemcpyHostToDevice)) {
-                err = PA_ERR_CUDA;
-                break;
-            }
+            pl->mem.upload(dR, tR.data(), tR.size() * sizeof(uint2), &err);
+            pl->mem.upload(dC, tC.data(), tC.size() * sizeof(uint2), &err);
+            if (err) break;
             a = 1;
             for (size_t e = 0; e < lo.size(); e++, a = a * w % p) lo[e] = (u32)a;
             const u32 wh = powmod(w, 1ULL << h, p);
             a = 1;
             for (size_t e = 0; e < hi.size(); e++, a = a * wh % p) hi[e] = (u32)a;
-            if (cudaMemcpy(dlo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice) ||
-                cudaMemcpy(dhi, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice) ||
-                p3_launch_fill_ctw(X.logR, X.logC, h, dlo, dhi, p, dT, nullptr) || cudaDeviceSynchronize()) {
-                err = PA_ERR_CUDA;
-                break;
-            }
+            // on the plan's private stream: building a plan waits for nothing else on the device;
+            // the stream orders the reuse of dlo / dhi by the next table
+            pl->mem.upload(dlo, lo.data(), lo.size() * 4, &err);
+            pl->mem.upload(dhi, hi.data(), hi.size() * 4, &err);
+            if (!err && p3_launch_fill_ctw(X.logR, X.logC, h, dlo, dhi, p, dT, pl->mem.stream)) err = PA_ERR_CUDA;
+            if (err) break;
             (dir ? X.itwR : X.twR)[j] = dR;
             (dir ? X.itwC : X.twC)[j] = dC;
             (dir ? X.ictw : X.ctw)[j] = dT;
@@ -1258,13 +1247,17 @@ uint64_t p3_plan_bytes(uint32_t gamma, uint64_t k) {
     return s + table_bytes(A) + (shared ? 0 : table_bytes(B)) + 2 * (1ULL << ((std::max(A.logT, B.logT) + 1) / 2)) * 4;
 }
 
-int p3_plan_create(uint64_t n, uint64_t r, uint32_t gamma, uint64_t k, P3Plan **out) {
+int p3_plan_create(uint64_t n, uint64_t r, uint32_t gamma, uint64_t k, bool stream_ordered, P3Plan **out) {
     *out = nullptr;
     Choice c1, c2;
     if (!choose(gamma, k, true, &c1) || !choose(gamma, 1, false, &c2)) return PA_ERR_UNSUPPORTED;
     if (p3_prepare_kernels()) return PA_ERR_CUDA;
     P3Plan *pl = new (std::nothrow) P3Plan();
     if (!pl) return PA_ERR_NOMEM;
+    if (pl->mem.init(stream_ordered)) {
+        delete pl;
+        return PA_ERR_CUDA;
+    }
     pl->n = n;
     pl->r = r;
     pl->gamma = gamma;
@@ -1286,10 +1279,12 @@ int p3_plan_create(uint64_t n, uint64_t r, uint32_t gamma, uint64_t k, P3Plan **
     pl->cta_cin = (unsigned char *)pl->alloc(nch / PA_CARRY_T + 1, &err);
     pl->flags_bytes = (4 + k) * sizeof(int);
     pl->flags = (int *)pl->alloc(pl->flags_bytes, &err);
+    if (!err) err = pl->mem.sync();  // the tables are filled
     if (err) {
         delete pl;
         return err;
     }
+    pl->ws_bytes = pl->mem.bytes;  // workspace and tables
     *out = pl;
     return PA_OK;
 }

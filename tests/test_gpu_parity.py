@@ -206,6 +206,15 @@ def test_paper_points_cv_dv():
         assert p.k * p.gamma == n
 
 
+def test_paper_point_cv_max_8e8():
+    """The largest CV block of Sec. 4 (k = 10, about 8e8 bits): n = 10 * 82589933,
+    r = floor(0.0972 n), no padding; both backends against the oracle."""
+    n = 10 * 82589933
+    r = int(np.floor(0.0972 * n))
+    p = _check(n, r, 12, parallel=True)
+    assert (p.gamma, p.k) == (82589933, 10) and p.k * p.gamma == n
+
+
 @pytest.mark.parametrize("backend", [GOLDILOCKS, P3])
 def test_host_async_stream_of_blocks(backend):
     """pa_hash_host_async: several blocks in flight on one stream (staging slots
