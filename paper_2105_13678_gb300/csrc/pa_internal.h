@@ -158,7 +158,7 @@ struct CarryDev {
 
 // One stage of the three-prime backend (pa_p3.cu): linear convolution of
 // digit vectors of M = T/2 digits of b bits, transform length T = R * C, over
-// the primes p[0..2] (< 2^30, 2^logT | p - 1).  Twiddle tables hold
+// the primes p[0..2] (< 2^28 for T <= 2^21, else < 2^30; 2^logT | p - 1).  Twiddle tables hold
 // (w, floor(w 2^32 / p)) pairs; device pointers owned by the plan.
 struct Geo3 {
     u64 T, M;        // transform length, digit slots per operand (T / 2)
@@ -166,6 +166,7 @@ struct Geo3 {
     u64 G;           // gamma: operand bits, and the modulus 2^G - 1 (Eq. 2) or 2^G (Eq. 4)
     u64 p01;         // p0 p1
     u32 logT, logR, logC, R, C, tc, b, K, stage;
+    u32 head;                   // 2^head p < 2^32 for all three primes (lazy-reduction headroom)
     u32 p[3], pinv[3];          // primes and p^-1 mod 2^32
     uint2 scale[3], red[3];     // 2^32 / T mod p; (1, floor(2^32 / p))
     uint2 c12, p0m2, c3;        // p0^-1 mod p1; p0 mod p2; (p0 p1)^-1 mod p2
@@ -264,7 +265,7 @@ int launch_fill_coltw(const Xform &X, u64 *coltw, void *stream);
 int p3_prepare_kernels();
 int p3_launch_fwd_col(const Geo3 &X, const Operands &S, int pairs, u32 *Y, void *stream, bool pair = true);
 int p3_launch_row_mac(const Geo3 &X, const u32 *Y, u32 *S3, void *stream, int mode = 0, u32 *spec = nullptr);
-int p3_launch_inv_col(const Geo3 &X, u32 *S3, void *stream);
+int p3_launch_inv_col(const Geo3 &X, u32 *S3, u64 *zero_out, u64 zero_words, void *stream);
 int p3_launch_digits(const Geo3 &X, const u32 *S3, u64 *z, u64 npad, const u64 *c_src, u64 c_base, u64 *zero_out,
                      u64 zero_words, void *stream);
 int p3_launch_fill_ctw(u32 logR, u32 logC, u32 h, const u32 *lo, const u32 *hi, u32 p, uint2 *out, void *stream);

@@ -66,19 +66,61 @@ __device__ __forceinline__ u32 rd32(const u64 *__restrict__ src, u64 pos, u32 nb
 __device__ __forceinline__ u32 round_ns(u32 l, u32 rd) { return rd ? 3u : l - 3u * ((l + 2) / 3 - 1); }
 __device__ __forceinline__ u32 round_s0(u32 l, u32 rd) { return rd ? round_ns(l, 0) + 3u * (rd - 1) : 0u; }
 
+// Lazy reduction.  Values are kept below B p with a bound B tracked per
+// element at compile time (the loops are fully unrolled, so every B folds to
+// a constant); 2^H p < 2^32 is the headroom of the prime set (H = 4 for the
+// primes below 2^28, 2 for those below 2^30).  A sum is formed unreduced while
+// its bound fits the headroom, otherwise its inputs are first brought down by
+// conditional subtractions; a difference a - b + B_b p is reduced by its Shoup
+// product into [0, 2p).  OUT is the bound the caller needs at the end of the
+// round (2: [0, 2p), 4: [0, 4p), 0: any 32-bit value, e.g. before a Shoup
+// product).
+__device__ __forceinline__ u32 csub(u32 x, u32 kp) { return min(x, x - kp); }  // x < 2 kp -> x < kp
+
+// Bring v below bound `to` (a power of two times p not below 2) from bound B.
+__device__ __forceinline__ void reduce_to(u32 &v, int &B, int to, u32 p) {
+#pragma unroll
+    for (int it = 0; it < 5; it++) {
+        if (B > to) {
+            v = csub(v, (u32)(B / 2) * p);
+            B /= 2;
+        }
+    }
+}
+
+// Operands a (bound Ba), b (bound Bb) of a sum must satisfy Ba + Bb <= 2^H:
+// reduce the larger bound first.
+template <int H>
+__device__ __forceinline__ void make_room(u32 &a, int &Ba, u32 &b, int &Bb, u32 p) {
+#pragma unroll
+    for (int it = 0; it < 8; it++) {
+        if (Ba + Bb > (1 << H)) {
+            if (Ba >= Bb) {
+                a = csub(a, (u32)(Ba / 2) * p);
+                Ba /= 2;
+            } else {
+                b = csub(b, (u32)(Bb / 2) * p);
+                Bb /= 2;
+            }
+        }
+    }
+}
+
 // Radix-2 DIF stages s0 .. s0+NS-1 of a length-L transform on the elements
 // base + m*stride (lo = base mod stride); stage s pairs (i, i + L/2^(s+1))
 // with twiddle omega_L^((i mod L/2^(s+1)) 2^s).  HZ: the upper half of the
 // group is zero on entry.  In the final round (LAST) the twiddles of the
-// pairs with i mod L/2^(s+1) = 0 are 1.
+// pairs with i mod L/2^(s+1) = 0 are 1.  Inputs below 2p.
 // rt: the task's round twiddles, stage sg's pair jj at q = 2^NS - 2^(NS-sg) + jj.
 // TS: the round table is in shared memory (plain loads) rather than global (read-only path).
 template <bool TS>
 __device__ __forceinline__ uint2 twl(const uint2 *__restrict__ p) { return TS ? *p : __ldg(p); }
 
-template <int NS, bool LAST, bool HZ, bool TS = false>
+template <int NS, bool LAST, bool HZ, bool TS = false, int H = 2, int OUT = 2>
 __device__ __forceinline__ void dif3(u32 (&v)[8], const uint2 *__restrict__ rt, u32 p) {
-    const u32 p2 = 2 * p;
+    int B[8];
+#pragma unroll
+    for (int m = 0; m < 8; m++) B[m] = 2;
 #pragma unroll
     for (int sg = 0; sg < NS; sg++) {
         const int half = 1 << (NS - 1 - sg);
@@ -88,24 +130,35 @@ __device__ __forceinline__ void dif3(u32 (&v)[8], const uint2 *__restrict__ rt, 
             const int jj = m & (half - 1);
             const bool one = LAST && jj == 0;
             const int q = (1 << NS) - (1 << (NS - sg)) + jj;
-            const u32 a = v[m], b = v[m + half];
+            u32 a = v[m], b = v[m + half];
             if (HZ && sg == 0) {
                 v[m + half] = one ? a : shoup(a, twl<TS>(rt + q), p);
+                B[m + half] = one ? B[m] : 2;
                 continue;
             }
-            v[m] = red2(a + b, p2);
-            const u32 d = a - b + p2;
-            v[m + half] = one ? red2(d, p2) : shoup(d, twl<TS>(rt + q), p);
+            int Ba = B[m], Bb = B[m + half];
+            make_room<H>(a, Ba, b, Bb, p);
+            v[m] = a + b;
+            const u32 d = a - b + (u32)Bb * p;
+            B[m] = Ba + Bb;
+            v[m + half] = one ? d : shoup(d, twl<TS>(rt + q), p);
+            B[m + half] = one ? Ba + Bb : 2;
         }
+    }
+    if (OUT) {
+#pragma unroll
+        for (int m = 0; m < (1 << NS); m++) reduce_to(v[m], B[m], OUT, p);
     }
 }
 
 // Inverse of dif3 up to a factor 2^NS (DIT, stages reversed, inverse
 // twiddles in the same table layout).  HO: the upper outputs of the last
-// stage are not needed.
-template <int NS, bool LAST, bool HO>
+// stage are not needed.  Inputs below 2p.
+template <int NS, bool LAST, bool HO, int H = 2, int OUT = 2>
 __device__ __forceinline__ void dit3(u32 (&v)[8], const uint2 *__restrict__ rt, u32 p) {
-    const u32 p2 = 2 * p;
+    int B[8];
+#pragma unroll
+    for (int m = 0; m < 8; m++) B[m] = 2;
 #pragma unroll
     for (int sg = NS - 1; sg >= 0; sg--) {
         const int half = 1 << (NS - 1 - sg);
@@ -115,19 +168,36 @@ __device__ __forceinline__ void dit3(u32 (&v)[8], const uint2 *__restrict__ rt, 
             const int jj = m & (half - 1);
             const bool one = LAST && jj == 0;
             const int q = (1 << NS) - (1 << (NS - sg)) + jj;
-            const u32 a = v[m];
-            const u32 t = one ? v[m + half] : shoup(v[m + half], __ldg(rt + q), p);
-            v[m] = red2(a + t, p2);
-            if (!(HO && sg == 0)) v[m + half] = red2(a - t + p2, p2);
+            u32 a = v[m];
+            int Ba = B[m];
+            u32 t = v[m + half];
+            int Bt = B[m + half];
+            if (!one) {
+                t = shoup(t, __ldg(rt + q), p);
+                Bt = 2;
+            }
+            make_room<H>(a, Ba, t, Bt, p);
+            v[m] = a + t;
+            if (!(HO && sg == 0)) v[m + half] = a - t + (u32)Bt * p;
+            B[m] = B[m + half] = Ba + Bt;
         }
+    }
+    if (OUT) {
+#pragma unroll
+        for (int m = 0; m < (1 << NS); m++)
+            if (!(HO && m >= (1 << (NS - 1)))) reduce_to(v[m], B[m], OUT, p);
     }
 }
 
 // Stages 0..3 of a length-L transform on 16 elements lo + m L/16 whose upper
 // 8 are zero on entry (the zero-padded half), twiddles rt[16 - 2^(4-sg) + jj]
 // = omega_L^((lo + jj L/16) 2^sg); the round table is in shared memory.
+// Inputs below 2p.
+template <int H = 2, int OUT = 2>
 __device__ __forceinline__ void dif16_hz(u32 (&v)[16], const uint2 *__restrict__ rt, u32 p) {
-    const u32 p2 = 2 * p;
+    int B[16];
+#pragma unroll
+    for (int m = 0; m < 16; m++) B[m] = 2;
 #pragma unroll
     for (int sg = 0; sg < 4; sg++) {
         const int half = 8 >> sg;
@@ -135,23 +205,34 @@ __device__ __forceinline__ void dif16_hz(u32 (&v)[16], const uint2 *__restrict__
         for (int m = 0; m < 16; m++) {
             if (m & half) continue;
             const int q = 16 - (16 >> sg) + (m & (half - 1));
-            const u32 a = v[m];
+            u32 a = v[m];
             if (sg == 0) {
                 v[m + half] = shoup(a, rt[q], p);  // (a, 0) -> (a, a w)
+                B[m + half] = 2;
                 continue;
             }
-            const u32 b = v[m + half];
-            v[m] = red2(a + b, p2);
-            v[m + half] = shoup(a - b + p2, rt[q], p);
+            u32 b = v[m + half];
+            int Ba = B[m], Bb = B[m + half];
+            make_room<H>(a, Ba, b, Bb, p);
+            v[m] = a + b;
+            v[m + half] = shoup(a - b + (u32)Bb * p, rt[q], p);
+            B[m] = Ba + Bb;
+            B[m + half] = 2;
         }
+    }
+    if (OUT) {
+#pragma unroll
+        for (int m = 0; m < 16; m++) reduce_to(v[m], B[m], OUT, p);
     }
 }
 
 // Inverse of the 4-stage round (DIT, stages 3..0, inverse twiddles in the same
-// layout); HO: the upper 8 outputs are not needed.
-template <bool HO>
+// layout); HO: the upper 8 outputs are not needed.  Inputs below 2p.
+template <bool HO, int H = 2, int OUT = 2>
 __device__ __forceinline__ void dit16(u32 (&v)[16], const uint2 *__restrict__ rt, u32 p) {
-    const u32 p2 = 2 * p;
+    int B[16];
+#pragma unroll
+    for (int m = 0; m < 16; m++) B[m] = 2;
 #pragma unroll
     for (int sg = 3; sg >= 0; sg--) {
         const int half = 8 >> sg;
@@ -159,11 +240,20 @@ __device__ __forceinline__ void dit16(u32 (&v)[16], const uint2 *__restrict__ rt
         for (int m = 0; m < 16; m++) {
             if (m & half) continue;
             const int q = 16 - (16 >> sg) + (m & (half - 1));
-            const u32 a = v[m];
-            const u32 t = shoup(v[m + half], __ldg(rt + q), p);
-            v[m] = red2(a + t, p2);
-            if (!(HO && sg == 0)) v[m + half] = red2(a - t + p2, p2);
+            u32 a = v[m];
+            int Ba = B[m];
+            u32 t = shoup(v[m + half], __ldg(rt + q), p);
+            int Bt = 2;
+            make_room<H>(a, Ba, t, Bt, p);
+            v[m] = a + t;
+            if (!(HO && sg == 0)) v[m + half] = a - t + (u32)Bt * p;
+            B[m] = B[m + half] = Ba + Bt;
         }
+    }
+    if (OUT) {
+#pragma unroll
+        for (int m = 0; m < 16; m++)
+            if (!(HO && m >= 8)) reduce_to(v[m], B[m], OUT, p);
     }
 }
 
@@ -275,7 +365,7 @@ __device__ __forceinline__ u32 digit_raw(const Geo3 &X, const Desc &d, u64 pos, 
 // ------------------------------------------------------------ column pass --
 
 // LL, TC: log2 R and the tile width when fixed at compile time (0: from X).
-template <int NS, bool PAIR, bool FIRST, bool LAST, int LL, int TC, bool TS = false>
+template <int NS, bool PAIR, bool FIRST, bool LAST, int LL, int TC, bool TS = false, int H = 2>
 __device__ __forceinline__ void fwd3_round(const Geo3 &X, u32 j, const Desc &dx, const Desc &da, u32 *__restrict__ smx,
                                            u32 *__restrict__ sma, u32 *__restrict__ Yx, u32 *__restrict__ Ya, u32 c0,
                                            u32 s0, u32 rd, bool &ones, const uint2 *__restrict__ stw = nullptr) {
@@ -313,8 +403,9 @@ __device__ __forceinline__ void fwd3_round(const Geo3 &X, u32 j, const Desc &dx,
             }
         }
         const uint2 *rt = tw + lo * ((1u << NS) - 1);
-        dif3<NS, LAST, FIRST, TS>(vx, rt, p);
-        if (PAIR) dif3<NS, LAST, FIRST, TS>(va, rt, p);
+        // the last round's outputs go straight into Shoup products (any bound)
+        dif3<NS, LAST, FIRST, TS, H, LAST ? 0 : 2>(vx, rt, p);
+        if (PAIR) dif3<NS, LAST, FIRST, TS, H, LAST ? 0 : 2>(va, rt, p);
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
             if (LAST) {
@@ -332,7 +423,7 @@ __device__ __forceinline__ void fwd3_round(const Geo3 &X, u32 j, const Desc &dx,
 }
 
 // grid (C / tc, pairs, 3 primes): a tile of tc columns of pair blockIdx.y + pair0.
-template <bool PAIR, int LL, int TC>
+template <bool PAIR, int LL, int TC, int H>
 __global__ void __launch_bounds__(kColThreads) k3_fwd_col(Geo3 X, Operands S, u32 *__restrict__ Y) {
     pdl_wait();
     extern __shared__ u32 sm3[];
@@ -351,11 +442,11 @@ __global__ void __launch_bounds__(kColThreads) k3_fwd_col(Geo3 X, Operands S, u3
 #define P3_FWD(NSV)                                                                                   \
     do {                                                                                              \
         if (first)                                                                                    \
-            fwd3_round<NSV, PAIR, true, false, LL, TC>(X, j, dx, da, smx, sma, Yx, Ya, c0, s0, rd, ones);         \
+            fwd3_round<NSV, PAIR, true, false, LL, TC, false, H>(X, j, dx, da, smx, sma, Yx, Ya, c0, s0, rd, ones);  \
         else if (last)                                                                                \
-            fwd3_round<NSV, PAIR, false, true, LL, TC>(X, j, dx, da, smx, sma, Yx, Ya, c0, s0, rd, ones);         \
+            fwd3_round<NSV, PAIR, false, true, LL, TC, false, H>(X, j, dx, da, smx, sma, Yx, Ya, c0, s0, rd, ones);  \
         else                                                                                          \
-            fwd3_round<NSV, PAIR, false, false, LL, TC>(X, j, dx, da, smx, sma, Yx, Ya, c0, s0, rd, ones);        \
+            fwd3_round<NSV, PAIR, false, false, LL, TC, false, H>(X, j, dx, da, smx, sma, Yx, Ya, c0, s0, rd, ones); \
     } while (0)
         P3_DISPATCH_NS(ns, P3_FWD);
 #undef P3_FWD
@@ -378,7 +469,7 @@ __global__ void __launch_bounds__(kColThreads) k3_fwd_col(Geo3 X, Operands S, u3
 // shared tile in three rounds -- stages 0-3 in registers on 16 elements
 // (upper half zero), then 4-6 and 7-9 -- with its round twiddles staged in
 // shared memory.  PAIR: both operands of pair i; else the single operand i.
-template <int LL, int TC, bool PAIR>
+template <int LL, int TC, bool PAIR, int H>
 __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32 *__restrict__ Y) {
     pdl_wait();
     static_assert(LL == 10 && TC == 8, "one task per thread: R/16 x 8 columns = 512");
@@ -422,7 +513,7 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
             u32 v[16];
 #pragma unroll
             for (u32 m = 0; m < 16; m++) v[m] = m < 8 ? (raw ? rx[m] : shoup(rx[m], red, p)) : 0u;
-            dif16_hz(v, rt, p);
+            dif16_hz<H, 2>(v, rt, p);
 #pragma unroll
             for (u32 m = 0; m < 16; m++) smx[a0 + m * dsm] = v[m];
         }
@@ -430,15 +521,15 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
             u32 v[16];
 #pragma unroll
             for (u32 m = 0; m < 16; m++) v[m] = m < 8 ? (raw ? ra[m] : shoup(ra[m], red, p)) : 0u;
-            dif16_hz(v, rt, p);
+            dif16_hz<H, 2>(v, rt, p);
 #pragma unroll
             for (u32 m = 0; m < 16; m++) sma[a0 + m * dsm] = v[m];
         }
         __syncthreads();
         // stages 4-6 and 7-9: the standard partition's rounds 2 and 3
-        fwd3_round<3, PAIR, false, false, LL, TC, true>(X, j, dx, da, smx, sma, Yx, Ya, c0, 4, 2, ones, stw);
+        fwd3_round<3, PAIR, false, false, LL, TC, true, H>(X, j, dx, da, smx, sma, Yx, Ya, c0, 4, 2, ones, stw);
         __syncthreads();
-        fwd3_round<3, PAIR, false, true, LL, TC, true>(X, j, dx, da, smx, sma, Yx, Ya, c0, 7, 3, ones, stw);
+        fwd3_round<3, PAIR, false, true, LL, TC, true, H>(X, j, dx, da, smx, sma, Yx, Ya, c0, 7, 3, ones, stw);
         __syncthreads();
     }
     pdl_trigger();
@@ -458,7 +549,7 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
 // base a multiple of 8), so their padded words are px(base) + m * pstep(stride).
 // MODE 0: both rows of pair i, product into acc; 1: row x only, its spectrum
 // stored to spec; 2: row x only, times the stored spectrum held in fa.
-template <int NS, int ACC, bool LAST, int LL, int MODE>
+template <int NS, int ACC, bool LAST, int LL, int MODE, int H>
 __device__ __forceinline__ void row_fwd3(const Geo3 &X, u32 j, const u32 (&fx)[ACC], const u32 (&fa)[ACC],
                                          u32 *__restrict__ smx, u32 *__restrict__ sma, u32 s0, u32 rd, bool first,
                                          u32 (&acc)[ACC], u32 *__restrict__ spec) {
@@ -480,8 +571,11 @@ __device__ __forceinline__ void row_fwd3(const Geo3 &X, u32 j, const u32 (&fx)[A
                 if (TWO) va[m] = first ? fa[t * (1 << NS) + m] : sma[a0 + m * dsm];
             }
             const uint2 *rt = tw + lo * ((1u << NS) - 1);
-            dif3<NS, LAST, false>(vx, rt, p);
-            if (TWO) dif3<NS, LAST, false>(va, rt, p);
+            // the last round feeds the Montgomery products (inputs below 4p when p < 2^28,
+            // whose product then stays below 2^32 p) or the stored spectra ([0, 2p))
+            constexpr int OUTL = (MODE == 1 || H < 4) ? 2 : 4;
+            dif3<NS, LAST, false, false, H, LAST ? OUTL : 2>(vx, rt, p);
+            if (TWO) dif3<NS, LAST, false, false, H, LAST ? OUTL : 2>(va, rt, p);
             if constexpr (LAST && MODE == 1) {  // the last round has stride 1: elements base + m
                 if constexpr (NS == 3) {
                     uint4 *d = reinterpret_cast<uint4 *>(spec + base);
@@ -525,7 +619,7 @@ __device__ __forceinline__ void row_load3(const Geo3 &X, const u32 *__restrict__
     }
 }
 
-template <int NS, int ACC, bool LAST, int LL>
+template <int NS, int ACC, bool LAST, int LL, int H>
 __device__ __forceinline__ void row_inv3(const Geo3 &X, u32 j, u32 *__restrict__ sm, u32 *__restrict__ Srow, u32 row,
                                          u32 s0, u32 rd, bool to_global, const u32 (&acc)[ACC]) {
     const u32 l = LL ? (u32)LL : X.logC, sh = l - s0 - NS, stride = 1u << sh, ngroups = (1u << l) >> NS, p = X.p[j];
@@ -541,7 +635,10 @@ __device__ __forceinline__ void row_inv3(const Geo3 &X, u32 j, u32 *__restrict__
             u32 v[8];
 #pragma unroll
             for (int m = 0; m < (1 << NS); m++) v[m] = LAST ? acc[t * (1 << NS) + m] : sm[a0 + m * dsm];
-            dit3<NS, LAST, false>(v, itw + lo * ((1u << NS) - 1), p);
+            if (to_global)  // followed by the Shoup product with the inverse inter-pass twiddle
+                dit3<NS, LAST, false, H, 0>(v, itw + lo * ((1u << NS) - 1), p);
+            else
+                dit3<NS, LAST, false, H, 2>(v, itw + lo * ((1u << NS) - 1), p);
 #pragma unroll
             for (int m = 0; m < (1 << NS); m++) {
                 if (to_global) {
@@ -582,7 +679,7 @@ __device__ __forceinline__ void row_load_spec(u32 ngroups, const u32 *__restrict
 // to spec ([prime][operand][T], last-round order); 2 (prepared hashing):
 // forward rows of the single operands times the stored spectra, then the
 // inverse rows.
-template <int ACC, int LL, int MODE>
+template <int ACC, int LL, int MODE, int H>
 __global__ void __launch_bounds__(1024) k3_row_mac(Geo3 X, const u32 *__restrict__ Y, u32 *__restrict__ S3,
                                                    u32 *__restrict__ spec) {
     pdl_wait();
@@ -614,9 +711,9 @@ __global__ void __launch_bounds__(1024) k3_row_mac(Geo3 X, const u32 *__restrict
 #define P3_ROWF(NSV)                                                                                  \
     do {                                                                                              \
         if (last)                                                                                     \
-            row_fwd3<NSV, ACC, true, LL, MODE>(X, j, fx, fa, smx, sma, s0, rd, first, acc, srow);     \
+            row_fwd3<NSV, ACC, true, LL, MODE, H>(X, j, fx, fa, smx, sma, s0, rd, first, acc, srow);  \
         else                                                                                          \
-            row_fwd3<NSV, ACC, false, LL, MODE>(X, j, fx, fa, smx, sma, s0, rd, first, acc, srow);    \
+            row_fwd3<NSV, ACC, false, LL, MODE, H>(X, j, fx, fa, smx, sma, s0, rd, first, acc, srow); \
     } while (0)
             P3_DISPATCH_NS(ns, P3_ROWF);
 #undef P3_ROWF
@@ -635,9 +732,9 @@ __global__ void __launch_bounds__(1024) k3_row_mac(Geo3 X, const u32 *__restrict
 #define P3_ROWI(NSV)                                                          \
     do {                                                                      \
         if (from_acc)                                                         \
-            row_inv3<NSV, ACC, true, LL>(X, j, smx, Srow, row, s0, rd, to_global, acc);  \
+            row_inv3<NSV, ACC, true, LL, H>(X, j, smx, Srow, row, s0, rd, to_global, acc);  \
         else                                                                  \
-            row_inv3<NSV, ACC, false, LL>(X, j, smx, Srow, row, s0, rd, to_global, acc); \
+            row_inv3<NSV, ACC, false, LL, H>(X, j, smx, Srow, row, s0, rd, to_global, acc); \
     } while (0)
         P3_DISPATCH_NS(ns, P3_ROWI);
 #undef P3_ROWI
@@ -648,7 +745,7 @@ __global__ void __launch_bounds__(1024) k3_row_mac(Geo3 X, const u32 *__restrict
 
 // -------------------------------------------------------- inverse columns --
 
-template <int NS, bool FIRSTR, bool TOGLOBAL, bool HO, int LL, int TC>
+template <int NS, bool FIRSTR, bool TOGLOBAL, bool HO, int LL, int TC, int H>
 __device__ __forceinline__ void inv3_round(const Geo3 &X, u32 j, u32 *__restrict__ S3, u32 *__restrict__ sm, u32 c0,
                                            u32 s0, u32 rd) {
     const u32 l = LL ? (u32)LL : X.logR, tc = TC ? (u32)TC : X.tc, p = X.p[j];
@@ -667,7 +764,8 @@ __device__ __forceinline__ void inv3_round(const Geo3 &X, u32 j, u32 *__restrict
         u32 v[8];
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) v[m] = FIRSTR ? Sj[e0 + m * dY] : sm[a0 + m * dsm];
-        dit3<NS, FIRSTR, HO>(v, itw + lo * ((1u << NS) - 1), p);
+        // the residues written to S3 only feed Shoup products (the CRT): any bound
+        dit3<NS, FIRSTR, HO, H, TOGLOBAL ? 0 : 2>(v, itw + lo * ((1u << NS) - 1), p);
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
             if (TOGLOBAL) {
@@ -682,9 +780,15 @@ __device__ __forceinline__ void inv3_round(const Geo3 &X, u32 j, u32 *__restrict
 
 // grid (C / tc, 3 primes).  In place on S3: every CTA reads its own columns
 // completely (first round) before it writes them (last round).
-template <int LL, int TC>
-__global__ void __launch_bounds__(kColThreads) k3_inv_col(Geo3 X, u32 *__restrict__ S3) {
+template <int LL, int TC, int H>
+__global__ void __launch_bounds__(kColThreads) k3_inv_col(Geo3 X, u32 *__restrict__ S3, u64 *__restrict__ zero_out,
+                                                          u64 zero_words) {
     pdl_wait();
+    {  // the output bits of the fused carry (k3_resolve_a ORs into them)
+        const u64 nthr = (u64)gridDim.x * gridDim.y * blockDim.x;
+        for (u64 i = ((u64)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x; i < zero_words; i += nthr)
+            zero_out[i] = 0;
+    }
     extern __shared__ u32 sm3[];
     const u32 j = blockIdx.y, tc = TC ? (u32)TC : X.tc, c0 = blockIdx.x * tc;
     const u32 l = LL ? (u32)LL : X.logR, nr = (l + 2) / 3;
@@ -699,13 +803,13 @@ __global__ void __launch_bounds__(kColThreads) k3_inv_col(Geo3 X, u32 *__restric
 #define P3_INV(NSV)                                                       \
     do {                                                                  \
         if (first)                                                        \
-            inv3_round<NSV, true, false, false, LL, TC>(X, j, S3, sm3, c0, s0, (u32)rd);   \
+            inv3_round<NSV, true, false, false, LL, TC, H>(X, j, S3, sm3, c0, s0, (u32)rd);   \
         else if (last && ho)                                              \
-            inv3_round<NSV, false, true, true, LL, TC>(X, j, S3, sm3, c0, s0, (u32)rd);    \
+            inv3_round<NSV, false, true, true, LL, TC, H>(X, j, S3, sm3, c0, s0, (u32)rd);    \
         else if (last)                                                    \
-            inv3_round<NSV, false, true, false, LL, TC>(X, j, S3, sm3, c0, s0, (u32)rd);   \
+            inv3_round<NSV, false, true, false, LL, TC, H>(X, j, S3, sm3, c0, s0, (u32)rd);   \
         else                                                              \
-            inv3_round<NSV, false, false, false, LL, TC>(X, j, S3, sm3, c0, s0, (u32)rd);  \
+            inv3_round<NSV, false, false, false, LL, TC, H>(X, j, S3, sm3, c0, s0, (u32)rd);  \
     } while (0)
         P3_DISPATCH_NS(ns, P3_INV);
 #undef P3_INV
@@ -725,11 +829,11 @@ __global__ void __launch_bounds__(kColThreads) k3_inv_col(Geo3 X, u32 *__restric
 #pragma unroll
                 for (u32 m = 0; m < 16; m++) v[m] = sm3[a0 + m * 576];  // 64 rows apart: pstepc(512)
                 if (ho) {
-                    dit16<true>(v, itw + lo * 15, p);
+                    dit16<true, H, 0>(v, itw + lo * 15, p);
 #pragma unroll
                     for (u32 m = 0; m < 8; m++) Sj[e0 + m * dY] = v[m];
                 } else {
-                    dit16<false>(v, itw + lo * 15, p);
+                    dit16<false, H, 0>(v, itw + lo * 15, p);
 #pragma unroll
                     for (u32 m = 0; m < 16; m++) Sj[e0 + m * dY] = v[m];
                 }
@@ -743,11 +847,11 @@ __global__ void __launch_bounds__(kColThreads) k3_inv_col(Geo3 X, u32 *__restric
 
 // Coefficient e from its three residues (scaled by 2^32 / T): Garner's mixed
 // radix x1 + p0 x2 + p0 p1 x3.
-__device__ __forceinline__ unsigned __int128 crt_value(const Geo3 &X, const u32 *__restrict__ S3, u64 e) {
+__device__ __forceinline__ unsigned __int128 crt_combine(const Geo3 &X, u32 res0, u32 res1, u32 res2) {
     const u32 p0 = X.p[0], p1 = X.p[1], p2 = X.p[2];
-    const u32 r0 = canon(shoup(__ldg(S3 + e), X.scale[0], p0), p0);
-    const u32 r1 = canon(shoup(__ldg(S3 + X.T + e), X.scale[1], p1), p1);
-    const u32 r2 = canon(shoup(__ldg(S3 + 2 * X.T + e), X.scale[2], p2), p2);
+    const u32 r0 = canon(shoup(res0, X.scale[0], p0), p0);
+    const u32 r1 = canon(shoup(res1, X.scale[1], p1), p1);
+    const u32 r2 = canon(shoup(res2, X.scale[2], p2), p2);
     const u32 x1 = r0;
     const u32 u1 = canon(shoup(x1, X.red[1], p1), p1);
     const u32 x2 = canon(shoup(r1 - u1 + p1, X.c12, p1), p1);
@@ -756,6 +860,10 @@ __device__ __forceinline__ unsigned __int128 crt_value(const Geo3 &X, const u32 
     const u32 s2 = canon(u2 + w2, p2);
     const u32 x3 = canon(shoup(r2 - s2 + p2, X.c3, p2), p2);
     return (unsigned __int128)x1 + (unsigned __int128)((u64)p0 * x2) + (unsigned __int128)X.p01 * x3;
+}
+
+__device__ __forceinline__ unsigned __int128 crt_value(const Geo3 &X, const u32 *__restrict__ S3, u64 e) {
+    return crt_combine(X, __ldg(S3 + e), __ldg(S3 + X.T + e), __ldg(S3 + 2 * X.T + e));
 }
 
 // Digit t (bit offset t b) of the value to resolve.  Coefficient e's value V_e
@@ -816,6 +924,297 @@ __global__ void __launch_bounds__(256) k3_digits(Geo3 X, const u32 *__restrict__
     pdl_trigger();
 }
 
+// ------------------------------------- fused digit gather + carry (large) --
+//
+// The digits of k3_digits and the chunk carries of the carry kernels in one
+// pass, for vectors whose chunks of PA_CARRY_D digits span >= 64 bits: thread
+// t of CTA q owns chunk q 255 - 1 + t (thread 0 the last chunk of the previous
+// CTA -- around the ring for CTA 0 -- whose carry-out it provides).  A thread
+// computes the CRT values of its chunk's 8 positions once per wrap and takes
+// the pieces its first two digits need from the previous lane (shuffles), the
+// previous warp (shared memory) or, for thread 0, two extra CRT values.  The
+// digits never go to memory: the chunk's carry-out H (zero carry-in), its bits
+// with carry-in H of the previous chunk (OR-ed into y, which the inverse
+// column pass zeroed), and its generate / propagate state are derived in
+// registers; the CTA's state feeds k3_resolve_c.
+constexpr u32 kResolveChunks = 255;  // chunks written per CTA (thread 0 only provides a carry-out)
+
+__device__ __forceinline__ bool digit_takes_wrap(const Geo3 &X, u64 t, u32 w, u64 off, u64 D) {
+    return t < X.nd && (w == 0 || (t * X.b + D < X.G && t + off <= 2 * X.M));
+}
+
+// b-bit pieces of coefficient e (0 outside [0, ncoef)): v0, v1 < 2^b <= 2^30.
+__device__ __forceinline__ void crt_pieces(const Geo3 &X, const u32 *__restrict__ S3, long long e, u64 ncoef, u32 &v0,
+                                           u32 &v1, u64 &v2) {
+    v0 = v1 = 0;
+    v2 = 0;
+    if (e < 0 || (u64)e >= ncoef) return;
+    const unsigned __int128 V = crt_value(X, S3, (u64)e);
+    const u64 mask = (1ULL << X.b) - 1;
+    v0 = (u32)((u64)V & mask);
+    v1 = (u32)((u64)(V >> X.b) & mask);
+    v2 = (u64)(V >> (2 * X.b));
+}
+
+template <bool RING>
+__global__ void __launch_bounds__(256) k3_resolve_a(Geo3 X, const u32 *__restrict__ S3, CarryDev cd,
+                                                    const u64 *__restrict__ c_src, u64 c_base, u64 *__restrict__ y) {
+    pdl_wait();
+    __shared__ u64 Hs[256];
+    __shared__ u64 xw[8][3];  // per warp: pieces v1(7), v2(6), v2(7) of its last lane
+    __shared__ unsigned wg[8], wp[8];
+    const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long cq = (long long)blockIdx.x * kResolveChunks - 1 + tid;
+    // chunk whose digits this thread forms (thread 0 of CTA 0: the top chunk around the ring)
+    const bool exists = cq >= 0 ? (u64)cq < cd.nchunks : RING;
+    const u64 ch = cq >= 0 ? (u64)cq : cd.nchunks - 1;
+    const bool real = tid > 0 && cq >= 0 && (u64)cq < cd.nchunks;  // chunks this CTA writes
+    const u64 t0 = ch * PA_CARRY_D;
+    const u64 b = X.b, G = X.G;
+    const u64 ncoef = RING ? 2 * X.M - 1 : X.M;
+    const u64 nd = X.nd, n2 = (2 * G + b - 1) / b;
+    u64 z[PA_CARRY_D];
+#pragma unroll
+    for (u32 d = 0; d < PA_CARRY_D; d++) z[d] = 0;
+    // threads whose previous thread holds a chunk that is not the one below:
+    // thread 0, and at the ring's wrap the thread of chunk 0
+    const bool own_prev = tid == 0 || cq == 0;
+#pragma unroll 1
+    for (u32 w = 0; w < (RING ? 3u : 1u); w++) {
+        const u64 off = w == 0 ? 0 : (w == 1 ? nd : n2);
+        const u64 D = w == 0 ? 0 : (w == 1 ? nd * b - G : n2 * b - 2 * G);
+        // positions t0 + j + off, j = 0..7; digit t0 + j needs pieces of j, j - 1, j - 2.
+        // All residues of the wrap are loaded before any CRT (memory-level parallelism).
+        u32 q0[PA_CARRY_D + 2], q1[PA_CARRY_D + 2], q2[PA_CARRY_D + 2];  // [0..7]: j, [8], [9]: j = -1, -2
+        bool need[PA_CARRY_D];
+#pragma unroll
+        for (u32 j = 0; j < PA_CARRY_D; j++) need[j] = exists && digit_takes_wrap(X, t0 + j, w, off, D);
+#pragma unroll
+        for (u32 j = 0; j < PA_CARRY_D + 2; j++) {
+            const long long e = j < PA_CARRY_D ? (long long)(t0 + off + j) : (long long)(t0 + off) - (long long)(j - 7);
+            const bool ld = (j < PA_CARRY_D ? need[j] : (own_prev && need[0])) && e >= 0 && (u64)e < ncoef;
+            q0[j] = ld ? __ldg(S3 + e) : 0u;
+            q1[j] = ld ? __ldg(S3 + X.T + e) : 0u;
+            q2[j] = ld ? __ldg(S3 + 2 * X.T + e) : 0u;
+        }
+        auto pieces = [&](u32 j, u32 &c0, u32 &c1, u64 &c2) {
+            const unsigned __int128 V = crt_combine(X, q0[j], q1[j], q2[j]);
+            const u64 mask = (1ULL << b) - 1;
+            c0 = (u32)((u64)V & mask);
+            c1 = (u32)((u64)(V >> b) & mask);
+            c2 = (u64)(V >> (2 * b));
+        };
+        // pieces the next lane needs (j = 6, 7) first; a residue triple of zeros gives zero pieces
+        u32 v0_6, v1_6, v0_7, v1_7;
+        u64 v2_6, v2_7;
+        pieces(6, v0_6, v1_6, v2_6);
+        pieces(7, v0_7, v1_7, v2_7);
+        // pieces of positions j = -1, -2 from the previous lane / warp / own CRT
+        u32 p1m1 = __shfl_up_sync(0xFFFFFFFFu, v1_7, 1);
+        u64 p2m1 = __shfl_up_sync(0xFFFFFFFFu, v2_7, 1), p2m2 = __shfl_up_sync(0xFFFFFFFFu, v2_6, 1);
+        if (lane == 31) {
+            xw[warp][0] = v1_7;
+            xw[warp][1] = v2_7;
+            xw[warp][2] = v2_6;
+        }
+        __syncthreads();
+        if (lane == 0 && warp > 0) {
+            p1m1 = (u32)xw[warp - 1][0];
+            p2m1 = xw[warp - 1][1];
+            p2m2 = xw[warp - 1][2];
+        }
+        if (own_prev) {
+            u32 a0, a1;
+            u64 a2;
+            pieces(8, a0, a1, a2);
+            p1m1 = a1;
+            p2m1 = a2;
+            pieces(9, a0, a1, a2);
+            p2m2 = a2;
+        }
+        u32 w1 = p1m1;               // v1 of position j - 1
+        u64 w2a = p2m1, w2b = p2m2;  // v2 of positions j - 1, j - 2
+#pragma unroll
+        for (u32 j = 0; j < PA_CARRY_D; j++) {
+            u32 c0, c1;
+            u64 c2;
+            if (j == 6) {
+                c0 = v0_6, c1 = v1_6, c2 = v2_6;
+            } else if (j == 7) {
+                c0 = v0_7, c1 = v1_7, c2 = v2_7;
+            } else {
+                pieces(j, c0, c1, c2);
+            }
+            if (need[j]) z[j] += ((u64)c0 + w1 + w2b) << D;
+            w1 = c1;
+            w2b = w2a;
+            w2a = c2;
+        }
+        __syncthreads();
+    }
+    if (!RING && c_src && exists) {
+#pragma unroll
+        for (u32 j = 0; j < PA_CARRY_D; j++) {
+            const u64 t = t0 + j;
+            if (t < nd) z[j] += rd32(c_src, c_base + t * b, (u32)min(b, G - t * b));
+        }
+    }
+    // chunk carry-out with zero carry-in
+    u32 bd[PA_CARRY_D];
+    u64 s = min(t0 * b, G);
+    const u64 s_begin = s;
+#pragma unroll
+    for (u32 d = 0; d < PA_CARRY_D; d++) {
+        const u64 s1 = min((t0 + d + 1) * b, G);
+        bd[d] = (u32)(s1 - s);
+        s = s1;
+    }
+    unsigned __int128 acc = 0;
+#pragma unroll
+    for (u32 d = 0; d < PA_CARRY_D; d++) {
+        acc += z[d];
+        acc >>= bd[d];
+    }
+    const u64 Ht = exists ? (u64)acc : 0;
+    Hs[tid] = Ht;
+    if (blockIdx.x == 0 && tid == 0) *cd.allones = 1;  // cleared by k3_resolve_c unless every chunk is all ones
+    __syncthreads();
+    bool g = false, p = true;
+    if (real) {
+        const u64 Hin = Hs[tid - 1];
+        acc = Hin;
+        bool ones = true;
+        u64 wi = s_begin >> 6, wv = 0;
+        u32 bo = (u32)(s_begin & 63);
+#pragma unroll
+        for (u32 d = 0; d < PA_CARRY_D; d++) {
+            acc += z[d];
+            const u64 mask = (1ULL << bd[d]) - 1;
+            const u64 bits = (u64)acc & mask;
+            ones = ones && (bits == mask);
+            acc >>= bd[d];
+            wv |= bits << bo;
+            const u32 nb = bo + bd[d];
+            if (nb >= 64) {
+                atomicOr(y + wi, wv);
+                wi++;
+                wv = (nb > 64) ? (bits >> (64 - bo)) : 0;
+                bo = nb - 64;
+            } else {
+                bo = nb;
+            }
+        }
+        if (bo) atomicOr(y + wi, wv);
+        g = (u64)acc != Ht;  // acc == H_t + (carry out of adding H_{t-1})
+        p = !g && ones;
+        cd.state[cq] = (unsigned char)((g ? 1 : 0) | (p ? 2 : 0));
+    }
+    pdl_trigger();
+    const unsigned gm = __ballot_sync(0xFFFFFFFFu, g), pm = __ballot_sync(0xFFFFFFFFu, p);
+    if (lane == 0) {
+        wg[warp] = (unsigned)((((u64)(gm | pm)) + gm) >> 32);
+        wp[warp] = (pm == 0xFFFFFFFFu);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned Gc = 0, Pc = 1;
+        for (u32 q = 0; q < 8; q++) {
+            Gc = wg[q] | (wp[q] & Gc);
+            Pc = wp[q] & Pc;
+        }
+        cd.cta_state[blockIdx.x] = (unsigned char)(Gc | (Pc << 1));
+    }
+}
+
+// Generate / propagate of the states [lo, hi) composed in order, by the CTA
+// (256 threads): (G, P) with G = carry out given no carry in, P = a carry in
+// passes through.  Every thread gets the result.
+__device__ __forceinline__ void fold_states(const unsigned char *__restrict__ st, u32 lo, u32 hi, unsigned &Gout,
+                                            unsigned &Pout, unsigned *wG, unsigned *wP) {
+    const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const u32 n = hi > lo ? hi - lo : 0, per = (n + 255) / 256;
+    const u32 b0 = lo + min(tid * per, n), b1 = lo + min(tid * per + per, n);
+    unsigned G = 0, P = 1;
+    for (u32 q = b0; q < b1; q++) {
+        const unsigned v = st[q];
+        G = (v & 1) | (((v >> 1) & 1) & G);
+        P = ((v >> 1) & 1) & P;
+    }
+    const unsigned gm = __ballot_sync(0xFFFFFFFFu, G), pm = __ballot_sync(0xFFFFFFFFu, P);
+    __syncthreads();  // wG / wP may still be read from a previous call
+    if (lane == 0) {
+        wG[warp] = (unsigned)((((u64)(gm | pm)) + gm) >> 32);
+        wP[warp] = (pm == 0xFFFFFFFFu);
+    }
+    __syncthreads();
+    G = 0;
+    P = 1;
+    for (u32 q = 0; q < 8; q++) {
+        G = wG[q] | (wP[q] & G);
+        P = wP[q] & P;
+    }
+    Gout = G;
+    Pout = P;
+}
+
+// Carries between chunks: the CTA's carry-in from the states of the CTAs below
+// it (and, around the ring, the carry out of the top with none in -- the
+// end-around carry of the Mersenne fold), then per chunk from the chunk states,
+// and the chunks receiving a carry increment their bit range.
+template <bool RING>
+__global__ void __launch_bounds__(256) k3_resolve_c(CarryDev cd, u32 nctas, u64 *__restrict__ y) {
+    pdl_wait();
+    __shared__ unsigned wG[8], wP[8], wg[8], wp[8];
+    const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned Gpre, Ppre, Gall = 0, Pall = 1;
+    fold_states(cd.cta_state, 0, blockIdx.x, Gpre, Ppre, wG, wP);
+    if (RING) fold_states(cd.cta_state, 0, nctas, Gall, Pall, wG, wP);
+    const unsigned ewrap = RING ? Gall : 0u;
+    const unsigned cin = Gpre | (Ppre & ewrap);
+    const long long cq = (long long)blockIdx.x * kResolveChunks - 1 + tid;
+    const bool real = tid > 0 && cq >= 0 && (u64)cq < cd.nchunks;
+    const unsigned st = real ? cd.state[cq] : 2u;
+    const unsigned gm = __ballot_sync(0xFFFFFFFFu, st & 1), pm = __ballot_sync(0xFFFFFFFFu, (st >> 1) & 1);
+    if (lane == 0) {
+        wg[warp] = (unsigned)((((u64)(gm | pm)) + gm) >> 32);
+        wp[warp] = (pm == 0xFFFFFFFFu);
+    }
+    __syncthreads();
+    unsigned cw = cin;
+    for (u32 q = 0; q < warp; q++) cw = wg[q] | (wp[q] & cw);
+    const u64 a = gm | pm, sum = a + gm + cw;
+    const bool e = ((sum ^ a ^ gm) >> lane) & 1;
+    pdl_trigger();
+    bool fin_ones = true;
+    if (real) {
+        const u64 j0 = (u64)cq * PA_CARRY_D;
+        const u64 s_lo = min(j0 * cd.ub, cd.G), s_hi = min((j0 + PA_CARRY_D) * cd.ub, cd.G);
+        bool flipping = e;
+        for (u64 wi = s_lo >> 6; (wi << 6) < s_hi; wi++) {
+            const u64 wb = wi << 6;
+            u64 m = ~0ULL;
+            if (s_lo > wb) m &= ~0ULL << (s_lo - wb);
+            if (s_hi < wb + 64) m &= (1ULL << (s_hi - wb)) - 1;
+            const u64 orig = y[wi] & m;
+            u64 flip = 0;
+            if (flipping) {
+                const u64 zeros = ~orig & m;
+                if (zeros) {
+                    const u32 pos = __ffsll((long long)zeros) - 1;
+                    flip = m & ((2ULL << pos) - 1);
+                    flipping = false;
+                } else {
+                    flip = m;
+                }
+                atomicXor(y + wi, flip);
+            }
+            fin_ones = fin_ones && (((orig ^ flip) & m) == m);
+        }
+    }
+    const int all = __syncthreads_and(fin_ones ? 1 : 0);
+    if (tid == 0 && !all) *cd.allones = 0;
+}
+
 // ------------------------------------------------------------------ tables --
 
 // ctw[r C + c] = omega_T^(dir * c bitrev_R(r)) with its Shoup companion; the
@@ -842,18 +1241,21 @@ static size_t col_smem3(const Geo3 &X, bool pair) {
 }
 static size_t row_smem3(const Geo3 &X) { return (size_t)2 * (X.C + (X.C >> 3) + 8) * sizeof(u32); }
 
+// Instantiated shapes.  Transforms up to 2^21 use the primes below 2^28
+// (headroom H = 4), longer ones the primes below 2^30 (H = 2); with R = 2^10
+// for T >= 2^20 the row length fixes H: rows of 2^10, 2^11 (and every shorter
+// transform) H = 4, rows of 2^12 .. 2^14 H = 2.
 template <int MODE>
 static cudaError_t p3_row_attrs(int big) {
     cudaError_t e;
 #define P3_ATTR(f) \
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    P3_ATTR((k3_row_mac<8, 0, MODE>))
-    P3_ATTR((k3_row_mac<16, 0, MODE>))
-    P3_ATTR((k3_row_mac<8, 10, MODE>))
-    P3_ATTR((k3_row_mac<8, 11, MODE>))
-    P3_ATTR((k3_row_mac<8, 12, MODE>))
-    P3_ATTR((k3_row_mac<8, 13, MODE>))
-    P3_ATTR((k3_row_mac<16, 14, MODE>))
+    P3_ATTR((k3_row_mac<8, 0, MODE, 4>))
+    P3_ATTR((k3_row_mac<8, 10, MODE, 4>))
+    P3_ATTR((k3_row_mac<8, 11, MODE, 4>))
+    P3_ATTR((k3_row_mac<8, 12, MODE, 2>))
+    P3_ATTR((k3_row_mac<8, 13, MODE, 2>))
+    P3_ATTR((k3_row_mac<16, 14, MODE, 2>))
 #undef P3_ATTR
     return cudaSuccess;
 }
@@ -869,12 +1271,15 @@ int p3_prepare_kernels() {
     cudaError_t e;
 #define P3_ATTR(f) \
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    P3_ATTR((k3_fwd_col<true, 0, 0>))
-    P3_ATTR((k3_fwd_col<false, 0, 0>))
-    P3_ATTR((k3_fwd_col_all<10, 8, true>))
-    P3_ATTR((k3_fwd_col_all<10, 8, false>))
-    P3_ATTR((k3_inv_col<0, 0>))
-    P3_ATTR((k3_inv_col<10, 8>))
+    P3_ATTR((k3_fwd_col<true, 0, 0, 4>))
+    P3_ATTR((k3_fwd_col<false, 0, 0, 4>))
+    P3_ATTR((k3_fwd_col_all<10, 8, true, 4>))
+    P3_ATTR((k3_fwd_col_all<10, 8, false, 4>))
+    P3_ATTR((k3_fwd_col_all<10, 8, true, 2>))
+    P3_ATTR((k3_fwd_col_all<10, 8, false, 2>))
+    P3_ATTR((k3_inv_col<0, 0, 4>))
+    P3_ATTR((k3_inv_col<10, 8, 4>))
+    P3_ATTR((k3_inv_col<10, 8, 2>))
 #undef P3_ATTR
     if ((e = p3_row_attrs<0>(big)) || (e = p3_row_attrs<1>(big)) || (e = p3_row_attrs<2>(big))) return e;
     done_mask.fetch_or(bit);
@@ -884,6 +1289,17 @@ int p3_prepare_kernels() {
 // Compile-time geometry for the production shapes (R = 2^10, 8-column tiles;
 // rows of 2^10 .. 2^14), runtime geometry otherwise.  pair: both operands of
 // each pair (Eq. 2 / Eq. 4), else the single operands of S.mode.
+template <int H>
+static void p3_fwd_all(const Geo3 &X, const Operands &S, int pairs, u32 *Y, void *stream, bool pair, size_t smem) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (pair)
+        TRACED("p3_fwd_col", X.stage, stream,
+               (launch_pdl(k3_fwd_col_all<10, 8, true, H>, dim3(pairs, X.C / X.tc), dim3(512), smem, s, X, S, Y)));
+    else
+        TRACED("p3_fwd_col", X.stage, stream,
+               (launch_pdl(k3_fwd_col_all<10, 8, false, H>, dim3(pairs, X.C / X.tc), dim3(512), smem, s, X, S, Y)));
+}
+
 int p3_launch_fwd_col(const Geo3 &X, const Operands &S, int pairs, u32 *Y, void *stream, bool pair) {
     if (int e = p3_prepare_kernels()) return e;
     const dim3 grid(X.C / X.tc, pairs, 3);
@@ -891,42 +1307,45 @@ int p3_launch_fwd_col(const Geo3 &X, const Operands &S, int pairs, u32 *Y, void 
     cudaStream_t s = (cudaStream_t)stream;
     const size_t smem_all = smem + (X.rof4R + 64 * 15) * sizeof(uint2);
     if (X.logR == 10 && X.tc == 8 && X.rof4R) {
+        if (X.head == 4)
+            p3_fwd_all<4>(X, S, pairs, Y, stream, pair, smem_all);
+        else
+            p3_fwd_all<2>(X, S, pairs, Y, stream, pair, smem_all);
+    } else {
+        if (X.head != 4) return (int)cudaErrorInvalidValue;  // short transforms use the primes below 2^28
         if (pair)
             TRACED("p3_fwd_col", X.stage, stream,
-                   (launch_pdl(k3_fwd_col_all<10, 8, true>, dim3(pairs, X.C / X.tc), dim3(512), smem_all, s, X, S, Y)));
+                   (launch_pdl(k3_fwd_col<true, 0, 0, 4>, grid, dim3(kColThreads), smem, s, X, S, Y)));
         else
             TRACED("p3_fwd_col", X.stage, stream,
-                   (launch_pdl(k3_fwd_col_all<10, 8, false>, dim3(pairs, X.C / X.tc), dim3(512), smem_all, s, X, S, Y)));
-    } else if (pair) {
-        TRACED("p3_fwd_col", X.stage, stream,
-               (launch_pdl(k3_fwd_col<true, 0, 0>, grid, dim3(kColThreads), smem, s, X, S, Y)));
-    } else {
-        TRACED("p3_fwd_col", X.stage, stream,
-               (launch_pdl(k3_fwd_col<false, 0, 0>, grid, dim3(kColThreads), smem, s, X, S, Y)));
+                   (launch_pdl(k3_fwd_col<false, 0, 0, 4>, grid, dim3(kColThreads), smem, s, X, S, Y)));
     }
     return (int)cudaGetLastError();
 }
 
 template <int MODE>
-static void p3_row_launch(const Geo3 &X, const u32 *Y, u32 *S3, u32 *spec, cudaStream_t s, void *stream) {
+static int p3_row_launch(const Geo3 &X, const u32 *Y, u32 *S3, u32 *spec, cudaStream_t s, void *stream) {
     const dim3 grid(X.R, 3);
     const size_t smem = row_smem3(X);
     const char *name = MODE == 1 ? "p3_row_store" : "p3_row_mac";
-#define P3_ROW(A, L) \
-    TRACED(name, X.stage, stream, (launch_pdl(k3_row_mac<A, L, MODE>, grid, dim3(X.C / A), smem, s, X, Y, S3, spec)))
+#define P3_ROW(A, L, H)                                                                                     \
+    do {                                                                                                    \
+        if (X.head != (u32)(H)) return (int)cudaErrorInvalidValue;                                          \
+        TRACED(name, X.stage, stream,                                                                       \
+               (launch_pdl(k3_row_mac<A, L, MODE, H>, grid, dim3(X.C / A), smem, s, X, Y, S3, spec)));      \
+    } while (0)
     switch (X.logC) {
-    case 10: P3_ROW(8, 10); break;
-    case 11: P3_ROW(8, 11); break;
-    case 12: P3_ROW(8, 12); break;
-    case 13: P3_ROW(8, 13); break;
-    case 14: P3_ROW(16, 14); break;
+    case 10: P3_ROW(8, 10, 4); break;
+    case 11: P3_ROW(8, 11, 4); break;
+    case 12: P3_ROW(8, 12, 2); break;
+    case 13: P3_ROW(8, 13, 2); break;
+    case 14: P3_ROW(16, 14, 2); break;
     default:
-        if (X.C > 8192)
-            P3_ROW(16, 0);
-        else
-            P3_ROW(8, 0);
+        if (X.C > 8192) return (int)cudaErrorInvalidValue;
+        P3_ROW(8, 0, 4);
     }
 #undef P3_ROW
+    return 0;
 }
 
 // mode 0: pairs (spec unused); 1: store the single operands' spectra to
@@ -934,24 +1353,51 @@ static void p3_row_launch(const Geo3 &X, const u32 *Y, u32 *S3, u32 *spec, cudaS
 int p3_launch_row_mac(const Geo3 &X, const u32 *Y, u32 *S3, void *stream, int mode, u32 *spec) {
     if (int e = p3_prepare_kernels()) return e;
     cudaStream_t s = (cudaStream_t)stream;
+    int e = 0;
     if (mode == 0)
-        p3_row_launch<0>(X, Y, S3, spec, s, stream);
+        e = p3_row_launch<0>(X, Y, S3, spec, s, stream);
     else if (mode == 1)
-        p3_row_launch<1>(X, Y, S3, spec, s, stream);
+        e = p3_row_launch<1>(X, Y, S3, spec, s, stream);
     else
-        p3_row_launch<2>(X, Y, S3, spec, s, stream);
-    return (int)cudaGetLastError();
+        e = p3_row_launch<2>(X, Y, S3, spec, s, stream);
+    return e ? e : (int)cudaGetLastError();
 }
 
-int p3_launch_inv_col(const Geo3 &X, u32 *S3, void *stream) {
+int p3_launch_inv_col(const Geo3 &X, u32 *S3, u64 *zero_out, u64 zero_words, void *stream) {
     if (int e = p3_prepare_kernels()) return e;
     const dim3 grid(X.C / X.tc, 3);
     const size_t smem = col_smem3(X, false);
     cudaStream_t s = (cudaStream_t)stream;
-    if (X.logR == 10 && X.tc == 8)
-        TRACED("p3_inv_col", X.stage, stream, (launch_pdl(k3_inv_col<10, 8>, grid, dim3(kColThreads), smem, s, X, S3)));
-    else
-        TRACED("p3_inv_col", X.stage, stream, (launch_pdl(k3_inv_col<0, 0>, grid, dim3(kColThreads), smem, s, X, S3)));
+    if (X.logR == 10 && X.tc == 8) {
+        if (X.head == 4)
+            TRACED("p3_inv_col", X.stage, stream,
+                   (launch_pdl(k3_inv_col<10, 8, 4>, grid, dim3(kColThreads), smem, s, X, S3, zero_out, zero_words)));
+        else
+            TRACED("p3_inv_col", X.stage, stream,
+                   (launch_pdl(k3_inv_col<10, 8, 2>, grid, dim3(kColThreads), smem, s, X, S3, zero_out, zero_words)));
+    } else {
+        if (X.head != 4) return (int)cudaErrorInvalidValue;
+        TRACED("p3_inv_col", X.stage, stream,
+               (launch_pdl(k3_inv_col<0, 0, 4>, grid, dim3(kColThreads), smem, s, X, S3, zero_out, zero_words)));
+    }
+    return (int)cudaGetLastError();
+}
+
+// Fused digit gather and carry of a stage whose chunks are wide (the parallel
+// carry): output bits y zeroed beforehand (by the inverse column pass).
+static int p3_launch_resolve(const Geo3 &X, const u32 *S3, const CarryDev &cd, const u64 *c_src, u64 c_base, u64 *y,
+                             void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    const u32 nctas = (u32)((cd.nchunks + kResolveChunks - 1) / kResolveChunks);
+    if (X.stage == 0) {
+        TRACED("p3_resolve_a", 0, stream,
+               (launch_pdl(k3_resolve_a<true>, dim3(nctas), dim3(256), 0, s, X, S3, cd, c_src, c_base, y)));
+        TRACED("p3_resolve_c", 0, stream, (launch_pdl(k3_resolve_c<true>, dim3(nctas), dim3(256), 0, s, cd, nctas, y)));
+    } else {
+        TRACED("p3_resolve_a", 1, stream,
+               (launch_pdl(k3_resolve_a<false>, dim3(nctas), dim3(256), 0, s, X, S3, cd, c_src, c_base, y)));
+        TRACED("p3_resolve_c", 1, stream, (launch_pdl(k3_resolve_c<false>, dim3(nctas), dim3(256), 0, s, cd, nctas, y)));
+    }
     return (int)cudaGetLastError();
 }
 
@@ -983,11 +1429,15 @@ namespace {
 struct PrimeSet {
     u32 p[3];
     u32 maxlog;  // 2^maxlog divides every p - 1
+    u32 head;    // 2^head p < 2^32: the lazy-reduction headroom of the butterflies
 };
-// The three largest primes below 2^30 with 2^23 | p - 1, and the three below
-// 2^30 with 2^24 | p - 1 (the only ones).
-const PrimeSet kSetA = {{998244353u, 754974721u, 469762049u}, 23};
-const PrimeSet kSetB = {{754974721u, 469762049u, 167772161u}, 24};
+// Transforms up to 2^21: the three largest primes below 2^28 with 2^21 | p - 1
+// (product 2^83.6; values may grow to 16p between reductions).  Up to 2^23:
+// the three largest below 2^30 with 2^23 | p - 1; 2^24: the three below 2^30
+// with 2^24 | p - 1 (the only ones); both reduce to [0, 2p) every stage.
+const PrimeSet kSetA4 = {{257949697u, 249561089u, 230686721u}, 21, 4};
+const PrimeSet kSetA = {{998244353u, 754974721u, 469762049u}, 23, 2};
+const PrimeSet kSetB = {{754974721u, 469762049u, 167772161u}, 24, 2};
 
 u32 powmod(u64 b, u64 e, u32 p) {
     u64 r = 1;
@@ -1035,7 +1485,7 @@ struct Choice {
 // top carry chunk must span >= 64 bits whenever the parallel carry runs.
 bool choose(uint64_t G, uint64_t K, bool ring, Choice *out) {
     for (u32 l = 8; l <= 24; l++) {
-        const PrimeSet &ps = l <= kSetA.maxlog ? kSetA : kSetB;
+        const PrimeSet &ps = l <= kSetA4.maxlog ? kSetA4 : (l <= kSetA.maxlog ? kSetA : kSetB);
         const unsigned __int128 P = (unsigned __int128)ps.p[0] * ps.p[1] * ps.p[2];
         const u64 M = 1ULL << (l - 1);
         const u64 bmin = std::max<u64>(1, (G + M - 1) / M);
@@ -1057,6 +1507,7 @@ bool choose(uint64_t G, uint64_t K, bool ring, Choice *out) {
 
 void geometry(Geo3 &X, const Choice &ch, uint64_t G, uint64_t K, u32 stage) {
     const u32 l = ch.logT;
+    X.head = ch.ps->head;
     X.logT = l;
     X.T = 1ULL << l;
     X.M = X.T / 2;
@@ -1230,7 +1681,7 @@ static void ws_parts(const Geo3 &A, const Geo3 &B, uint64_t k, uint64_t *total_n
     s += 3 * std::max<uint64_t>(2 * k * A.T, 2 * B.T) * 4;  // Y (also the digit vector)
     s += 3 * Tm * 4;                                       // S3
     s += 2 * ((A.G + 63) / 64 + 2) * 8;                    // ybuf, tbuf
-    s += nch * 9 + 2 * (nch / PA_CARRY_T + 1);             // carry state
+    s += nch * 9 + 2 * (nch / kResolveChunks + 2);         // carry state
     s += (4 + k) * sizeof(int);
     *total_no_tables = s;
 }
@@ -1275,8 +1726,8 @@ int p3_plan_create(uint64_t n, uint64_t r, uint32_t gamma, uint64_t k, bool stre
     pl->tbuf = (u64 *)pl->alloc(((gamma + 63) / 64 + 2) * 8, &err);
     pl->H = (u64 *)pl->alloc(nch * 8, &err);
     pl->cstate = (unsigned char *)pl->alloc(nch, &err);
-    pl->cta_state = (unsigned char *)pl->alloc(nch / PA_CARRY_T + 1, &err);
-    pl->cta_cin = (unsigned char *)pl->alloc(nch / PA_CARRY_T + 1, &err);
+    pl->cta_state = (unsigned char *)pl->alloc(nch / kResolveChunks + 2, &err);
+    pl->cta_cin = (unsigned char *)pl->alloc(nch / kResolveChunks + 2, &err);
     pl->flags_bytes = (4 + k) * sizeof(int);
     pl->flags = (int *)pl->alloc(pl->flags_bytes, &err);
     if (!err) err = pl->mem.sync();  // the tables are filled
@@ -1298,6 +1749,13 @@ void p3_plan_query(const P3Plan *pl, uint64_t *len_mmh, uint64_t *len_mh, uint64
 }
 
 const Geo3 *p3_stage(const P3Plan *pl, int stage) { return stage ? &pl->mh : &pl->mmh; }
+
+// The fused digit gather + carry runs where the parallel carry would (enough
+// chunks, each spanning >= 64 bits); smaller vectors take the digit kernel and
+// the one-CTA carry.
+static bool p3_fused_carry(const Geo3 &X, const CarryDev &cd) {
+    return cd.nchunks >= PA_CARRY_T && X.b * PA_CARRY_D >= 64;
+}
 
 static CarryDev p3_carry_dev(P3Plan *pl, const Geo3 &X, bool ring, int *allones) {
     CarryDev cd;
@@ -1335,13 +1793,18 @@ static int mmh_impl(P3Plan *pl, const u64 *key, const u64 *seed, u64 *y, bool ca
     const Geo3 &X = pl->mmh;
     if ((e = p3_launch_fwd_col(X, ops, (int)pl->k, pl->Y, stream, !prep))) return e;
     if ((e = p3_launch_row_mac(X, pl->Y, pl->S3, stream, prep ? 2 : 0, prep ? pl->spec_a : nullptr))) return e;
-    if ((e = p3_launch_inv_col(X, pl->S3, stream))) return e;
     const CarryDev cd = p3_carry_dev(pl, X, true, pl->flags + 1);
-    u64 *z = (u64 *)pl->Y;
     const u64 npad = cd.nchunks * PA_CARRY_D;
     const u64 ywords = (pl->gamma + 63) / 64;
-    if ((e = p3_launch_digits(X, pl->S3, z, npad, nullptr, 0, y, ywords, stream))) return e;
-    if ((e = launch_carry_chunks(cd, npad, X.b * PA_CARRY_D >= 64, 0, z, y, ywords, stream, true, true))) return e;
+    if (p3_fused_carry(X, cd)) {
+        if ((e = p3_launch_inv_col(X, pl->S3, y, ywords, stream))) return e;
+        if ((e = p3_launch_resolve(X, pl->S3, cd, nullptr, 0, y, stream))) return e;
+    } else {
+        u64 *z = (u64 *)pl->Y;
+        if ((e = p3_launch_inv_col(X, pl->S3, nullptr, 0, stream))) return e;
+        if ((e = p3_launch_digits(X, pl->S3, z, npad, nullptr, 0, y, ywords, stream))) return e;
+        if ((e = launch_carry_chunks(cd, npad, X.b * PA_CARRY_D >= 64, 0, z, y, ywords, stream, true, true))) return e;
+    }
     if (canonical && (e = launch_canonical_zero(pl->flags + 1, y, ywords, stream, true))) return e;
     return 0;
 }
@@ -1364,15 +1827,20 @@ static int mh_impl(P3Plan *pl, const u64 *seed, u64 *out, int *status, void *str
     const Geo3 &X = pl->mh;
     if ((e = p3_launch_fwd_col(X, ops, 1, pl->Y, stream, !prep))) return e;
     if ((e = p3_launch_row_mac(X, pl->Y, pl->S3, stream, prep ? 2 : 0, prep ? pl->spec_b : nullptr))) return e;
-    if ((e = p3_launch_inv_col(X, pl->S3, stream))) return e;
     const CarryDev cd = p3_carry_dev(pl, X, false, pl->flags + 2);
-    u64 *z = (u64 *)pl->Y;
     const u64 npad = cd.nchunks * PA_CARRY_D;
     const u64 twords = (pl->gamma + 63) / 64;
-    if ((e = p3_launch_digits(X, pl->S3, z, npad, seed, (pl->k + 1) * (u64)pl->gamma, pl->tbuf, twords, stream)))
-        return e;
-    if ((e = launch_carry_chunks(cd, npad, X.b * PA_CARRY_D >= 64, 1, z, pl->tbuf, twords, stream, true, true)))
-        return e;
+    const u64 c_base = (pl->k + 1) * (u64)pl->gamma;
+    if (p3_fused_carry(X, cd)) {
+        if ((e = p3_launch_inv_col(X, pl->S3, pl->tbuf, twords, stream))) return e;
+        if ((e = p3_launch_resolve(X, pl->S3, cd, seed, c_base, pl->tbuf, stream))) return e;
+    } else {
+        u64 *z = (u64 *)pl->Y;
+        if ((e = p3_launch_inv_col(X, pl->S3, nullptr, 0, stream))) return e;
+        if ((e = p3_launch_digits(X, pl->S3, z, npad, seed, c_base, pl->tbuf, twords, stream))) return e;
+        if ((e = launch_carry_chunks(cd, npad, X.b * PA_CARRY_D >= 64, 1, z, pl->tbuf, twords, stream, true, true)))
+            return e;
+    }
     if ((e = launch_extract(pl->tbuf, pl->gamma, pl->r, pl->flags, pl->k, out, status, stream, true))) return e;
     return 0;
 }

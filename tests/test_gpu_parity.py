@@ -117,10 +117,12 @@ def test_reload_on_all_ones_slice_1024_row_columns(backend):
         assert st == oracle.ORA_RELOAD and not out.any()
 
 
-def test_zero_mmh_value_and_all_ones_representation():
+@pytest.mark.parametrize("gamma", [44497, 1257787])
+def test_zero_mmh_value_and_all_ones_representation(gamma):
     """Seeds that make y = 0: a = 0, and a pair with a_2 = -a_1, x_2 = x_1 (the
-    carry ring may land on the all-ones representation of 0)."""
-    gamma = 44497
+    carry ring may land on the all-ones representation of 0); at gamma = 44497
+    the three-prime plan resolves carries in one CTA, at 1257787 in the fused
+    multi-CTA pass."""
     n, r = 2 * gamma, 1000
     plan = _plan(n, r, gamma)  # k and the seed layout (both backends are checked below)
     k = plan.k
