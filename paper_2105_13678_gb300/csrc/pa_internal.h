@@ -179,6 +179,10 @@ struct Geo3 {
     u32 rof4R;      // forward R table: offset of the 4-stage first round (15 twiddles per lo), 0: none
     u32 rof4Ri;     // inverse R table: the same 4-stage round with inverse twiddles, 0: none
     const uint2 *ctw[3], *ictw[3];  // T entries, [r][c]: omega_T^(+-c bitrev_R(r))
+    // R = 2^10: the forward ctw of the last column round (rows 8 g + m, m < 8)
+    // as A[g][c] = omega_T^(c bitrev_7(g)) (128 C entries) times
+    // B[c][m] = omega_T^(128 c bitrev_3(m)) (8 C entries)
+    const uint2 *ctwA[3], *ctwB[3];
 };
 
 constexpr u32 PA_CARRY_D = 8;      // digits per thread chunk

@@ -365,10 +365,15 @@ __device__ __forceinline__ u32 digit_raw(const Geo3 &X, const Desc &d, u64 pos, 
 // ------------------------------------------------------------ column pass --
 
 // LL, TC: log2 R and the tile width when fixed at compile time (0: from X).
-template <int NS, bool PAIR, bool FIRST, bool LAST, int LL, int TC, bool TS = false, int H = 2>
+// SPLIT (the last round of k3_fwd_col_all: stride 1, R = 2^10, 512 threads):
+// the inter-pass twiddle of row 8 g + m is A[g][c] -- loaded by the caller a
+// round early, one per task (apre) -- times the staged sB[c][m].
+template <int NS, bool PAIR, bool FIRST, bool LAST, int LL, int TC, bool TS = false, int H = 2, bool SPLIT = false>
 __device__ __forceinline__ void fwd3_round(const Geo3 &X, u32 j, const Desc &dx, const Desc &da, u32 *__restrict__ smx,
                                            u32 *__restrict__ sma, u32 *__restrict__ Yx, u32 *__restrict__ Ya, u32 c0,
-                                           u32 s0, u32 rd, bool &ones, const uint2 *__restrict__ stw = nullptr) {
+                                           u32 s0, u32 rd, bool &ones, const uint2 *__restrict__ stw = nullptr,
+                                           const uint2 *__restrict__ sB = nullptr, uint2 apre0 = uint2{},
+                                           uint2 apre1 = uint2{}) {
     const u32 l = LL ? (u32)LL : X.logR, tc = TC ? (u32)TC : X.tc, p = X.p[j];
     const u32 sh = l - s0 - NS, stride = 1u << sh;
     const u32 ntask = ((1u << l) >> NS) * tc;
@@ -383,10 +388,12 @@ __device__ __forceinline__ void fwd3_round(const Geo3 &X, u32 j, const Desc &dx,
         const u32 a0 = pxc(base * tc + c);
         const u64 e0 = (u64)base * X.C + c0 + c;
         u32 vx[8], va[8];
-        uint2 ct[LAST ? 8 : 1];
-        if (LAST) {  // inter-pass twiddles first: their L2 latency overlaps the round's arithmetic
+        uint2 ct[(LAST && !SPLIT) ? 8 : 1];
+        if (LAST && SPLIT) {
+            ct[0] = task >= blockDim.x ? apre1 : apre0;
+        } else if (LAST) {  // inter-pass twiddles first: their L2 latency overlaps the round's arithmetic
 #pragma unroll
-            for (int m = 0; m < (1 << NS); m++) ct[LAST ? m : 0] = __ldg(X.ctw[j] + e0 + m * dY);
+            for (int m = 0; m < (1 << NS); m++) ct[(LAST && !SPLIT) ? m : 0] = __ldg(X.ctw[j] + e0 + m * dY);
         }
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
@@ -408,10 +415,15 @@ __device__ __forceinline__ void fwd3_round(const Geo3 &X, u32 j, const Desc &dx,
         if (PAIR) dif3<NS, LAST, FIRST, TS, H, LAST ? 0 : 2>(va, rt, p);
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
-            if (LAST) {
+            if (LAST && SPLIT) {
+                const u64 e = e0 + m * dY;
+                const uint2 bm = sB[c * 8 + m];
+                Yx[e] = shoup(shoup(vx[m], bm, p), ct[0], p);
+                if (PAIR) Ya[e] = shoup(shoup(va[m], bm, p), ct[0], p);
+            } else if (LAST) {
                 // position r holds column frequency bitrev(r): times omega_T^(c bitrev(r))
                 const u64 e = e0 + m * dY;
-                const uint2 t = ct[LAST ? m : 0];
+                const uint2 t = ct[(LAST && !SPLIT) ? m : 0];
                 Yx[e] = shoup(vx[m], t, p);
                 if (PAIR) Ya[e] = shoup(va[m], t, p);
             } else {
@@ -487,12 +499,11 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
     constexpr u32 D64 = 64;
     u32 rx[8], ra[8];
     {
-        const u64 e0 = (u64)lo * X.C + c0 + c;
+        const u64 P0 = ((u64)lo * X.C + c0 + c) * X.b, stride = (u64)D64 * X.C * X.b;
 #pragma unroll
         for (u32 m = 0; m < 8; m++) {
-            const u64 pos = (e0 + (u64)(m * D64) * X.C) * X.b;
-            rx[m] = digit_raw(X, dx, pos, ones);
-            if (PAIR) ra[m] = digit_raw(X, da, pos, ones);
+            rx[m] = digit_raw(X, dx, P0 + m * stride, ones);
+            if (PAIR) ra[m] = digit_raw(X, da, P0 + m * stride, ones);
         }
     }
     const u32 a0 = pxc(lo * TC + c);
@@ -503,9 +514,11 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
         const uint2 red = X.red[j];
         const bool raw = (1ULL << X.b) <= 2ULL * p;  // b-bit digits already lie in [0, 2p)
         u32 *Yx = Y + ((u64)j * 2 * X.K + i) * X.T, *Ya = Y + ((u64)j * 2 * X.K + X.K + i) * X.T;
+        uint2 *sB = stw + X.rof4R + 64 * 15;  // this tile's split inter-pass twiddles B[c][m]
         {
             const u32 ntw = X.rof4R + 64 * 15;  // standard rounds, then the 4-stage first round
             for (u32 q = threadIdx.x; q < ntw; q += NTH) stw[q] = __ldg(X.twR[j] + q);
+            if (threadIdx.x < 8 * TC) sB[threadIdx.x] = __ldg(X.ctwB[j] + (u64)c0 * 8 + threadIdx.x);
             __syncthreads();
         }
         const uint2 *rt = stw + X.rof4R + lo * 15;
@@ -526,10 +539,15 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
             for (u32 m = 0; m < 16; m++) sma[a0 + m * dsm] = v[m];
         }
         __syncthreads();
+        // the last round's A twiddles of this thread's two tasks (rows 8 g + m,
+        // g = lo and lo + 64), loaded now so that round 2 hides their latency
+        const uint2 apre0 = __ldg(X.ctwA[j] + (u64)lo * X.C + c0 + c);
+        const uint2 apre1 = __ldg(X.ctwA[j] + (u64)(lo + 64) * X.C + c0 + c);
         // stages 4-6 and 7-9: the standard partition's rounds 2 and 3
         fwd3_round<3, PAIR, false, false, LL, TC, true, H>(X, j, dx, da, smx, sma, Yx, Ya, c0, 4, 2, ones, stw);
         __syncthreads();
-        fwd3_round<3, PAIR, false, true, LL, TC, true, H>(X, j, dx, da, smx, sma, Yx, Ya, c0, 7, 3, ones, stw);
+        fwd3_round<3, PAIR, false, true, LL, TC, true, H, true>(X, j, dx, da, smx, sma, Yx, Ya, c0, 7, 3, ones, stw, sB,
+                                                                  apre0, apre1);
         __syncthreads();
     }
     pdl_trigger();
@@ -989,6 +1007,8 @@ __global__ void __launch_bounds__(256) k3_resolve_a(Geo3 X, const u32 *__restric
         bool need[PA_CARRY_D];
 #pragma unroll
         for (u32 j = 0; j < PA_CARRY_D; j++) need[j] = exists && digit_takes_wrap(X, t0 + j, w, off, D);
+        // a wrap none of the CTA's digits takes is skipped (validity falls with the digit index)
+        if (!__syncthreads_or(need[0] ? 1 : 0)) continue;
 #pragma unroll
         for (u32 j = 0; j < PA_CARRY_D + 2; j++) {
             const long long e = j < PA_CARRY_D ? (long long)(t0 + off + j) : (long long)(t0 + off) - (long long)(j - 7);
@@ -998,6 +1018,11 @@ __global__ void __launch_bounds__(256) k3_resolve_a(Geo3 X, const u32 *__restric
             q2[j] = ld ? __ldg(S3 + 2 * X.T + e) : 0u;
         }
         auto pieces = [&](u32 j, u32 &c0, u32 &c1, u64 &c2) {
+            if (!(j < PA_CARRY_D ? need[j] : (own_prev && need[0]))) {  // no digit of this thread takes them
+                c0 = c1 = 0;
+                c2 = 0;
+                return;
+            }
             const unsigned __int128 V = crt_combine(X, q0[j], q1[j], q2[j]);
             const u64 mask = (1ULL << b) - 1;
             c0 = (u32)((u64)V & mask);
@@ -1230,6 +1255,23 @@ __global__ void k3_fill_ctw(u32 logR, u32 logC, u32 h, const u32 *__restrict__ l
     }
 }
 
+// The split inter-pass twiddles of R = 2^10 plans: out[r C + c] =
+// omega_T^(c bitrev_7(r)) for r < 128 (A), or out[c 8 + m] =
+// omega_T^(128 c bitrev_3(m)) (B), with Shoup companions.
+__global__ void k3_fill_split(u32 logC, u32 logT, u32 h, bool b_table, const u32 *__restrict__ lo,
+                              const u32 *__restrict__ hi, u32 p, uint2 *__restrict__ out) {
+    const u64 T = 1ULL << logT, C = 1ULL << logC, n = (b_table ? 8 : 128) * C;
+    for (u64 idx = (u64)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (u64)gridDim.x * blockDim.x) {
+        u64 e;
+        if (b_table)
+            e = (128 * (idx >> 3) * brev((u32)(idx & 7), 3)) & (T - 1);
+        else
+            e = ((idx & (C - 1)) * brev((u32)(idx >> logC), 7)) & (T - 1);
+        const u32 w = (u32)(((u64)__ldg(lo + (e & ((1ULL << h) - 1))) * __ldg(hi + (e >> h))) % p);
+        out[idx] = make_uint2(w, (u32)(((u64)w << 32) / p));
+    }
+}
+
 }  // namespace p3
 
 // ---------------------------------------------------------------- launchers --
@@ -1305,7 +1347,7 @@ int p3_launch_fwd_col(const Geo3 &X, const Operands &S, int pairs, u32 *Y, void 
     const dim3 grid(X.C / X.tc, pairs, 3);
     const size_t smem = col_smem3(X, pair);
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t smem_all = smem + (X.rof4R + 64 * 15) * sizeof(uint2);
+    const size_t smem_all = smem + (X.rof4R + 64 * 15 + 8 * 8) * sizeof(uint2);
     if (X.logR == 10 && X.tc == 8 && X.rof4R) {
         if (X.head == 4)
             p3_fwd_all<4>(X, S, pairs, Y, stream, pair, smem_all);
@@ -1419,6 +1461,12 @@ int p3_launch_digits(const Geo3 &X, const u32 *S3, u64 *z, u64 npad, const u64 *
 
 int p3_launch_fill_ctw(u32 logR, u32 logC, u32 h, const u32 *lo, const u32 *hi, u32 p, uint2 *out, void *stream) {
     k3_fill_ctw<<<152 * 8, 256, 0, (cudaStream_t)stream>>>(logR, logC, h, lo, hi, p, out);
+    return (int)cudaGetLastError();
+}
+
+static int p3_launch_fill_split(u32 logC, u32 logT, u32 h, bool b_table, const u32 *lo, const u32 *hi, u32 p,
+                                uint2 *out, void *stream) {
+    k3_fill_split<<<152 * 2, 256, 0, (cudaStream_t)stream>>>(logC, logT, h, b_table, lo, hi, p, out);
     return (int)cudaGetLastError();
 }
 
@@ -1544,7 +1592,7 @@ std::vector<uint2> round_table(u32 w, u32 l, u32 p, u32 *rof) {
     return t;
 }
 
-uint64_t table_bytes(const Geo3 &X) { return 3ULL * (4 * X.R + 4 * X.C + 2 * X.T) * sizeof(uint2); }
+uint64_t table_bytes(const Geo3 &X) { return 3ULL * (4 * X.R + 4 * X.C + 2 * X.T + 136 * X.C) * sizeof(uint2); }
 
 }  // namespace
 
@@ -1596,6 +1644,8 @@ int build_tables(P3Plan *pl, Geo3 &X, const PrimeSet &ps, const Geo3 *other) {
             X.itwC[j] = other->itwC[j];
             X.ctw[j] = other->ctw[j];
             X.ictw[j] = other->ictw[j];
+            X.ctwA[j] = other->ctwA[j];
+            X.ctwB[j] = other->ctwB[j];
         }
         for (int rd = 0; rd < 6; rd++) {
             X.rofR[rd] = other->rofR[rd];
@@ -1655,6 +1705,15 @@ int build_tables(P3Plan *pl, Geo3 &X, const PrimeSet &ps, const Geo3 *other) {
             pl->mem.upload(dlo, lo.data(), lo.size() * 4, &err);
             pl->mem.upload(dhi, hi.data(), hi.size() * 4, &err);
             if (!err && p3_launch_fill_ctw(X.logR, X.logC, h, dlo, dhi, p, dT, pl->mem.stream)) err = PA_ERR_CUDA;
+            if (!err && dir == 0 && X.logR == 10) {
+                uint2 *dA = (uint2 *)pl->alloc(128ULL * X.C * sizeof(uint2), &err);
+                uint2 *dB = (uint2 *)pl->alloc(8ULL * X.C * sizeof(uint2), &err);
+                if (!err && (p3_launch_fill_split(X.logC, X.logT, h, false, dlo, dhi, p, dA, pl->mem.stream) ||
+                             p3_launch_fill_split(X.logC, X.logT, h, true, dlo, dhi, p, dB, pl->mem.stream)))
+                    err = PA_ERR_CUDA;
+                X.ctwA[j] = dA;
+                X.ctwB[j] = dB;
+            }
             if (err) break;
             (dir ? X.itwR : X.twR)[j] = dR;
             (dir ? X.itwC : X.twC)[j] = dC;
