@@ -423,6 +423,10 @@ def run_gb300(args):
         except Exception as e:  # noqa: BLE001
             line["paper_points"] = {"error": repr(e)}
         try:
+            line["tensor_core"] = run_tc_probe(n, plan.gamma, plan.k, total_ms / args.steps)
+        except Exception as e:  # noqa: BLE001
+            line["tensor_core"] = {"error": repr(e)}
+        try:
             line["comparator"] = run_modular_hash()
         except Exception as e:  # noqa: BLE001
             line["comparator"] = {"error": repr(e)}
@@ -615,6 +619,25 @@ def run_sweep(points=SWEEP_POINTS, steps: int = 5):
         plan.close()
         del dk, ds, do
     return out
+
+
+def run_tc_probe(n: int, gamma: int, k: int, block_ms: float):
+    """The tensor-core alternative (exact limb convolution on int8 tensor cores),
+    decided by measurement: mma.sync m16n8k32 int8 throughput on this GPU (GB300
+    has no int8 tcgen05.mma kind), and what the block's k + 1 gamma-bit
+    products would cost as 8-bit-limb convolutions (2 L^2 multiply-adds for L
+    limbs) at that rate, beside the NTT block time."""
+    from paper_2105_13678_gb300 import _lib
+    best = max(_lib.tc_int8_rate(20000, c)[0] for c in (2, 4, 8))
+    limbs = (gamma + 7) // 8
+    macs = (k + 1) * 2 * limbs ** 2
+    est_ms = 2 * macs / (best * 1e12) * 1e3
+    return {"int8_mma_sync_tops": round(best, 1), "tcgen05_int8": "not available on sm_103a (ptxas: .kind::i8 not "
+            "supported)", "limb_conv_int8_ops_per_block": float(2 * macs),
+            "limb_conv_ms_per_block_at_measured_rate": round(est_ms, 3), "ntt_ms_per_block": round(block_ms, 4),
+            "ntt_advantage": round(est_ms / block_ms, 1),
+            "int8_ops_per_input_bit": round(2 * macs / n, 1),
+            "workload": f"n={n:.3g}, gamma={gamma}, {k + 1} products of gamma bits (8-bit limbs)"}
 
 
 def run_modular_hash(steps: int = 5):

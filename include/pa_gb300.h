@@ -257,6 +257,20 @@ int pa_plan_geometry(const pa_plan_t *plan, int stage, uint32_t *log_r, uint32_t
  * Asynchronous. */
 int pa_selftest_field(const uint64_t *a, const uint64_t *b, uint64_t *out, uint64_t n, void *stream);
 
+/* ---- tensor-core limb convolution (the alternative arithmetic, measured) ---
+ * An exact n-limb product as int8 matrix products costs 2 n^2 multiply-adds
+ * (32-limb blocks: Toeplitz(B_q) (64 x 32) times columns A_p); GB300 has no
+ * int8 tcgen05.mma kind, so these use the warp-level mma.sync m16n8k32.
+ * pa_tc_limbconv_tile: for t < ntiles, out[t] (64 x 8 int32, row-major) =
+ *   Toeplitz(bq[t]) x a[t], bq[t] 32 limbs, a[t] 8 columns of 32 limbs
+ *   (a[t][c * 32 + j]); device pointers; asynchronous.  Entry i of column c is
+ *   the convolution of bq[t] with column c at index i (exact).
+ * pa_tc_int8_rate: int8 multiply-add throughput of mma.sync on this device
+ *   (ctas_per_sm x SMs CTAs of 8 warps, `iters` rounds of 8 independent
+ *   products each, timed with CUDA events); blocking. */
+int pa_tc_limbconv_tile(const uint8_t *bq, const uint8_t *a, int32_t *out, int ntiles, void *stream);
+int pa_tc_int8_rate(uint64_t iters, uint32_t ctas_per_sm, double *tops, double *ms);
+
 /* Failure injection for tests of the error paths (host side only; no device
  * work fails): of the library's next device and pinned host allocations,
  * `skip` succeed and the following `count` fail as if the memory were

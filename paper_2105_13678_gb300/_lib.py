@@ -86,6 +86,9 @@ SIGNATURES = {
     "pa_trace_enable": (ctypes.c_int, [ctypes.c_int]),
     "pa_trace_collect": (ctypes.c_int, [ctypes.POINTER(pa_trace_entry), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "pa_trace_select": (ctypes.c_int, [ctypes.c_char_p]),
+    "pa_tc_limbconv_tile": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
+    "pa_tc_int8_rate": (ctypes.c_int, [_u64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]),
     "pa_debug_fail_allocs": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32]),
     "pa_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pa_version": (ctypes.c_char_p, []),
@@ -315,3 +318,10 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def tc_int8_rate(iters: int = 20000, ctas_per_sm: int = 4):
+    """(achieved int8 TOPS of mma.sync m16n8k32, ms) on the current device."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    check(lib().pa_tc_int8_rate(iters, ctas_per_sm, ctypes.byref(t), ctypes.byref(ms)), "pa_tc_int8_rate")
+    return float(t.value), float(ms.value)
