@@ -57,9 +57,13 @@ typedef struct pa_params {
                               with params != NULL, 0 means gamma > r strictly */
     uint32_t tune;         /* 1: time the candidate four-step splits and column
                               tiles of each transform shape on this plan's
-                              workspace at pa_plan time and keep the fastest
-                              (cached per process); 0: default geometry.
-                              The output bits do not depend on it.           */
+                              workspace at pa_plan time and keep the fastest;
+                              with backend AUTO also build both backends and
+                              keep the one whose hash measured faster.  Cached
+                              per process (pa_tune_cache_save / _load carry it
+                              across processes); 0: default geometry and the
+                              AUTO rule below.  The output bits do not depend
+                              on it.                                          */
     uint32_t backend;      /* PA_BACKEND_AUTO (0), PA_BACKEND_GOLDILOCKS or
                               PA_BACKEND_P3; the output bits do not depend on it */
     uint32_t reserved[4];  /* must be zero */
@@ -256,6 +260,14 @@ int pa_plan_geometry(const pa_plan_t *plan, int stage, uint32_t *log_r, uint32_t
  * mod q, canonical; a, b, out (4n words) are device arrays, any 64-bit inputs.
  * Asynchronous. */
 int pa_selftest_field(const uint64_t *a, const uint64_t *b, uint64_t *out, uint64_t n, void *stream);
+
+/* Tuning results (pa_params.tune): pa_tune_cache_save writes every cached
+ * geometry and backend decision of this process to a text file and returns the
+ * number of entries; pa_tune_cache_load adds a file's entries to the cache and
+ * returns their number, or PA_ERR_INVALID if the file cannot be read or holds
+ * a malformed or invalid entry (the valid ones are kept).  Host-only. */
+int pa_tune_cache_save(const char *path);
+int pa_tune_cache_load(const char *path);
 
 /* ---- tensor-core limb convolution (the alternative arithmetic, measured) ---
  * An exact n-limb product as int8 matrix products costs 2 n^2 multiply-adds

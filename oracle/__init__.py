@@ -59,6 +59,7 @@ def _load():
             lib.ora_mh.argtypes = [_u64p, _u64p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, _u64p]
             lib.ora_mersenne_at.restype = ctypes.c_uint32
             lib.ora_set_karatsuba_threshold.argtypes = [ctypes.c_size_t]
+            lib.ora_toeplitz.argtypes = [_u64p, ctypes.c_uint64, _u64p, ctypes.c_uint64, _u64p]
             _lib = lib
     return _lib
 
@@ -156,3 +157,18 @@ def mod_mersenne(s: int, gamma: int) -> int:
 
 def set_karatsuba_threshold(limbs: int) -> None:
     _load().ora_set_karatsuba_threshold(limbs)
+
+
+def toeplitz(key: np.ndarray, n: int, seed: np.ndarray, r: int) -> np.ndarray:
+    """Toeplitz-hashing PA (the comparison scheme of Sec. 1 / Table 1): z = T x
+    over GF(2), T[i][j] = s[i - j + n - 1], s of n + r - 1 bits.  Returns the
+    r output bits as words."""
+    lib = _load()
+    key = np.ascontiguousarray(key, dtype=np.uint64)
+    seed = np.ascontiguousarray(seed, dtype=np.uint64)
+    assert key.size >= words(n) and seed.size >= words(n + r - 1)
+    out = np.zeros(words(r), dtype=np.uint64)
+    rc = lib.ora_toeplitz(_ptr(key), n, _ptr(seed), r, _ptr(out))
+    if rc < 0:
+        raise RuntimeError(f"oracle error {rc}")
+    return out

@@ -355,3 +355,25 @@ int ora_mh(const uint64_t *y, const uint64_t *seed, uint32_t gamma, uint64_t k, 
 }
 
 void ora_set_karatsuba_threshold(size_t limbs) { g_kara_threshold = limbs < 4 ? 4 : limbs; }
+
+/* ----------------------------------------------------- Toeplitz hashing -- */
+/* The comparison scheme of Sec. 1 / Table 1: Toeplitz-hashing privacy
+ * amplification, z = T x over GF(2) with T the r x n Toeplitz matrix whose
+ * entries are constant along diagonals, T[i][j] = s[i - j + n - 1], drawn
+ * from a seed s of n + r - 1 bits (s[0] is T[0][n - 1], s[n + r - 2] is
+ * T[r - 1][0]).  Reading used: that diagonal convention (the paper fixes
+ * none; any fixed one gives the same family); key, seed and output bit order
+ * as everywhere (bit t of a string is bit t % 64 of word t / 64).  Plain
+ * double loop: z_i = XOR_j T[i][j] x_j. */
+static int bit_at(const uint64_t *w, uint64_t t) { return (int)((w[t >> 6] >> (t & 63)) & 1u); }
+
+int ora_toeplitz(const uint64_t *key, uint64_t n, const uint64_t *seed, uint64_t r, uint64_t *out) {
+    if (!key || !seed || !out || n == 0 || r == 0) return ORA_ERR_INVALID;
+    memset(out, 0, words_for(r) * sizeof(uint64_t));
+    for (uint64_t i = 0; i < r; i++) {
+        int acc = 0;
+        for (uint64_t j = 0; j < n; j++) acc ^= bit_at(key, j) & bit_at(seed, i - j + n - 1);
+        if (acc) out[i >> 6] |= 1ULL << (i & 63);
+    }
+    return ORA_OK;
+}

@@ -86,6 +86,8 @@ SIGNATURES = {
     "pa_trace_enable": (ctypes.c_int, [ctypes.c_int]),
     "pa_trace_collect": (ctypes.c_int, [ctypes.POINTER(pa_trace_entry), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "pa_trace_select": (ctypes.c_int, [ctypes.c_char_p]),
+    "pa_tune_cache_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "pa_tune_cache_load": (ctypes.c_int, [ctypes.c_char_p]),
     "pa_tc_limbconv_tile": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
     "pa_tc_int8_rate": (ctypes.c_int, [_u64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)]),

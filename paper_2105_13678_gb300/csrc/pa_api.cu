@@ -314,6 +314,38 @@ static int build_xform(pa_plan_t *pl, Xform &X, uint64_t G, uint64_t K, u32 logR
 // and keeps the fastest.  Results are cached per process.
 static std::mutex g_tune_mu;
 static std::map<std::tuple<uint64_t, uint64_t, uint32_t>, std::pair<u32, u32>> g_tune_cache;
+// Measured backend of tuned AUTO plans, per (gamma, k): PA_BACKEND_GOLDILOCKS or PA_BACKEND_P3.
+static std::map<std::pair<uint32_t, uint64_t>, uint32_t> g_backend_cache;
+
+// Device time of one pa_hash on the plan (synthetic key and seed, best of
+// three after a warm-up, private stream); -1 on failure.
+static float time_plan_ms(pa_plan_t *pl) {
+    const uint64_t kw = (pl->n + 63) / 64, sw = ((pl->k + 2) * (uint64_t)pl->gamma + 63) / 64;
+    DevAlloc scratch;
+    int err = scratch.init(pl->mem.async);
+    uint64_t *buf = (uint64_t *)scratch.take((kw + sw + (pl->r + 63) / 64 + 1) * 8, &err);
+    if (err) return -1.f;
+    cudaStream_t s = scratch.stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float best = -1.f;
+    if (!cudaMemsetAsync(buf, 0x5A, (kw + sw) * 8, s) && !cudaEventCreate(&e0) && !cudaEventCreate(&e1)) {
+        for (int rep = 0; rep < 4; rep++) {
+            if (cudaEventRecord(e0, s) || pa_hash(pl, buf, buf + kw, buf + kw + sw, nullptr, s) ||
+                cudaEventRecord(e1, s) || cudaEventSynchronize(e1)) {
+                best = -1.f;
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && (best < 0 || ms < best)) best = ms;
+        }
+    }
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    scratch.sync();
+    return best;
+}
 
 static int tune_geometry(pa_plan_t *pl, int stage, uint64_t G, uint64_t K, uint32_t l, u32 *logR_out, u32 *tc_out);
 
@@ -406,6 +438,43 @@ int pa::plan_create(uint64_t n_bits, uint64_t r_bits, const pa_params *params, b
     if ((rc = choose_backend(gamma, pl->k, params, l1, &backend))) {
         delete pl;
         return rc;
+    }
+    if (params && params->tune && params->backend == PA_BACKEND_AUTO &&
+        p3_feasible(gamma, pl->k, nullptr, nullptr) == PA_OK) {
+        // tuned AUTO plan: the backend is the one measured faster for this (gamma, k)
+        const auto key = std::make_pair(gamma, pl->k);
+        uint32_t chosen = 0;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_backend_cache.find(key);
+            if (it != g_backend_cache.end()) chosen = it->second;
+        }
+        const uint64_t k = pl->k;
+        delete pl;
+        pa_params pp = *params;
+        if (chosen) {
+            pp.backend = chosen;
+            return plan_create(n_bits, r_bits, &pp, stream_ordered, out);
+        }
+        pa_plan_t *cand[2] = {nullptr, nullptr};
+        float ms[2] = {-1.f, -1.f};
+        const uint32_t be[2] = {PA_BACKEND_P3, PA_BACKEND_GOLDILOCKS};
+        for (int c = 0; c < 2; c++) {
+            pp.backend = be[c];
+            if (plan_create(n_bits, r_bits, &pp, stream_ordered, &cand[c]) == PA_OK) ms[c] = time_plan_ms(cand[c]);
+        }
+        int win = -1;
+        for (int c = 0; c < 2; c++)
+            if (cand[c] && ms[c] >= 0 && (win < 0 || ms[c] < ms[win])) win = c;
+        for (int c = 0; c < 2; c++)
+            if (c != win && cand[c]) pa_plan_destroy(cand[c]);
+        if (win < 0) return cand[0] || cand[1] ? PA_ERR_CUDA : PA_ERR_NOMEM;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_backend_cache[std::make_pair(gamma, k)] = be[win];
+        }
+        *out = cand[win];
+        return PA_OK;
     }
     if (backend == PA_BACKEND_P3) {
         if ((rc = p3_plan_create(n_bits, r_bits, gamma, pl->k, stream_ordered, &pl->p3))) {
@@ -1023,6 +1092,61 @@ int pa_plan_geometry(const pa_plan_t *pl, int stage, uint32_t *log_r, uint32_t *
     *log_c = X.logC;
     *tile_cols = X.tc;
     return PA_OK;
+}
+
+// Tuning results across processes: one line per entry,
+//   "geometry G K logN logR tile"   (four-step split of a Goldilocks transform)
+//   "backend gamma k choice"        (measured backend of tuned AUTO plans)
+int pa_tune_cache_save(const char *path) {
+    if (!path) return PA_ERR_INVALID;
+    FILE *f = fopen(path, "w");
+    if (!f) return PA_ERR_INVALID;
+    int n = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (auto &kv : g_tune_cache) {
+            fprintf(f, "geometry %llu %llu %u %u %u\n", (unsigned long long)std::get<0>(kv.first),
+                    (unsigned long long)std::get<1>(kv.first), std::get<2>(kv.first), kv.second.first, kv.second.second);
+            n++;
+        }
+        for (auto &kv : g_backend_cache) {
+            fprintf(f, "backend %u %llu %u\n", kv.first.first, (unsigned long long)kv.first.second, kv.second);
+            n++;
+        }
+    }
+    return fclose(f) == 0 ? n : PA_ERR_INVALID;
+}
+
+int pa_tune_cache_load(const char *path) {
+    if (!path) return PA_ERR_INVALID;
+    FILE *f = fopen(path, "r");
+    if (!f) return PA_ERR_INVALID;
+    char line[256];
+    int n = 0, bad = 0;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    while (fgets(line, sizeof line, f)) {
+        unsigned long long G, K, k;
+        unsigned l, logR, tc, gamma, choice;
+        if (sscanf(line, "geometry %llu %llu %u %u %u", &G, &K, &l, &logR, &tc) == 5) {
+            if (!geometry_ok(l, logR, tc)) {
+                bad = 1;
+                continue;
+            }
+            g_tune_cache[std::make_tuple((uint64_t)G, (uint64_t)K, (uint32_t)l)] = std::make_pair(logR, tc);
+            n++;
+        } else if (sscanf(line, "backend %u %llu %u", &gamma, &k, &choice) == 3) {
+            if (choice != PA_BACKEND_GOLDILOCKS && choice != PA_BACKEND_P3) {
+                bad = 1;
+                continue;
+            }
+            g_backend_cache[std::make_pair((uint32_t)gamma, (uint64_t)k)] = choice;
+            n++;
+        } else if (line[0] != '\n' && line[0] != '#') {
+            bad = 1;
+        }
+    }
+    fclose(f);
+    return bad ? PA_ERR_INVALID : n;
 }
 
 // Failure injection for tests: of the library's next device (and pinned host)
