@@ -139,6 +139,20 @@ int pa_debug_mmh(pa_plan_t *plan, const uint64_t *key, const uint64_t *seed, uin
  * accept such a plan.  n <= about 1.3e8 bits (one exact n x n-bit product). */
 int pa_mh_plan(uint64_t n_bits, uint64_t r_bits, pa_plan_t **out);
 
+/* Comparison scheme: Toeplitz-hashing PA (the other prior-art family the
+ * paper compares against, Sec. 1 and Table 1, computed with the key split into
+ * segments): z = T x over GF(2), T the r x n Toeplitz matrix
+ * T[i][j] = s[i - j + n - 1] of a seed s of n + r - 1 bits
+ * (ceil((n + r - 1)/64) words).  Key segments and output blocks of
+ * 2^block_log bits (6..22; 0: the smallest power of two >= r, at most 2^22);
+ * each block product is an exact integer convolution of 1-bit digits on the
+ * three-prime transforms of length 4 * 2^block_log, accumulated over the
+ * segments, whose coefficients' parities are the output bits.  Only pa_hash
+ * (status always PA_OK) and pa_hash_batch accept such a plan; pa_plan_info
+ * reports gamma = 0, k = the number of segments, mmh_len = the transform
+ * length.  Device workspace about 96 n bytes. */
+int pa_toeplitz_plan(uint64_t n_bits, uint64_t r_bits, uint32_t block_log, pa_plan_t **out);
+
 /* Seed reuse.  When the same hash seed (a, b, c) serves many blocks,
  * pa_seed_prepare transforms a_1..a_k and b once and keeps their spectra (and
  * a copy of the seed) in the plan: k N_mmh + N_mh 64-bit words (GOLDILOCKS) or

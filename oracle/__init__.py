@@ -60,6 +60,8 @@ def _load():
             lib.ora_mersenne_at.restype = ctypes.c_uint32
             lib.ora_set_karatsuba_threshold.argtypes = [ctypes.c_size_t]
             lib.ora_toeplitz.argtypes = [_u64p, ctypes.c_uint64, _u64p, ctypes.c_uint64, _u64p]
+            lib.ora_toeplitz_bits.argtypes = [_u64p, ctypes.c_uint64, _u64p, ctypes.c_uint64, _u64p, ctypes.c_uint64,
+                                              ctypes.POINTER(ctypes.c_uint8)]
             _lib = lib
     return _lib
 
@@ -169,6 +171,20 @@ def toeplitz(key: np.ndarray, n: int, seed: np.ndarray, r: int) -> np.ndarray:
     assert key.size >= words(n) and seed.size >= words(n + r - 1)
     out = np.zeros(words(r), dtype=np.uint64)
     rc = lib.ora_toeplitz(_ptr(key), n, _ptr(seed), r, _ptr(out))
+    if rc < 0:
+        raise RuntimeError(f"oracle error {rc}")
+    return out
+
+
+def toeplitz_bits(key: np.ndarray, n: int, seed: np.ndarray, r: int, idx) -> np.ndarray:
+    """Output bits z_i of the Toeplitz product for the indices idx (each O(n))."""
+    lib = _load()
+    key = np.ascontiguousarray(key, dtype=np.uint64)
+    seed = np.ascontiguousarray(seed, dtype=np.uint64)
+    ix = np.ascontiguousarray(np.asarray(idx, dtype=np.uint64))
+    out = np.zeros(ix.size, dtype=np.uint8)
+    rc = lib.ora_toeplitz_bits(_ptr(key), n, _ptr(seed), r, _ptr(ix), ix.size,
+                               out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
     if rc < 0:
         raise RuntimeError(f"oracle error {rc}")
     return out

@@ -377,3 +377,17 @@ int ora_toeplitz(const uint64_t *key, uint64_t n, const uint64_t *seed, uint64_t
     }
     return ORA_OK;
 }
+
+/* Selected output bits of the same product: out_bits[q] = z_(idx[q]). */
+int ora_toeplitz_bits(const uint64_t *key, uint64_t n, const uint64_t *seed, uint64_t r, const uint64_t *idx,
+                      uint64_t count, uint8_t *out_bits) {
+    if (!key || !seed || !idx || !out_bits || n == 0 || r == 0) return ORA_ERR_INVALID;
+    for (uint64_t q = 0; q < count; q++) {
+        const uint64_t i = idx[q];
+        if (i >= r) return ORA_ERR_INVALID;
+        int acc = 0;
+        for (uint64_t j = 0; j < n; j++) acc ^= bit_at(key, j) & bit_at(seed, i - j + n - 1);
+        out_bits[q] = (uint8_t)acc;
+    }
+    return ORA_OK;
+}

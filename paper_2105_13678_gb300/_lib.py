@@ -64,6 +64,7 @@ SIGNATURES = {
     "pa_plan": (ctypes.c_int, [_u64, _u64, ctypes.POINTER(pa_params), ctypes.POINTER(_vp)]),
     "pa_plan_info_get": (ctypes.c_int, [_vp, ctypes.POINTER(pa_plan_info)]),
     "pa_mh_plan": (ctypes.c_int, [_u64, _u64, ctypes.POINTER(_vp)]),
+    "pa_toeplitz_plan": (ctypes.c_int, [_u64, _u64, ctypes.c_uint32, ctypes.POINTER(_vp)]),
     "pa_plan_destroy": (ctypes.c_int, [_vp]),
     "pa_hash": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "pa_hash_host": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
@@ -148,12 +149,16 @@ def params(gamma: int = 0, margin: int = 128, tune: bool = False, backend: int =
 
 class Plan:
     """Owns a ``pa_plan_t``: step 0 of Algorithm 1 plus the device workspace.
-    ``modular_hash=True`` builds the comparison scheme (Eq. 4 over the whole key)."""
+    ``modular_hash=True`` builds the comparison scheme (Eq. 4 over the whole key),
+    ``toeplitz=True`` the Toeplitz-hashing comparison scheme."""
 
     def __init__(self, n_bits: int, r_bits: int, gamma: int = 0, margin: int = 128, tune: bool = False,
-                 modular_hash: bool = False, backend: int = BACKEND_AUTO):
+                 modular_hash: bool = False, backend: int = BACKEND_AUTO, toeplitz: bool = False,
+                 block_log: int = 0):
         h = _vp()
-        if modular_hash:
+        if toeplitz:
+            check(lib().pa_toeplitz_plan(n_bits, r_bits, block_log, ctypes.byref(h)), "pa_toeplitz_plan")
+        elif modular_hash:
             check(lib().pa_mh_plan(n_bits, r_bits, ctypes.byref(h)), "pa_mh_plan")
         else:
             p = params(gamma, margin, tune, backend)

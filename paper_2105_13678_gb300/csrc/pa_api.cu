@@ -173,6 +173,7 @@ struct pa_plan_s {
     uint64_t n, r, k;
     uint32_t gamma;
     bool mh_only = false;   // modular-arithmetic hash over the whole key (gamma = n, k = 0)
+    bool toeplitz = false;  // Toeplitz-hashing comparison scheme (three-prime plan in p3)
     P3Plan *p3 = nullptr;   // three-prime backend (pa_p3.cu): owns its own workspace
     Xform mmh, mh;
     DevAlloc mem;           // every device buffer and table of the plan
@@ -574,9 +575,54 @@ int pa_mh_plan(uint64_t n_bits, uint64_t r_bits, pa_plan_t **out) {
     return PA_OK;
 }
 
+// Comparison scheme: Toeplitz hashing, z = T x over GF(2) (Sec. 1, Table 1),
+// output blocks / key segments of 2^block_log bits (0: automatic).
+int pa_toeplitz_plan(uint64_t n_bits, uint64_t r_bits, uint32_t block_log, pa_plan_t **out) {
+    if (!out || n_bits == 0 || r_bits == 0 || r_bits > n_bits) return PA_ERR_INVALID;
+    *out = nullptr;
+    if (block_log == 0) {
+        block_log = 6;
+        while (block_log < 22 && (1ULL << block_log) < r_bits) block_log++;
+    }
+    if (block_log < 6 || block_log > 22) return PA_ERR_INVALID;
+    pa_plan_t *pl = new (std::nothrow) pa_plan_s();
+    if (!pl) return PA_ERR_NOMEM;
+    int rc = pl->mem.init(false);
+    if (!rc) rc = p3_toeplitz_create(n_bits, r_bits, block_log, &pl->p3);
+    if (rc) {
+        delete pl;
+        return rc;
+    }
+    pl->toeplitz = true;
+    pl->n = n_bits;
+    pl->r = r_bits;
+    pl->gamma = 0;
+    uint64_t rb = 0, seg = 0, blk = 0, t1 = 0, t2 = 0, ws = 0;
+    p3_toeplitz_query(pl->p3, &rb, &seg, &blk);
+    p3_plan_query(pl->p3, &t1, &t2, &ws);
+    pl->k = seg;
+    pl->mmh.N = t1;
+    pl->mh.N = 0;
+    pl->ws_bytes = ws;
+    *out = pl;
+    return PA_OK;
+}
+
 int pa_plan_info_get(const pa_plan_t *pl, pa_plan_info *info) {
     if (!pl || !info) return PA_ERR_INVALID;
     memset(info, 0, sizeof(*info));
+    if (pl->toeplitz) {
+        info->n_bits = pl->n;
+        info->r_bits = pl->r;
+        info->k = pl->k;
+        info->key_words = (pl->n + 63) / 64;
+        info->seed_words = (pl->n + pl->r - 1 + 63) / 64;
+        info->out_words = (pl->r + 63) / 64;
+        info->mmh_len = pl->mmh.N;
+        info->workspace_bytes = pl->ws_bytes;
+        info->backend = PA_BACKEND_P3;
+        return PA_OK;
+    }
     info->n_bits = pl->n;
     info->r_bits = pl->r;
     info->gamma = pl->gamma;
@@ -699,6 +745,11 @@ extern "C" {
 
 int pa_hash(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint64_t *out, int *status, void *stream) {
     if (!pl || !key || !seed || !out) return PA_ERR_INVALID;
+    if (pl->toeplitz) {
+        int e = p3_toeplitz_hash(pl->p3, (const u64 *)key, (const u64 *)seed, (u64 *)out, stream);
+        if (!e && status) e = cudaMemsetAsync(status, 0, sizeof(int), (cudaStream_t)stream);
+        return cuda_rc(e);
+    }
     if (pl->mh_only) {
         // Eq. 4 with alpha = n: the key itself is the MH input y
         cudaStream_t s = (cudaStream_t)stream;
@@ -719,7 +770,7 @@ int pa_hash(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint64_t *
 
 int pa_debug_mmh(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint64_t *y, int *status, void *stream) {
     if (!pl || !key || !seed || !y) return PA_ERR_INVALID;
-    if (pl->mh_only) return PA_ERR_INVALID;
+    if (pl->mh_only || pl->toeplitz) return PA_ERR_INVALID;
     if (pl->p3) {
         int e = p3_enqueue_mmh(pl->p3, (const u64 *)key, (const u64 *)seed, (u64 *)y, true, stream);
         if (!e && status)
@@ -743,7 +794,7 @@ static int host_groups(uint64_t k) { return (int)((k + host_group_size(k) - 1) /
 int pa_hash_host_async(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint64_t *out, int *status,
                        void *stream) {
     if (!pl || !key || !seed || !out) return PA_ERR_INVALID;
-    if (pl->mh_only) return PA_ERR_INVALID;
+    if (pl->mh_only || pl->toeplitz) return PA_ERR_INVALID;
     const uint64_t kw = (pl->n + 63) / 64, sw = ((pl->k + 2) * pl->gamma + 63) / 64, ow = (pl->r + 63) / 64;
     const uint64_t g = pl->gamma, k = pl->k;
     const int ng = host_groups(k);
@@ -863,7 +914,7 @@ int pa_hash_host(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint6
 // and y.  The plan keeps a copy of the seed (c is read from it).
 int pa_seed_prepare(pa_plan_t *pl, const uint64_t *seed, void *stream) {
     if (!pl || !seed) return PA_ERR_INVALID;
-    if (pl->mh_only) return PA_ERR_INVALID;
+    if (pl->mh_only || pl->toeplitz) return PA_ERR_INVALID;
     if (pl->p3) {
         const int e = p3_seed_prepare(pl->p3, (const u64 *)seed, stream);  // PA_ERR_* (< 0) or a CUDA error
         return e < 0 ? e : cuda_rc(e);
@@ -902,6 +953,7 @@ int pa_seed_prepare(pa_plan_t *pl, const uint64_t *seed, void *stream) {
 
 int pa_hash_prepared(pa_plan_t *pl, const uint64_t *key, uint64_t *out, int *status, void *stream) {
     if (!pl || !key || !out) return PA_ERR_INVALID;
+    if (pl->toeplitz) return PA_ERR_INVALID;
     if (pl->p3) {
         if (!p3_prepared(pl->p3)) return PA_ERR_INVALID;
         return cuda_rc(p3_hash_prepared(pl->p3, (const u64 *)key, (u64 *)out, status, stream));

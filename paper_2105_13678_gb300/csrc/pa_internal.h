@@ -138,8 +138,13 @@ struct Operands {
     const int *y_zero;  // if *y_zero != 0, y is p itself and reads as 0
     int *reload;        // reload flag + per-slice all-ones counters (Algorithm 1)
     u64 n, gamma, k;
-    int mode;           // pairs: 0 MMH (x_i, a_i), 1 MH (y, b); single: 2 a_i, 3 x_i, 4 b, 5 y
+    int mode;           // pairs: 0 MMH (x_i, a_i), 1 MH (y, b), 6 Toeplitz (x_J, w_IJ);
+                        // single: 2 a_i, 3 x_i, 4 b, 5 y
     u32 pair0;          // first pair / operand handled by the launch (blockIdx.y offset)
+    // Toeplitz (mode 6): key segments of rb bits; the seed, shifted up by rb
+    // zero bits, holds seed_bits bits; the windows of output block blk
+    u64 rb = 0, seed_bits = 0;
+    u32 blk = 0;
 };
 
 // Carry resolution of N digits (value mod 2^G - 1, end-around carry).
@@ -276,6 +281,11 @@ int p3_launch_fill_ctw(u32 logR, u32 logC, u32 h, const u32 *lo, const u32 *hi, 
 
 // Three-prime plans (pa_p3.cu).
 struct P3Plan;
+// Toeplitz-hashing PA (the comparison scheme): z = T x over GF(2) as block
+// products on 1-bit digits, output blocks of 2^rb_log bits.
+int p3_toeplitz_create(uint64_t n, uint64_t r, uint32_t rb_log, P3Plan **out);
+int p3_toeplitz_hash(P3Plan *pl, const u64 *key, const u64 *seed, u64 *out, void *stream);
+void p3_toeplitz_query(const P3Plan *pl, uint64_t *rb, uint64_t *segments, uint64_t *blocks);
 int p3_feasible(uint32_t gamma, uint64_t k, uint32_t *logT_mmh, uint32_t *logT_mh);
 uint64_t p3_plan_bytes(uint32_t gamma, uint64_t k);
 int p3_plan_create(uint64_t n, uint64_t r, uint32_t gamma, uint64_t k, bool stream_ordered, P3Plan **out);

@@ -321,6 +321,17 @@ __device__ __forceinline__ void descs(const Operands &S, u32 i, Desc &dx, Desc &
         da.src = S.seed;
         da.base = (u64)i * S.gamma;
         da.len = S.gamma;
+    } else if (S.mode == 6) {
+        // Toeplitz block (blk, i): key segment i, and the 2 rb - 1 seed bits of
+        // the block's diagonals, starting at n + (blk - i) rb in the shifted seed
+        dx.src = S.key;
+        dx.base = (u64)i * S.rb;
+        const u64 rem = S.n - dx.base;
+        dx.len = rem < S.rb ? rem : S.rb;
+        da.src = S.seed;
+        da.base = S.n + (u64)S.blk * S.rb - (u64)i * S.rb;
+        const u64 avail = S.seed_bits > da.base ? S.seed_bits - da.base : 0;
+        da.len = avail < 2 * S.rb - 1 ? avail : 2 * S.rb - 1;
     } else {
         dx.src = S.y;
         dx.base = 0;
@@ -1240,6 +1251,22 @@ __global__ void __launch_bounds__(256) k3_resolve_c(CarryDev cd, u32 nctas, u64 
     if (tid == 0 && !all) *cd.allones = 0;
 }
 
+// ----------------------------------------------------- Toeplitz parity --
+
+// Output block blk of the Toeplitz product: bit i' is the parity of
+// coefficient rb - 1 + i' of sum_J w_J * x_J (its exact value from the CRT;
+// all primes are odd).  Thread per bit, two ballots per output word.
+__global__ void __launch_bounds__(256) k3_toeplitz_bits(Geo3 X, const u32 *__restrict__ S3, u64 rb, u64 bit0, u64 r,
+                                                        u32 *__restrict__ out32) {
+    pdl_wait();
+    const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;  // bit within the block
+    bool bit = false;
+    if (i < rb && bit0 + i < r) bit = ((u64)crt_value(X, S3, rb - 1 + i) & 1) != 0;
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, bit);
+    if ((threadIdx.x & 31) == 0 && i < rb && bit0 + i < r) out32[(bit0 + i) >> 5] = m;
+    pdl_trigger();
+}
+
 // ------------------------------------------------------------------ tables --
 
 // ctw[r C + c] = omega_T^(dir * c bitrev_R(r)) with its Shoup companion; the
@@ -1611,6 +1638,11 @@ struct P3Plan {
     u32 *spec_a = nullptr, *spec_b = nullptr;
     u64 *seed_copy = nullptr;
     bool prepared = false;
+    // Toeplitz hashing: output blocks and key segments of rb bits, the seed
+    // shifted up by rb zero bits (pseed)
+    bool toep = false;
+    uint64_t rb = 0, nblk = 0;
+    u64 *pseed = nullptr;
     ~P3Plan() { mem.release(); }
     void *alloc(size_t bytes, int *err) {
         void *p = mem.take(bytes, err);
@@ -1954,6 +1986,102 @@ int p3_hash_prepared(P3Plan *pl, const u64 *key, u64 *out, int *status, void *st
 }
 
 bool p3_prepared(const P3Plan *pl) { return pl->prepared; }
+
+// ------------------------------------------------------ Toeplitz hashing --
+// The comparison scheme of Sec. 1 / Table 1 (Toeplitz hashing with the key
+// split into segments): z = T x over GF(2), T[i][j] = s[i - j + n - 1].  With
+// segments x_J of rb bits and output blocks z_I of rb bits, block (I, J) of T
+// is Toeplitz, so z_I = sum_J w_IJ * x_J taken at positions rb - 1 .. 2 rb - 2
+// and mod 2, w_IJ the 2 rb - 1 seed bits starting at n - rb + (I - J) rb (bits
+// before 0 read as 0).  Each term is an exact integer convolution of 1-bit
+// digits on the transforms of length 4 rb (both operands in the lower half),
+// accumulated in the transform domain like the k products of Eq. 2; the
+// coefficients (at most n) come back through the CRT and their parities are
+// the output bits.
+int p3_toeplitz_create(uint64_t n, uint64_t r, uint32_t rb_log, P3Plan **out) {
+    *out = nullptr;
+    if (rb_log < 6 || rb_log > 22) return PA_ERR_UNSUPPORTED;
+    const uint64_t rb = 1ULL << rb_log, K = (n + rb - 1) / rb, nblk = (r + rb - 1) / rb;
+    if (K > 65535) return PA_ERR_UNSUPPORTED;  // segments index the column grid
+    if (p3_prepare_kernels()) return PA_ERR_CUDA;
+    Choice ch;
+    ch.logT = rb_log + 2;
+    ch.b = 1;
+    ch.ps = ch.logT <= kSetA4.maxlog ? &kSetA4 : (ch.logT <= kSetA.maxlog ? &kSetA : &kSetB);
+    // coefficients are at most n (< every prime): exact
+    P3Plan *pl = new (std::nothrow) P3Plan();
+    if (!pl) return PA_ERR_NOMEM;
+    if (pl->mem.init(false)) {
+        delete pl;
+        return PA_ERR_CUDA;
+    }
+    pl->n = n;
+    pl->r = r;
+    pl->k = K;
+    pl->toep = true;
+    pl->rb = rb;
+    pl->nblk = nblk;
+    geometry(pl->mmh, ch, 2 * rb, K, 0);
+    int err = build_tables(pl, pl->mmh, *ch.ps, nullptr);
+    const Geo3 &A = pl->mmh;
+    pl->Y = (u32 *)pl->alloc(3 * 2 * K * A.T * 4, &err);
+    pl->S3 = (u32 *)pl->alloc(3 * A.T * 4, &err);
+    pl->pseed = (u64 *)pl->alloc(((n + r - 1 + rb + 63) / 64 + 1) * 8, &err);
+    pl->flags_bytes = (4 + K) * sizeof(int);
+    pl->flags = (int *)pl->alloc(pl->flags_bytes, &err);
+    if (!err) err = pl->mem.sync();
+    if (err) {
+        delete pl;
+        return err;
+    }
+    pl->ws_bytes = pl->mem.bytes;
+    *out = pl;
+    return PA_OK;
+}
+
+int p3_toeplitz_hash(P3Plan *pl, const u64 *key, const u64 *seed, u64 *out, void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t n = pl->n, r = pl->r, rb = pl->rb;
+    const uint64_t sw = (n + r - 1 + 63) / 64;
+    int e;
+    if ((e = cudaMemsetAsync(out, 0, ((r + 63) / 64) * 8, s))) return e;
+    if ((e = cudaMemsetAsync(pl->pseed, 0, (rb / 64) * 8, s))) return e;
+    if ((e = cudaMemcpyAsync(pl->pseed + rb / 64, seed, sw * 8, cudaMemcpyDeviceToDevice, s))) return e;
+    if ((e = cudaMemsetAsync(pl->flags, 0, pl->flags_bytes, s))) return e;
+    Operands ops;
+    ops.pair0 = 0;
+    ops.key = key;
+    ops.seed = pl->pseed;
+    ops.y = nullptr;
+    ops.y_zero = nullptr;
+    ops.reload = pl->flags;
+    ops.n = n;
+    ops.gamma = 2 * rb;
+    ops.k = pl->k;
+    ops.mode = 6;
+    ops.rb = rb;
+    ops.seed_bits = n + r - 1 + rb;
+    const Geo3 &X = pl->mmh;
+    for (uint64_t I = 0; I < pl->nblk; I++) {
+        ops.blk = (u32)I;
+        if ((e = p3_launch_fwd_col(X, ops, (int)pl->k, pl->Y, stream, true))) return e;
+        if ((e = p3_launch_row_mac(X, pl->Y, pl->S3, stream))) return e;
+        if ((e = p3_launch_inv_col(X, pl->S3, nullptr, 0, stream))) return e;
+        const uint64_t nbits = std::min<uint64_t>(rb, r - I * rb);
+        const unsigned blocks = (unsigned)((nbits + 255) / 256);
+        TRACED("p3_toeplitz_bits", 0, stream,
+               (launch_pdl(k3_toeplitz_bits, dim3(blocks), dim3(256), 0, s, X, (const u32 *)pl->S3, rb, I * rb, r,
+                           reinterpret_cast<u32 *>(out))));
+        if ((e = (int)cudaGetLastError())) return e;
+    }
+    return 0;
+}
+
+void p3_toeplitz_query(const P3Plan *pl, uint64_t *rb, uint64_t *segments, uint64_t *blocks) {
+    if (rb) *rb = pl->rb;
+    if (segments) *segments = pl->k;
+    if (blocks) *blocks = pl->nblk;
+}
 
 u64 *p3_ybuf(P3Plan *pl) { return pl->ybuf; }
 int *p3_flags(P3Plan *pl) { return pl->flags; }

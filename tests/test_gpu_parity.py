@@ -276,3 +276,24 @@ def test_p3_fold_offsets_wrap(gamma, k):
     (t b) mod gamma), every k up to the segment count."""
     n = k * gamma - 3
     _check(n, max(1, gamma // 3), gamma * 31 + k, gamma=gamma)
+
+
+def test_tuned_auto_plan_measures_the_backend(tmp_path):
+    """pa_params.tune with backend AUTO builds both backends and keeps the one
+    that hashed faster; the decision is cached per (gamma, k), written by
+    pa_tune_cache_save, and the plan gives the oracle's bits."""
+    from paper_2105_13678_gb300 import _lib
+    for n, r, seed_id in ((10_000_000, 1_000_000, 41), (1 << 20, 104858, 42)):
+        p = _lib.Plan(n, r, tune=True)
+        assert p.backend in (GOLDILOCKS, P3)
+        key, hseed = synthetic.block_inputs(seed_id, n, (p.k + 2) * p.gamma)
+        st, out, _, _ = gpu_hash(p, key, hseed)
+        rc, ref, _ = oracle_hash_parallel(key, n, hseed, r, p.gamma, p.k)
+        assert st == rc == 0 and np.array_equal(out, ref)
+        again = _lib.Plan(n, r, tune=True)  # cached decision
+        assert again.backend == p.backend
+        path = tmp_path / "tune.txt"
+        assert _lib.lib().pa_tune_cache_save(str(path).encode()) >= 1
+        assert f"backend {p.gamma} {p.k} {p.backend}" in path.read_text().split("\n")
+        p.close()
+        again.close()

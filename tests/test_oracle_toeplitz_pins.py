@@ -86,3 +86,11 @@ def test_gf2_linearity():
     z = lambda k, s: oracle.words_to_int(oracle.toeplitz(k, n, s, r))  # noqa: E731
     assert z(k1 ^ k2, s1) == z(k1, s1) ^ z(k2, s1)
     assert z(k1, s1 ^ s2) == z(k1, s1) ^ z(k1, s2)
+
+
+def test_selected_bits_equal_the_full_product():
+    n, r = 3001, 777
+    key, seed = synthetic.block_inputs(21, n, n + r - 1)
+    full = _bits(oracle.toeplitz(key, n, seed, r), r)
+    idx = [0, 1, 63, 64, 500, r - 1]
+    assert list(oracle.toeplitz_bits(key, n, seed, r, idx)) == [full[i] for i in idx]
