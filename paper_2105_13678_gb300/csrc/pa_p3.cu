@@ -957,7 +957,7 @@ __global__ void __launch_bounds__(256) k3_digits(Geo3 X, const u32 *__restrict__
 //
 // The digits of k3_digits and the chunk carries of the carry kernels in one
 // pass, for vectors whose chunks of PA_CARRY_D digits span >= 64 bits: thread
-// t of CTA q owns chunk q 255 - 1 + t (thread 0 the last chunk of the previous
+// t of CTA q owns chunk q (NT - 1) - 1 + t (thread 0 the last chunk of the previous
 // CTA -- around the ring for CTA 0 -- whose carry-out it provides).  A thread
 // computes the CRT values of its chunk's 8 positions once per wrap and takes
 // the pieces its first two digits need from the previous lane (shuffles), the
@@ -966,7 +966,10 @@ __global__ void __launch_bounds__(256) k3_digits(Geo3 X, const u32 *__restrict__
 // with carry-in H of the previous chunk (OR-ed into y, which the inverse
 // column pass zeroed), and its generate / propagate state are derived in
 // registers; the CTA's state feeds k3_resolve_c.
-constexpr u32 kResolveChunks = 255;  // chunks written per CTA (thread 0 only provides a carry-out)
+// NT threads per CTA (256, or 64 for short vectors so that they still spread
+// over the SMs): NT - 1 chunks written per CTA (thread 0 only provides a
+// carry-out).
+constexpr u32 kResolveMinChunks = 63;  // the smallest CTA's chunks: sizes the per-CTA state arrays
 
 __device__ __forceinline__ bool digit_takes_wrap(const Geo3 &X, u64 t, u32 w, u64 off, u64 D) {
     return t < X.nd && (w == 0 || (t * X.b + D < X.G && t + off <= 2 * X.M));
@@ -985,15 +988,16 @@ __device__ __forceinline__ void crt_pieces(const Geo3 &X, const u32 *__restrict_
     v2 = (u64)(V >> (2 * X.b));
 }
 
-template <bool RING>
-__global__ void __launch_bounds__(256) k3_resolve_a(Geo3 X, const u32 *__restrict__ S3, CarryDev cd,
-                                                    const u64 *__restrict__ c_src, u64 c_base, u64 *__restrict__ y) {
+template <bool RING, int NT>
+__global__ void __launch_bounds__(NT) k3_resolve_a(Geo3 X, const u32 *__restrict__ S3, CarryDev cd,
+                                                   const u64 *__restrict__ c_src, u64 c_base, u64 *__restrict__ y) {
     pdl_wait();
-    __shared__ u64 Hs[256];
-    __shared__ u64 xw[8][3];  // per warp: pieces v1(7), v2(6), v2(7) of its last lane
-    __shared__ unsigned wg[8], wp[8];
+    constexpr int NW = NT / 32;
+    __shared__ u64 Hs[NT];
+    __shared__ u64 xw[NW][3];  // per warp: pieces v1(7), v2(6), v2(7) of its last lane
+    __shared__ unsigned wg[NW], wp[NW];
     const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const long long cq = (long long)blockIdx.x * kResolveChunks - 1 + tid;
+    const long long cq = (long long)blockIdx.x * (NT - 1) - 1 + tid;
     // chunk whose digits this thread forms (thread 0 of CTA 0: the top chunk around the ring)
     const bool exists = cq >= 0 ? (u64)cq < cd.nchunks : RING;
     const u64 ch = cq >= 0 ? (u64)cq : cd.nchunks - 1;
@@ -1154,7 +1158,7 @@ __global__ void __launch_bounds__(256) k3_resolve_a(Geo3 X, const u32 *__restric
     __syncthreads();
     if (tid == 0) {
         unsigned Gc = 0, Pc = 1;
-        for (u32 q = 0; q < 8; q++) {
+        for (u32 q = 0; q < NW; q++) {
             Gc = wg[q] | (wp[q] & Gc);
             Pc = wp[q] & Pc;
         }
@@ -1163,12 +1167,13 @@ __global__ void __launch_bounds__(256) k3_resolve_a(Geo3 X, const u32 *__restric
 }
 
 // Generate / propagate of the states [lo, hi) composed in order, by the CTA
-// (256 threads): (G, P) with G = carry out given no carry in, P = a carry in
+// (NT threads): (G, P) with G = carry out given no carry in, P = a carry in
 // passes through.  Every thread gets the result.
+template <int NT>
 __device__ __forceinline__ void fold_states(const unsigned char *__restrict__ st, u32 lo, u32 hi, unsigned &Gout,
                                             unsigned &Pout, unsigned *wG, unsigned *wP) {
     const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const u32 n = hi > lo ? hi - lo : 0, per = (n + 255) / 256;
+    const u32 n = hi > lo ? hi - lo : 0, per = (n + NT - 1) / NT;
     const u32 b0 = lo + min(tid * per, n), b1 = lo + min(tid * per + per, n);
     unsigned G = 0, P = 1;
     for (u32 q = b0; q < b1; q++) {
@@ -1185,7 +1190,7 @@ __device__ __forceinline__ void fold_states(const unsigned char *__restrict__ st
     __syncthreads();
     G = 0;
     P = 1;
-    for (u32 q = 0; q < 8; q++) {
+    for (u32 q = 0; q < NT / 32; q++) {
         G = wG[q] | (wP[q] & G);
         P = wP[q] & P;
     }
@@ -1197,17 +1202,18 @@ __device__ __forceinline__ void fold_states(const unsigned char *__restrict__ st
 // it (and, around the ring, the carry out of the top with none in -- the
 // end-around carry of the Mersenne fold), then per chunk from the chunk states,
 // and the chunks receiving a carry increment their bit range.
-template <bool RING>
-__global__ void __launch_bounds__(256) k3_resolve_c(CarryDev cd, u32 nctas, u64 *__restrict__ y) {
+template <bool RING, int NT>
+__global__ void __launch_bounds__(NT) k3_resolve_c(CarryDev cd, u32 nctas, u64 *__restrict__ y) {
     pdl_wait();
-    __shared__ unsigned wG[8], wP[8], wg[8], wp[8];
+    constexpr int NW = NT / 32;
+    __shared__ unsigned wG[NW], wP[NW], wg[NW], wp[NW];
     const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned Gpre, Ppre, Gall = 0, Pall = 1;
-    fold_states(cd.cta_state, 0, blockIdx.x, Gpre, Ppre, wG, wP);
-    if (RING) fold_states(cd.cta_state, 0, nctas, Gall, Pall, wG, wP);
+    fold_states<NT>(cd.cta_state, 0, blockIdx.x, Gpre, Ppre, wG, wP);
+    if (RING) fold_states<NT>(cd.cta_state, 0, nctas, Gall, Pall, wG, wP);
     const unsigned ewrap = RING ? Gall : 0u;
     const unsigned cin = Gpre | (Ppre & ewrap);
-    const long long cq = (long long)blockIdx.x * kResolveChunks - 1 + tid;
+    const long long cq = (long long)blockIdx.x * (NT - 1) - 1 + tid;
     const bool real = tid > 0 && cq >= 0 && (u64)cq < cd.nchunks;
     const unsigned st = real ? cd.state[cq] : 2u;
     const unsigned gm = __ballot_sync(0xFFFFFFFFu, st & 1), pm = __ballot_sync(0xFFFFFFFFu, (st >> 1) & 1);
@@ -1454,19 +1460,31 @@ int p3_launch_inv_col(const Geo3 &X, u32 *S3, u64 *zero_out, u64 zero_words, voi
 
 // Fused digit gather and carry of a stage whose chunks are wide (the parallel
 // carry): output bits y zeroed beforehand (by the inverse column pass).
-static int p3_launch_resolve(const Geo3 &X, const u32 *S3, const CarryDev &cd, const u64 *c_src, u64 c_base, u64 *y,
-                             void *stream) {
+template <int NT>
+static void p3_resolve_nt(const Geo3 &X, const u32 *S3, const CarryDev &cd, const u64 *c_src, u64 c_base, u64 *y,
+                          void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
-    const u32 nctas = (u32)((cd.nchunks + kResolveChunks - 1) / kResolveChunks);
+    const u32 nctas = (u32)((cd.nchunks + NT - 2) / (NT - 1));
     if (X.stage == 0) {
         TRACED("p3_resolve_a", 0, stream,
-               (launch_pdl(k3_resolve_a<true>, dim3(nctas), dim3(256), 0, s, X, S3, cd, c_src, c_base, y)));
-        TRACED("p3_resolve_c", 0, stream, (launch_pdl(k3_resolve_c<true>, dim3(nctas), dim3(256), 0, s, cd, nctas, y)));
+               (launch_pdl(k3_resolve_a<true, NT>, dim3(nctas), dim3(NT), 0, s, X, S3, cd, c_src, c_base, y)));
+        TRACED("p3_resolve_c", 0, stream,
+               (launch_pdl(k3_resolve_c<true, NT>, dim3(nctas), dim3(NT), 0, s, cd, nctas, y)));
     } else {
         TRACED("p3_resolve_a", 1, stream,
-               (launch_pdl(k3_resolve_a<false>, dim3(nctas), dim3(256), 0, s, X, S3, cd, c_src, c_base, y)));
-        TRACED("p3_resolve_c", 1, stream, (launch_pdl(k3_resolve_c<false>, dim3(nctas), dim3(256), 0, s, cd, nctas, y)));
+               (launch_pdl(k3_resolve_a<false, NT>, dim3(nctas), dim3(NT), 0, s, X, S3, cd, c_src, c_base, y)));
+        TRACED("p3_resolve_c", 1, stream,
+               (launch_pdl(k3_resolve_c<false, NT>, dim3(nctas), dim3(NT), 0, s, cd, nctas, y)));
     }
+}
+
+static int p3_launch_resolve(const Geo3 &X, const u32 *S3, const CarryDev &cd, const u64 *c_src, u64 c_base, u64 *y,
+                             void *stream) {
+    // 256-thread CTAs while they number at least 64; 64-thread CTAs below
+    if (cd.nchunks >= 64 * 255)
+        p3_resolve_nt<256>(X, S3, cd, c_src, c_base, y, stream);
+    else
+        p3_resolve_nt<64>(X, S3, cd, c_src, c_base, y, stream);
     return (int)cudaGetLastError();
 }
 
@@ -1772,7 +1790,7 @@ static void ws_parts(const Geo3 &A, const Geo3 &B, uint64_t k, uint64_t *total_n
     s += 3 * std::max<uint64_t>(2 * k * A.T, 2 * B.T) * 4;  // Y (also the digit vector)
     s += 3 * Tm * 4;                                       // S3
     s += 2 * ((A.G + 63) / 64 + 2) * 8;                    // ybuf, tbuf
-    s += nch * 9 + 2 * (nch / kResolveChunks + 2);         // carry state
+    s += nch * 9 + 2 * (nch / kResolveMinChunks + 2);      // carry state
     s += (4 + k) * sizeof(int);
     *total_no_tables = s;
 }
@@ -1817,8 +1835,8 @@ int p3_plan_create(uint64_t n, uint64_t r, uint32_t gamma, uint64_t k, bool stre
     pl->tbuf = (u64 *)pl->alloc(((gamma + 63) / 64 + 2) * 8, &err);
     pl->H = (u64 *)pl->alloc(nch * 8, &err);
     pl->cstate = (unsigned char *)pl->alloc(nch, &err);
-    pl->cta_state = (unsigned char *)pl->alloc(nch / kResolveChunks + 2, &err);
-    pl->cta_cin = (unsigned char *)pl->alloc(nch / kResolveChunks + 2, &err);
+    pl->cta_state = (unsigned char *)pl->alloc(nch / kResolveMinChunks + 2, &err);
+    pl->cta_cin = (unsigned char *)pl->alloc(nch / kResolveMinChunks + 2, &err);
     pl->flags_bytes = (4 + k) * sizeof(int);
     pl->flags = (int *)pl->alloc(pl->flags_bytes, &err);
     if (!err) err = pl->mem.sync();  // the tables are filled
