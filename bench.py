@@ -154,13 +154,22 @@ def _dft_work(length: int, count: int):
     return full + trivial, full, full * (ALU_ADD + ALU_SUB + ALU_MUL) + trivial * (ALU_ADD + ALU_SUB)
 
 
-# Three-prime backend, per 32-bit residue: a DIF butterfly is one add with its
-# [0, 2p) reduction (3 ALU ops: add, subtract, minimum) and one difference
-# (1); a DIT butterfly two reduced adds (6); a Montgomery multiply-accumulate
-# 4; a digit read a shift and a mask (2), once per operand for all three
-# primes.  The first column stage of a zero-padded input has no additions.
-# The multiplies (Shoup and Montgomery products) run on the IMAD (FMA) pipe.
-P3_DIF, P3_DIT, P3_MAC, P3_DIGIT = 4, 6, 4, 2
+# Three-prime backend, per 32-bit residue.  With the primes below 2^28
+# (transforms up to 2^21, lazy reductions) a DIF butterfly is its sum and its
+# difference (2 ALU ops) plus the conditional subtractions a radix-8 round
+# needs at its end, about 1 per butterfly (3); a DIT butterfly 4.  With the
+# primes below 2^30 (eager reductions) a DIF butterfly is one add with its
+# [0, 2p) reduction (add, subtract, minimum) and one difference (4), a DIT
+# butterfly two reduced adds (6).  A Montgomery multiply-accumulate is 4; a
+# digit read a shift and a mask (2), once per operand for all three primes.
+# The first column stage of a zero-padded input has no additions.  The
+# multiplies (Shoup and Montgomery products) run on the IMAD (FMA) pipe.
+P3_MAC, P3_DIGIT = 4, 2
+
+
+def p3_butterfly_alu(T: int):
+    """(DIF, DIT) ALU operations per butterfly for a transform of length T."""
+    return (3, 4) if T <= (1 << 21) else (4, 6)
 
 
 def kernel_model_p3(info, stage: str, kernel: str, geometry=None):
@@ -175,6 +184,7 @@ def kernel_model_p3(info, stage: str, kernel: str, geometry=None):
     logR = geometry[0] if geometry else min(logT // 2, 10)
     logC = logT - logR
     R, C = 1 << logR, 1 << logC
+    P3_DIF, P3_DIT = p3_butterfly_alu(T)
     if kernel == "p3_fwd_col":
         ops = 3 * 2 * K
         # first stage: upper half zero (a, 0) -> (a, a w): products only
@@ -497,6 +507,11 @@ def roofline(info, trace, steps, peaks, peak_kind, step_ms, geometries=None, blo
             ncu["alu_ops_counted"] = int(counted)
             ncu["alu_frac_counted"] = round(counted / (rec["duration_ns"] / 1e9) / alu_peak, 4)
             ncu["model_over_counted"] = round(alu / counted, 4)
+        if "warp_inst" in rec and rec.get("duration_ns"):
+            # every instruction against the issue slots (4 warp instructions per SM per clock)
+            issue_peak = sms * 4 * sm_mhz * 1e6
+            ncu["warp_inst"] = int(rec["warp_inst"])
+            ncu["issue_frac_counted"] = round(rec["warp_inst"] / (rec["duration_ns"] / 1e9) / issue_peak, 4)
         for k_ in ("alu_pipe_pct", "issue_active_pct"):
             if k_ in rec:
                 ncu[k_] = round(rec[k_], 2)

@@ -60,7 +60,8 @@ def _num(s: str):
 def _scale(unit: str) -> float:
     unit = unit.strip().lower()
     return {"byte": 1, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9, "nsecond": 1, "usecond": 1e3, "msecond": 1e6,
-            "second": 1e9, "hz": 1, "khz": 1e3, "mhz": 1e6, "ghz": 1e9}.get(unit, 1.0)
+            "second": 1e9, "ns": 1, "us": 1e3, "ms": 1e6, "s": 1e9, "hz": 1, "khz": 1e3, "mhz": 1e6,
+            "ghz": 1e9}.get(unit, 1.0)
 
 
 def parse_raw(path: str) -> list[dict]:
