@@ -116,6 +116,21 @@ __device__ __forceinline__ void make_room(u32 &a, int &Ba, u32 &b, int &Bb, u32 
 template <bool TS>
 __device__ __forceinline__ uint2 twl(const uint2 *__restrict__ p) { return TS ? *p : __ldg(p); }
 
+// Shared-memory twiddles of one prime in the column kernel (R = 2^10, uint2
+// entries): the forward R table from round 2 on -- round 2 (56 entries),
+// round 3 (7), the 4-stage first round (960) and one pad entry that the plan
+// stores so that the window is 1024 entries, 512 16-byte copies -- then the
+// tile's 64 split inter-pass twiddles B[c][m].
+constexpr u32 kColTab = 1024, kColTabStride = kColTab + 64, kColTabR3 = 56, kColTab4 = 63;
+
+// Asynchronous 16-byte global -> shared copies (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
+    const u32 d = (u32)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <int NS, bool LAST, bool HZ, bool TS = false, int H = 2, int OUT = 2>
 __device__ __forceinline__ void dif3(u32 (&v)[8], const uint2 *__restrict__ rt, u32 p) {
     int B[8];
@@ -392,7 +407,8 @@ __device__ __forceinline__ void fwd3_round(const Geo3 &X, u32 j, const Desc &dx,
     const u32 dsm = pstepc(stride * tc);  // tc = 8
     const u64 dY = (u64)stride * X.C;
     const uint2 red = X.red[j];
-    const uint2 *tw = (TS ? stw : X.twR[j]) + X.rofR[rd];
+    // shared-memory tables (TS: R = 2^10) start at round 2 of the forward R table
+    const uint2 *tw = TS ? stw + (rd == 2 ? 0u : kColTabR3) : X.twR[j] + X.rofR[rd];
     for (u32 task = threadIdx.x; task < ntask; task += blockDim.x) {
         const u32 c = task & (tc - 1), g = task >> logtc;
         const u32 lo = g & (stride - 1), base = ((g >> sh) << (l - s0)) + lo;
@@ -486,17 +502,25 @@ __global__ void __launch_bounds__(kColThreads) k3_fwd_col(Geo3 X, Operands S, u3
     }
 }
 
+// Start the copies of prime j's twiddles into the buffer tb (512 threads).
+template <int TC>
+__device__ __forceinline__ void col_tables_async(const Geo3 &X, u32 j, uint2 *tb, u32 c0) {
+    cp_async16(tb + 2 * threadIdx.x, X.twR[j] + X.rofR[2] + 2 * threadIdx.x);
+    if (threadIdx.x < 4 * TC) cp_async16(tb + kColTab + 2 * threadIdx.x, X.ctwB[j] + (u64)c0 * 8 + 2 * threadIdx.x);
+    cp_async_commit();
+}
+
 // All three primes in one CTA (R = 2^10, 8-column tiles, 512 threads): each
 // thread reads the 8 nonzero digits of its first-round group once into
 // registers; each prime then runs its column transform through the same
 // shared tile in three rounds -- stages 0-3 in registers on 16 elements
-// (upper half zero), then 4-6 and 7-9 -- with its round twiddles staged in
-// shared memory.  PAIR: both operands of pair i; else the single operand i.
+// (upper half zero), then 4-6 and 7-9 -- with its round twiddles in shared
+// memory, copied asynchronously one prime ahead (two buffers).  PAIR: both
+// operands of pair i; else the single operand i.
 template <int LL, int TC, bool PAIR, int H>
 __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32 *__restrict__ Y) {
     pdl_wait();
     static_assert(LL == 10 && TC == 8, "one task per thread: R/16 x 8 columns = 512");
-    constexpr u32 NTH = 512;
     extern __shared__ u32 sm3[];
     // pairs vary fastest across the grid, so the tile's inter-pass twiddles are
     // reused from L2 by the CTAs of all pairs
@@ -504,7 +528,8 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
     Desc dx, da;
     descs<PAIR>(S, i, dx, da);
     u32 *smx = sm3, *sma = sm3 + pxc((1u << LL) * TC);
-    uint2 *stw = reinterpret_cast<uint2 *>(sm3 + (PAIR ? 2 : 1) * pxc((1u << LL) * TC));  // this prime's round tables
+    uint2 *stw = reinterpret_cast<uint2 *>(sm3 + (PAIR ? 2 : 1) * pxc((1u << LL) * TC));  // two twiddle buffers
+    col_tables_async<TC>(X, 0, stw, c0);
     bool ones = true;
     const u32 c = threadIdx.x & (TC - 1), lo = threadIdx.x >> 3;  // group lo: rows lo + 64 m
     constexpr u32 D64 = 64;
@@ -525,14 +550,13 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
         const uint2 red = X.red[j];
         const bool raw = (1ULL << X.b) <= 2ULL * p;  // b-bit digits already lie in [0, 2p)
         u32 *Yx = Y + ((u64)j * 2 * X.K + i) * X.T, *Ya = Y + ((u64)j * 2 * X.K + X.K + i) * X.T;
-        uint2 *sB = stw + X.rof4R + 64 * 15;  // this tile's split inter-pass twiddles B[c][m]
-        {
-            const u32 ntw = X.rof4R + 64 * 15;  // standard rounds, then the 4-stage first round
-            for (u32 q = threadIdx.x; q < ntw; q += NTH) stw[q] = __ldg(X.twR[j] + q);
-            if (threadIdx.x < 8 * TC) sB[threadIdx.x] = __ldg(X.ctwB[j] + (u64)c0 * 8 + threadIdx.x);
-            __syncthreads();
-        }
-        const uint2 *rt = stw + X.rof4R + lo * 15;
+        uint2 *tb = stw + (j & 1) * kColTabStride;
+        // prime j's twiddles have landed, and prime j - 1's rounds are done with
+        // the tile and with the other buffer, which now receives prime j + 1's
+        cp_async_wait_all();
+        __syncthreads();
+        const uint2 *sB = tb + kColTab;  // this tile's split inter-pass twiddles B[c][m]
+        const uint2 *rt = tb + kColTab4 + lo * 15;
         {
             u32 v[16];
 #pragma unroll
@@ -550,16 +574,16 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
             for (u32 m = 0; m < 16; m++) sma[a0 + m * dsm] = v[m];
         }
         __syncthreads();
+        if (j + 1 < 3) col_tables_async<TC>(X, j + 1, stw + ((j + 1) & 1) * kColTabStride, c0);
         // the last round's A twiddles of this thread's two tasks (rows 8 g + m,
         // g = lo and lo + 64), loaded now so that round 2 hides their latency
         const uint2 apre0 = __ldg(X.ctwA[j] + (u64)lo * X.C + c0 + c);
         const uint2 apre1 = __ldg(X.ctwA[j] + (u64)(lo + 64) * X.C + c0 + c);
         // stages 4-6 and 7-9: the standard partition's rounds 2 and 3
-        fwd3_round<3, PAIR, false, false, LL, TC, true, H>(X, j, dx, da, smx, sma, Yx, Ya, c0, 4, 2, ones, stw);
+        fwd3_round<3, PAIR, false, false, LL, TC, true, H>(X, j, dx, da, smx, sma, Yx, Ya, c0, 4, 2, ones, tb);
         __syncthreads();
-        fwd3_round<3, PAIR, false, true, LL, TC, true, H, true>(X, j, dx, da, smx, sma, Yx, Ya, c0, 7, 3, ones, stw, sB,
+        fwd3_round<3, PAIR, false, true, LL, TC, true, H, true>(X, j, dx, da, smx, sma, Yx, Ya, c0, 7, 3, ones, tb, sB,
                                                                   apre0, apre1);
-        __syncthreads();
     }
     pdl_trigger();
     if (dx.check_ones) {
@@ -1380,7 +1404,7 @@ int p3_launch_fwd_col(const Geo3 &X, const Operands &S, int pairs, u32 *Y, void 
     const dim3 grid(X.C / X.tc, pairs, 3);
     const size_t smem = col_smem3(X, pair);
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t smem_all = smem + (X.rof4R + 64 * 15 + 8 * 8) * sizeof(uint2);
+    const size_t smem_all = smem + 2 * kColTabStride * sizeof(uint2);
     if (X.logR == 10 && X.tc == 8 && X.rof4R) {
         if (X.head == 4)
             p3_fwd_all<4>(X, S, pairs, Y, stream, pair, smem_all);
@@ -1736,6 +1760,11 @@ int build_tables(P3Plan *pl, Geo3 &X, const PrimeSet &ps, const Geo3 *other) {
                 for (u32 lo = 0; lo < 64; lo++)
                     for (u32 sg = 0; sg < 4; sg++)
                         for (u32 jj = 0; jj < (8u >> sg); jj++) tR.push_back(shoup_pair(pw[((lo + jj * 64) << sg) % X.R], p));
+                // the column kernel copies entries [rofR[2], rofR[2] + kColTab) in 16-byte pieces
+                while (tR.size() < (size_t)X.rofR[2] + kColTab) tR.push_back(make_uint2(0u, 0u));
+                if (tR.size() != (size_t)X.rofR[2] + kColTab || X.rofR[3] - X.rofR[2] != kColTabR3 ||
+                    X.rof4R - X.rofR[2] != kColTab4 || (X.rofR[2] & 1))
+                    err = PA_ERR_INVALID;
             }
             u64 a = 1;
             uint2 *dR = (uint2 *)pl->alloc(tR.size() * sizeof(uint2), &err);
