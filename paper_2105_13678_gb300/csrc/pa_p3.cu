@@ -207,12 +207,12 @@ __device__ __forceinline__ void dit3(u32 (&v)[8], const uint2 *__restrict__ rt, 
 // Stages 0..3 of a length-L transform on 16 elements lo + m L/16 whose upper
 // 8 are zero on entry (the zero-padded half), twiddles rt[16 - 2^(4-sg) + jj]
 // = omega_L^((lo + jj L/16) 2^sg); the round table is in shared memory.
-// Inputs below 2p.
-template <int H = 2, int OUT = 2>
+// Inputs below IB p (2 or 4: raw digits of up to log2(4p) bits).
+template <int H = 2, int OUT = 2, int IB = 2>
 __device__ __forceinline__ void dif16_hz(u32 (&v)[16], const uint2 *__restrict__ rt, u32 p) {
     int B[16];
 #pragma unroll
-    for (int m = 0; m < 16; m++) B[m] = 2;
+    for (int m = 0; m < 16; m++) B[m] = m < 8 ? IB : 2;
 #pragma unroll
     for (int sg = 0; sg < 4; sg++) {
         const int half = 8 >> sg;
@@ -444,9 +444,10 @@ __device__ __forceinline__ void fwd3_round(const Geo3 &X, u32 j, const Desc &dx,
         for (int m = 0; m < (1 << NS); m++) {
             if (LAST && SPLIT) {
                 const u64 e = e0 + m * dY;
+                // B[c][0] = 1 (bitrev(0) = 0): row 8 g takes the A factor alone
                 const uint2 bm = sB[c * 8 + m];
-                Yx[e] = shoup(shoup(vx[m], bm, p), ct[0], p);
-                if (PAIR) Ya[e] = shoup(shoup(va[m], bm, p), ct[0], p);
+                Yx[e] = shoup(m == 0 ? vx[m] : shoup(vx[m], bm, p), ct[0], p);
+                if (PAIR) Ya[e] = shoup(m == 0 ? va[m] : shoup(va[m], bm, p), ct[0], p);
             } else if (LAST) {
                 // position r holds column frequency bitrev(r): times omega_T^(c bitrev(r))
                 const u64 e = e0 + m * dY;
@@ -548,7 +549,10 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
     for (u32 j = 0; j < 3; j++) {
         const u32 p = X.p[j];
         const uint2 red = X.red[j];
-        const bool raw = (1ULL << X.b) <= 2ULL * p;  // b-bit digits already lie in [0, 2p)
+        // b-bit digits enter unreduced when they lie in [0, 4p) (the first stage only
+        // multiplies them; later sums reduce as their bounds require), else through a
+        // Shoup product into [0, 2p)
+        const bool raw = (1ULL << X.b) <= 4ULL * p;
         u32 *Yx = Y + ((u64)j * 2 * X.K + i) * X.T, *Ya = Y + ((u64)j * 2 * X.K + X.K + i) * X.T;
         uint2 *tb = stw + (j & 1) * kColTabStride;
         // prime j's twiddles have landed, and prime j - 1's rounds are done with
@@ -561,7 +565,10 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
             u32 v[16];
 #pragma unroll
             for (u32 m = 0; m < 16; m++) v[m] = m < 8 ? (raw ? rx[m] : shoup(rx[m], red, p)) : 0u;
-            dif16_hz<H, 2>(v, rt, p);
+            if (raw)
+                dif16_hz<H, 2, 4>(v, rt, p);
+            else
+                dif16_hz<H, 2, 2>(v, rt, p);
 #pragma unroll
             for (u32 m = 0; m < 16; m++) smx[a0 + m * dsm] = v[m];
         }
@@ -569,7 +576,10 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
             u32 v[16];
 #pragma unroll
             for (u32 m = 0; m < 16; m++) v[m] = m < 8 ? (raw ? ra[m] : shoup(ra[m], red, p)) : 0u;
-            dif16_hz<H, 2>(v, rt, p);
+            if (raw)
+                dif16_hz<H, 2, 4>(v, rt, p);
+            else
+                dif16_hz<H, 2, 2>(v, rt, p);
 #pragma unroll
             for (u32 m = 0; m < 16; m++) sma[a0 + m * dsm] = v[m];
         }
@@ -642,8 +652,11 @@ __device__ __forceinline__ void row_fwd3(const Geo3 &X, u32 j, const u32 (&fx)[A
 #pragma unroll
                 for (int m = 0; m < (1 << NS); m++) {
                     if (LAST) {
+                        // Montgomery outputs lie in (0, 2p); with headroom 16p the sum
+                        // takes 7 of them before the caller reduces it (mac_reduce)
                         u32 &a = acc[t * (1 << NS) + m];
-                        a = red2(a + mont(vx[m], TWO ? va[m] : fa[t * (1 << NS) + m], p, pinv), 2 * p);
+                        const u32 prod = mont(vx[m], TWO ? va[m] : fa[t * (1 << NS) + m], p, pinv);
+                        a = H >= 4 ? a + prod : red2(a + prod, 2 * p);
                     } else {
                         smx[a0 + m * dsm] = vx[m];
                         if (TWO) sma[a0 + m * dsm] = va[m];
@@ -652,6 +665,14 @@ __device__ __forceinline__ void row_fwd3(const Geo3 &X, u32 j, const u32 (&fx)[A
             }
         }
     }
+}
+
+// Accumulators of the lazy multiply-accumulate (H = 4): below 16p after at
+// most 7 products since the last reduction, brought below 2p.
+template <int ACC>
+__device__ __forceinline__ void mac_reduce(u32 (&acc)[ACC], u32 p) {
+#pragma unroll
+    for (int m = 0; m < ACC; m++) acc[m] = csub(csub(csub(acc[m], 8 * p), 4 * p), 2 * p);
 }
 
 // The first round's inputs of one row pair (elements g + m C/2^NS of group g).
@@ -772,6 +793,7 @@ __global__ void __launch_bounds__(1024) k3_row_mac(Geo3 X, const u32 *__restrict
 #undef P3_ROWF
             __syncthreads();
         }
+        if (H >= 4 && MODE != 1 && (i % 7 == 6 || i + 1 == X.K)) mac_reduce(acc, X.p[j]);
     }
     if (MODE == 1) {
         pdl_trigger();
