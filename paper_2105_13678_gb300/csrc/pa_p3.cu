@@ -73,19 +73,23 @@ __device__ __forceinline__ u32 round_s0(u32 l, u32 rd) { return rd ? round_ns(l,
 // its bound fits the headroom, otherwise its inputs are first brought down by
 // conditional subtractions; a difference a - b + B_b p is reduced by its Shoup
 // product into [0, 2p).  OUT is the bound the caller needs at the end of the
-// round (2: [0, 2p), 4: [0, 4p), 0: any 32-bit value, e.g. before a Shoup
-// product).
+// round (2: [0, 2p), 4: [0, 4p), 8: [0, 8p), 0: any 32-bit value, e.g. before
+// a Shoup product) and IB the bound of the round's inputs.  With headroom 16p
+// the radix-8 rounds hand their outputs on below 4p (forward) or 8p
+// (inverse), which takes the fewest conditional subtractions over a transform.
 __device__ __forceinline__ u32 csub(u32 x, u32 kp) { return min(x, x - kp); }  // x < 2 kp -> x < kp
 
-// Bring v below bound `to` (a power of two times p not below 2) from bound B.
+// One conditional subtraction of floor(B/2) p: x < B p -> x < ceil(B/2) p.
+__device__ __forceinline__ void halve(u32 &v, int &B, u32 p) {
+    v = csub(v, (u32)(B / 2) * p);
+    B -= B / 2;
+}
+
+// Bring v below bound `to` (2, 4 or 8, in units of p) from bound B <= 32.
 __device__ __forceinline__ void reduce_to(u32 &v, int &B, int to, u32 p) {
 #pragma unroll
-    for (int it = 0; it < 5; it++) {
-        if (B > to) {
-            v = csub(v, (u32)(B / 2) * p);
-            B /= 2;
-        }
-    }
+    for (int it = 0; it < 5; it++)
+        if (B > to) halve(v, B, p);
 }
 
 // Operands a (bound Ba), b (bound Bb) of a sum must satisfy Ba + Bb <= 2^H:
@@ -95,13 +99,10 @@ __device__ __forceinline__ void make_room(u32 &a, int &Ba, u32 &b, int &Bb, u32 
 #pragma unroll
     for (int it = 0; it < 8; it++) {
         if (Ba + Bb > (1 << H)) {
-            if (Ba >= Bb) {
-                a = csub(a, (u32)(Ba / 2) * p);
-                Ba /= 2;
-            } else {
-                b = csub(b, (u32)(Bb / 2) * p);
-                Bb /= 2;
-            }
+            if (Ba >= Bb)
+                halve(a, Ba, p);
+            else
+                halve(b, Bb, p);
         }
     }
 }
@@ -131,11 +132,11 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-template <int NS, bool LAST, bool HZ, bool TS = false, int H = 2, int OUT = 2>
+template <int NS, bool LAST, bool HZ, bool TS = false, int H = 2, int OUT = 2, int IB = 2>
 __device__ __forceinline__ void dif3(u32 (&v)[8], const uint2 *__restrict__ rt, u32 p) {
     int B[8];
 #pragma unroll
-    for (int m = 0; m < 8; m++) B[m] = 2;
+    for (int m = 0; m < 8; m++) B[m] = IB;
 #pragma unroll
     for (int sg = 0; sg < NS; sg++) {
         const int half = 1 << (NS - 1 - sg);
@@ -168,12 +169,12 @@ __device__ __forceinline__ void dif3(u32 (&v)[8], const uint2 *__restrict__ rt, 
 
 // Inverse of dif3 up to a factor 2^NS (DIT, stages reversed, inverse
 // twiddles in the same table layout).  HO: the upper outputs of the last
-// stage are not needed.  Inputs below 2p.
-template <int NS, bool LAST, bool HO, int H = 2, int OUT = 2>
+// stage are not needed.  Inputs below IB p.
+template <int NS, bool LAST, bool HO, int H = 2, int OUT = 2, int IB = 2>
 __device__ __forceinline__ void dit3(u32 (&v)[8], const uint2 *__restrict__ rt, u32 p) {
     int B[8];
 #pragma unroll
-    for (int m = 0; m < 8; m++) B[m] = 2;
+    for (int m = 0; m < 8; m++) B[m] = IB;
 #pragma unroll
     for (int sg = NS - 1; sg >= 0; sg--) {
         const int half = 1 << (NS - 1 - sg);
@@ -394,7 +395,8 @@ __device__ __forceinline__ u32 digit_raw(const Geo3 &X, const Desc &d, u64 pos, 
 // SPLIT (the last round of k3_fwd_col_all: stride 1, R = 2^10, 512 threads):
 // the inter-pass twiddle of row 8 g + m is A[g][c] -- loaded by the caller a
 // round early, one per task (apre) -- times the staged sB[c][m].
-template <int NS, bool PAIR, bool FIRST, bool LAST, int LL, int TC, bool TS = false, int H = 2, bool SPLIT = false>
+template <int NS, bool PAIR, bool FIRST, bool LAST, int LL, int TC, bool TS = false, int H = 2, bool SPLIT = false,
+          int RIB = 2, int ROUT = 2>
 __device__ __forceinline__ void fwd3_round(const Geo3 &X, u32 j, const Desc &dx, const Desc &da, u32 *__restrict__ smx,
                                            u32 *__restrict__ sma, u32 *__restrict__ Yx, u32 *__restrict__ Ya, u32 c0,
                                            u32 s0, u32 rd, bool &ones, const uint2 *__restrict__ stw = nullptr,
@@ -438,8 +440,8 @@ __device__ __forceinline__ void fwd3_round(const Geo3 &X, u32 j, const Desc &dx,
         }
         const uint2 *rt = tw + lo * ((1u << NS) - 1);
         // the last round's outputs go straight into Shoup products (any bound)
-        dif3<NS, LAST, FIRST, TS, H, LAST ? 0 : 2>(vx, rt, p);
-        if (PAIR) dif3<NS, LAST, FIRST, TS, H, LAST ? 0 : 2>(va, rt, p);
+        dif3<NS, LAST, FIRST, TS, H, LAST ? 0 : ROUT, RIB>(vx, rt, p);
+        if (PAIR) dif3<NS, LAST, FIRST, TS, H, LAST ? 0 : ROUT, RIB>(va, rt, p);
 #pragma unroll
         for (int m = 0; m < (1 << NS); m++) {
             if (LAST && SPLIT) {
@@ -522,6 +524,7 @@ template <int LL, int TC, bool PAIR, int H>
 __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32 *__restrict__ Y) {
     pdl_wait();
     static_assert(LL == 10 && TC == 8, "one task per thread: R/16 x 8 columns = 512");
+    constexpr int RB = H >= 4 ? 4 : 2;  // bound of the rounds' outputs (units of p)
     extern __shared__ u32 sm3[];
     // pairs vary fastest across the grid, so the tile's inter-pass twiddles are
     // reused from L2 by the CTAs of all pairs
@@ -566,9 +569,9 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
 #pragma unroll
             for (u32 m = 0; m < 16; m++) v[m] = m < 8 ? (raw ? rx[m] : shoup(rx[m], red, p)) : 0u;
             if (raw)
-                dif16_hz<H, 2, 4>(v, rt, p);
+                dif16_hz<H, RB, 4>(v, rt, p);
             else
-                dif16_hz<H, 2, 2>(v, rt, p);
+                dif16_hz<H, RB, 2>(v, rt, p);
 #pragma unroll
             for (u32 m = 0; m < 16; m++) smx[a0 + m * dsm] = v[m];
         }
@@ -577,9 +580,9 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
 #pragma unroll
             for (u32 m = 0; m < 16; m++) v[m] = m < 8 ? (raw ? ra[m] : shoup(ra[m], red, p)) : 0u;
             if (raw)
-                dif16_hz<H, 2, 4>(v, rt, p);
+                dif16_hz<H, RB, 4>(v, rt, p);
             else
-                dif16_hz<H, 2, 2>(v, rt, p);
+                dif16_hz<H, RB, 2>(v, rt, p);
 #pragma unroll
             for (u32 m = 0; m < 16; m++) sma[a0 + m * dsm] = v[m];
         }
@@ -590,10 +593,11 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
         const uint2 apre0 = __ldg(X.ctwA[j] + (u64)lo * X.C + c0 + c);
         const uint2 apre1 = __ldg(X.ctwA[j] + (u64)(lo + 64) * X.C + c0 + c);
         // stages 4-6 and 7-9: the standard partition's rounds 2 and 3
-        fwd3_round<3, PAIR, false, false, LL, TC, true, H>(X, j, dx, da, smx, sma, Yx, Ya, c0, 4, 2, ones, tb);
+        fwd3_round<3, PAIR, false, false, LL, TC, true, H, false, RB, RB>(X, j, dx, da, smx, sma, Yx, Ya, c0, 4, 2, ones,
+                                                                          tb);
         __syncthreads();
-        fwd3_round<3, PAIR, false, true, LL, TC, true, H, true>(X, j, dx, da, smx, sma, Yx, Ya, c0, 7, 3, ones, tb, sB,
-                                                                  apre0, apre1);
+        fwd3_round<3, PAIR, false, true, LL, TC, true, H, true, RB>(X, j, dx, da, smx, sma, Yx, Ya, c0, 7, 3, ones, tb,
+                                                                     sB, apre0, apre1);
     }
     pdl_trigger();
     if (dx.check_ones) {
@@ -612,7 +616,7 @@ __global__ void __launch_bounds__(512, 2) k3_fwd_col_all(Geo3 X, Operands S, u32
 // base a multiple of 8), so their padded words are px(base) + m * pstep(stride).
 // MODE 0: both rows of pair i, product into acc; 1: row x only, its spectrum
 // stored to spec; 2: row x only, times the stored spectrum held in fa.
-template <int NS, int ACC, bool LAST, int LL, int MODE, int H>
+template <int NS, int ACC, bool LAST, int LL, int MODE, int H, int RIB, int ROUT>
 __device__ __forceinline__ void row_fwd3(const Geo3 &X, u32 j, const u32 (&fx)[ACC], const u32 (&fa)[ACC],
                                          u32 *__restrict__ smx, u32 *__restrict__ sma, u32 s0, u32 rd, bool first,
                                          u32 (&acc)[ACC], u32 *__restrict__ spec) {
@@ -637,8 +641,8 @@ __device__ __forceinline__ void row_fwd3(const Geo3 &X, u32 j, const u32 (&fx)[A
             // the last round feeds the Montgomery products (inputs below 4p when p < 2^28,
             // whose product then stays below 2^32 p) or the stored spectra ([0, 2p))
             constexpr int OUTL = (MODE == 1 || H < 4) ? 2 : 4;
-            dif3<NS, LAST, false, false, H, LAST ? OUTL : 2>(vx, rt, p);
-            if (TWO) dif3<NS, LAST, false, false, H, LAST ? OUTL : 2>(va, rt, p);
+            dif3<NS, LAST, false, false, H, LAST ? OUTL : ROUT, RIB>(vx, rt, p);
+            if (TWO) dif3<NS, LAST, false, false, H, LAST ? OUTL : ROUT, RIB>(va, rt, p);
             if constexpr (LAST && MODE == 1) {  // the last round has stride 1: elements base + m
                 if constexpr (NS == 3) {
                     uint4 *d = reinterpret_cast<uint4 *>(spec + base);
@@ -709,10 +713,13 @@ __device__ __forceinline__ void row_inv3(const Geo3 &X, u32 j, u32 *__restrict__
             u32 v[8];
 #pragma unroll
             for (int m = 0; m < (1 << NS); m++) v[m] = LAST ? acc[t * (1 << NS) + m] : sm[a0 + m * dsm];
+            // the first inverse round takes the accumulators (below 2p), later ones the
+            // previous round's outputs (below RBI p)
+            constexpr int RBI = H >= 4 ? 8 : 2, IB = LAST ? 2 : RBI;
             if (to_global)  // followed by the Shoup product with the inverse inter-pass twiddle
-                dit3<NS, LAST, false, H, 0>(v, itw + lo * ((1u << NS) - 1), p);
+                dit3<NS, LAST, false, H, 0, IB>(v, itw + lo * ((1u << NS) - 1), p);
             else
-                dit3<NS, LAST, false, H, 2>(v, itw + lo * ((1u << NS) - 1), p);
+                dit3<NS, LAST, false, H, RBI, IB>(v, itw + lo * ((1u << NS) - 1), p);
 #pragma unroll
             for (int m = 0; m < (1 << NS); m++) {
                 if (to_global) {
@@ -761,6 +768,7 @@ __global__ void __launch_bounds__(1024) k3_row_mac(Geo3 X, const u32 *__restrict
     const u32 j = blockIdx.y, row = blockIdx.x, l = LL ? (u32)LL : X.logC, C = 1u << l;
     u32 *smx = sm3, *sma = sm3 + px(C);
     u32 acc[ACC], fx[ACC], fa[ACC];
+    constexpr int RB = H >= 4 ? 4 : 2;  // bound of the forward rounds' outputs (units of p)
 #pragma unroll
     for (int m = 0; m < ACC; m++) acc[m] = 0;
     const u32 nr = (l + 2) / 3, ns0 = round_ns(l, 0), nsl = round_ns(l, nr - 1);
@@ -782,12 +790,17 @@ __global__ void __launch_bounds__(1024) k3_row_mac(Geo3 X, const u32 *__restrict
         for (u32 rd = 0; rd < nr; rd++) {
             const u32 s0 = round_s0(l, rd), ns = round_ns(l, rd);
             const bool first = rd == 0, last = rd == nr - 1;
-#define P3_ROWF(NSV)                                                                                  \
-    do {                                                                                              \
-        if (last)                                                                                     \
-            row_fwd3<NSV, ACC, true, LL, MODE, H>(X, j, fx, fa, smx, sma, s0, rd, first, acc, srow);  \
-        else                                                                                          \
-            row_fwd3<NSV, ACC, false, LL, MODE, H>(X, j, fx, fa, smx, sma, s0, rd, first, acc, srow); \
+// inputs of the first round (spectra of the column pass) below 2p, of later rounds below RB p
+#define P3_ROWF(NSV)                                                                                              \
+    do {                                                                                                          \
+        if (last && first)                                                                                        \
+            row_fwd3<NSV, ACC, true, LL, MODE, H, 2, RB>(X, j, fx, fa, smx, sma, s0, rd, first, acc, srow);       \
+        else if (last)                                                                                            \
+            row_fwd3<NSV, ACC, true, LL, MODE, H, RB, RB>(X, j, fx, fa, smx, sma, s0, rd, first, acc, srow);      \
+        else if (first)                                                                                           \
+            row_fwd3<NSV, ACC, false, LL, MODE, H, 2, RB>(X, j, fx, fa, smx, sma, s0, rd, first, acc, srow);      \
+        else                                                                                                      \
+            row_fwd3<NSV, ACC, false, LL, MODE, H, RB, RB>(X, j, fx, fa, smx, sma, s0, rd, first, acc, srow);     \
     } while (0)
             P3_DISPATCH_NS(ns, P3_ROWF);
 #undef P3_ROWF
