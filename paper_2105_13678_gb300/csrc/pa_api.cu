@@ -759,9 +759,7 @@ int pa_hash(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed, uint64_t *
         return cuda_rc(e);
     }
     if (pl->p3) {
-        int e = p3_enqueue_mmh(pl->p3, (const u64 *)key, (const u64 *)seed, p3_ybuf(pl->p3), false, stream);
-        if (!e) e = p3_enqueue_mh(pl->p3, (const u64 *)seed, (u64 *)out, status, stream);
-        return cuda_rc(e);
+        return cuda_rc(p3_enqueue_hash(pl->p3, (const u64 *)key, (const u64 *)seed, (u64 *)out, status, stream));
     }
     int e = enqueue_mmh(pl, (const u64 *)key, (const u64 *)seed, pl->ybuf, false, stream);
     if (!e) e = enqueue_mh(pl, (const u64 *)seed, (u64 *)out, status, stream);
@@ -858,8 +856,7 @@ int pa_hash_host_async(pa_plan_t *pl, const uint64_t *key, const uint64_t *seed,
         // three-prime plans start once the whole key and seed have landed
         if (!e) e = cudaStreamWaitEvent(s, st.ready[ng], 0);
         for (int q = 0; q < ng && !e; q++) e = cudaStreamWaitEvent(s, st.ready[q], 0);
-        if (!e) e = p3_enqueue_mmh(pl->p3, st.dkey, st.dseed, p3_ybuf(pl->p3), false, stream);
-        if (!e) e = p3_enqueue_mh(pl->p3, st.dseed, st.dout, st.dstatus, stream);
+        if (!e) e = p3_enqueue_hash(pl->p3, st.dkey, st.dseed, st.dout, st.dstatus, stream);
         if (!e) e = cudaEventRecord(st.free_ev, s);
         if (!e) e = cudaMemcpyAsync(out, st.dout, ow * 8, cudaMemcpyDeviceToHost, s);
         if (!e) e = cudaMemcpyAsync(status ? status : st.hstatus, st.dstatus, sizeof(int), cudaMemcpyDeviceToHost, s);

@@ -293,12 +293,11 @@ void p3_plan_destroy(P3Plan *pl);
 void p3_plan_query(const P3Plan *pl, uint64_t *len_mmh, uint64_t *len_mh, uint64_t *ws_bytes);
 const Geo3 *p3_stage(const P3Plan *pl, int stage);
 int p3_enqueue_mmh(P3Plan *pl, const u64 *key, const u64 *seed, u64 *y, bool canonical, void *stream);
-int p3_enqueue_mh(P3Plan *pl, const u64 *seed, u64 *out, int *status, void *stream);
+int p3_enqueue_hash(P3Plan *pl, const u64 *key, const u64 *seed, u64 *out, int *status, void *stream);
 // Seed reuse: spectra of a_1..a_k and b (and a seed copy) kept in the plan.
 int p3_seed_prepare(P3Plan *pl, const u64 *seed, void *stream);
 int p3_hash_prepared(P3Plan *pl, const u64 *key, u64 *out, int *status, void *stream);
 bool p3_prepared(const P3Plan *pl);
-u64 *p3_ybuf(P3Plan *pl);
 int *p3_flags(P3Plan *pl);
 size_t p3_flags_bytes(const P3Plan *pl);
 

@@ -1720,7 +1720,18 @@ struct P3Plan {
     bool toep = false;
     uint64_t rb = 0, nblk = 0;
     u64 *pseed = nullptr;
-    ~P3Plan() { mem.release(); }
+    // Eq. 4's seed operand b is transformed on `side` while the Eq. 2 stage runs
+    // (fork / join events); its column pass writes Yb (3 x 2 T_mh words, the column
+    // layout of a stage with one pair), its row pass the spectrum bspec (3 T_mh)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    u32 *Yb = nullptr, *bspec = nullptr;
+    ~P3Plan() {
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (side) cudaStreamDestroy(side);
+        mem.release();
+    }
     void *alloc(size_t bytes, int *err) {
         void *p = mem.take(bytes, err);
         if (p) ws_bytes += bytes;
@@ -1856,6 +1867,7 @@ static void ws_parts(const Geo3 &A, const Geo3 &B, uint64_t k, uint64_t *total_n
     s += 2 * ((A.G + 63) / 64 + 2) * 8;                    // ybuf, tbuf
     s += nch * 9 + 2 * (nch / kResolveMinChunks + 2);      // carry state
     s += (4 + k) * sizeof(int);
+    s += (3 * 2 + 3) * B.T * 4;  // Yb, bspec
     *total_no_tables = s;
 }
 
@@ -1903,6 +1915,13 @@ int p3_plan_create(uint64_t n, uint64_t r, uint32_t gamma, uint64_t k, bool stre
     pl->cta_cin = (unsigned char *)pl->alloc(nch / kResolveMinChunks + 2, &err);
     pl->flags_bytes = (4 + k) * sizeof(int);
     pl->flags = (int *)pl->alloc(pl->flags_bytes, &err);
+    // the column pass lays operand i of prime j at (2 K j + i) T, K = 1 for Eq. 4
+    pl->Yb = (u32 *)pl->alloc(3 * 2 * B.T * 4, &err);
+    pl->bspec = (u32 *)pl->alloc(3 * B.T * 4, &err);
+    if (!err && (cudaStreamCreateWithFlags(&pl->side, cudaStreamNonBlocking) ||
+                 cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming) ||
+                 cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming)))
+        err = PA_ERR_CUDA;
     if (!err) err = pl->mem.sync();  // the tables are filled
     if (err) {
         delete pl;
@@ -1984,7 +2003,10 @@ static int mmh_impl(P3Plan *pl, const u64 *key, const u64 *seed, u64 *y, bool ca
 
 // Eq. 4: out = ((b y + c) mod 2^gamma) >> (gamma - r), y from the plan's
 // buffer.  prep: the spectrum of b comes from the plan, only y is transformed.
-static int mh_impl(P3Plan *pl, const u64 *seed, u64 *out, int *status, void *stream, bool prep) {
+// Eq. 4: z from y and the seed.  spec: b's spectrum (seed reuse, or computed
+// beside the Eq. 2 stage); null: b is transformed here with y.
+static int mh_impl(P3Plan *pl, const u64 *seed, u64 *out, int *status, void *stream, const u32 *spec) {
+    const bool prep = spec != nullptr;
     int e;
     Operands ops;
     ops.pair0 = 0;
@@ -1999,7 +2021,7 @@ static int mh_impl(P3Plan *pl, const u64 *seed, u64 *out, int *status, void *str
     ops.mode = prep ? 5 : 1;
     const Geo3 &X = pl->mh;
     if ((e = p3_launch_fwd_col(X, ops, 1, pl->Y, stream, !prep))) return e;
-    if ((e = p3_launch_row_mac(X, pl->Y, pl->S3, stream, prep ? 2 : 0, prep ? pl->spec_b : nullptr))) return e;
+    if ((e = p3_launch_row_mac(X, pl->Y, pl->S3, stream, prep ? 2 : 0, const_cast<u32 *>(spec)))) return e;
     const CarryDev cd = p3_carry_dev(pl, X, false, pl->flags + 2);
     const u64 npad = cd.nchunks * PA_CARRY_D;
     const u64 twords = (pl->gamma + 63) / 64;
@@ -2022,8 +2044,39 @@ int p3_enqueue_mmh(P3Plan *pl, const u64 *key, const u64 *seed, u64 *y, bool can
     return mmh_impl(pl, key, seed, y, canonical, stream, false);
 }
 
-int p3_enqueue_mh(P3Plan *pl, const u64 *seed, u64 *out, int *status, void *stream) {
-    return mh_impl(pl, seed, out, status, stream, false);
+// A whole block (Algorithm 1).  b's column and row transforms (Eq. 4) do not
+// depend on y: from Eq. 4 transforms of 2^20 on (whose single-pair column
+// pass fills less than a wave) they run on the plan's side stream, forked
+// from `stream` at the start and joined before Eq. 4, filling SMs the Eq. 2
+// kernels leave idle; Eq. 4 then transforms y alone and multiplies by the
+// stored spectrum of b.  Shorter blocks keep the pair (y, b) in Eq. 4.
+int p3_enqueue_hash(P3Plan *pl, const u64 *key, const u64 *seed, u64 *out, int *status, void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    int e;
+    if (pl->mh.T < (1ULL << 20)) {
+        if ((e = mmh_impl(pl, key, seed, pl->ybuf, false, stream, false))) return e;
+        return mh_impl(pl, seed, out, status, stream, nullptr);
+    }
+    if ((e = cudaEventRecord(pl->ev_fork, s)) || (e = cudaStreamWaitEvent(pl->side, pl->ev_fork, 0))) return e;
+    Geo3 Xb = pl->mh;
+    Xb.stage = 2;  // traced as mh_b.*
+    Operands ops;
+    ops.pair0 = 0;
+    ops.key = nullptr;
+    ops.seed = seed;
+    ops.y = nullptr;
+    ops.y_zero = nullptr;
+    ops.reload = pl->flags;
+    ops.n = pl->n;
+    ops.gamma = pl->gamma;
+    ops.k = pl->k;
+    ops.mode = 4;  // b
+    if ((e = p3_launch_fwd_col(Xb, ops, 1, pl->Yb, pl->side, false))) return e;
+    if ((e = p3_launch_row_mac(Xb, pl->Yb, nullptr, pl->side, 1, pl->bspec))) return e;
+    if ((e = cudaEventRecord(pl->ev_join, pl->side))) return e;
+    if ((e = mmh_impl(pl, key, seed, pl->ybuf, false, stream, false))) return e;
+    if ((e = cudaStreamWaitEvent(s, pl->ev_join, 0))) return e;
+    return mh_impl(pl, seed, out, status, stream, pl->bspec);
 }
 
 // Seed reuse: forward transforms (columns, then rows) of a_1..a_k and of b,
@@ -2063,7 +2116,7 @@ int p3_seed_prepare(P3Plan *pl, const u64 *seed, void *stream) {
 
 int p3_hash_prepared(P3Plan *pl, const u64 *key, u64 *out, int *status, void *stream) {
     int e = mmh_impl(pl, key, pl->seed_copy, pl->ybuf, false, stream, true);
-    if (!e) e = mh_impl(pl, pl->seed_copy, out, status, stream, true);
+    if (!e) e = mh_impl(pl, pl->seed_copy, out, status, stream, pl->spec_b);
     return e;
 }
 
@@ -2165,7 +2218,6 @@ void p3_toeplitz_query(const P3Plan *pl, uint64_t *rb, uint64_t *segments, uint6
     if (blocks) *blocks = pl->nblk;
 }
 
-u64 *p3_ybuf(P3Plan *pl) { return pl->ybuf; }
 int *p3_flags(P3Plan *pl) { return pl->flags; }
 size_t p3_flags_bytes(const P3Plan *pl) { return pl->flags_bytes; }
 

@@ -51,7 +51,8 @@ void *trace_begin(const char *name, u32 stage, void *stream) {
     if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
         return nullptr;
     Rec r;
-    r.name = std::string(stage == 0 ? "mmh." : "mh.") + name;
+    // stage 2: Eq. 4's seed operand transformed beside the Eq. 2 stage
+    r.name = std::string(stage == 0 ? "mmh." : stage == 1 ? "mh." : "mh_b.") + name;
     if (!g_only.empty() && r.name != g_only) return nullptr;
     r.a = take_event();
     r.b = take_event();

@@ -40,3 +40,33 @@ def test_trace_all_and_selected(backend):
     _lib.trace_select(None)
     assert list(sel) == [name] and sel[name][0] == 3
     plan.close()
+
+
+def test_eq4_seed_transforms_beside_eq2():
+    """Three-prime blocks with Eq. 4 transforms of 2^20 or more transform b on
+    the plan's side stream (traced as mh_b.*, once per block) and y alone in
+    Eq. 4, whose row pass multiplies by b's stored spectrum; the output is the
+    one of the same block hashed through seed reuse, where b's spectrum comes
+    from pa_seed_prepare."""
+    import torch
+    from paper_2105_13678_gb300 import _lib
+    n, r = 100_000_000, 10_000_000
+    plan = _lib.Plan(n, r, backend=2)
+    assert plan.info.mh_len >= 1 << 20
+    key, seed = synthetic.block_inputs(18, n, (plan.k + 2) * plan.gamma)
+    _lib.trace_enable(True)
+    _run(plan, key, seed)
+    tr = _lib.trace_collect()
+    _lib.trace_enable(False)
+    assert tr["mh_b.p3_fwd_col"][0] == 2 and tr["mh_b.p3_row_store"][0] == 2, tr
+    assert tr["mh.p3_fwd_col"][0] == 2 and tr["mh.p3_row_mac"][0] == 2, tr
+    dk, ds = dev(key), dev(seed)
+    sp = torch.cuda.current_stream().cuda_stream
+    o1 = torch.zeros(plan.info.out_words, dtype=torch.int64, device="cuda")
+    o2 = torch.zeros_like(o1)
+    _lib.pa_hash(plan, dk.data_ptr(), ds.data_ptr(), o1.data_ptr(), 0, sp)
+    _lib.pa_seed_prepare(plan, ds.data_ptr(), sp)
+    _lib.pa_hash_prepared(plan, dk.data_ptr(), o2.data_ptr(), 0, sp)
+    torch.cuda.synchronize()
+    assert torch.equal(o1, o2)
+    plan.close()
