@@ -51,3 +51,11 @@ def test_reference_arm_other_ranks_exit_quietly(capsys, monkeypatch):
     monkeypatch.setenv("WORLD_SIZE", "2")
     bench.run_reference(types.SimpleNamespace(steps=1, warmup=0))
     assert capsys.readouterr().out == ""
+
+
+def test_dominant_kernel_skips_side_stream_spans():
+    """Event spans of the side-stream transforms (mh_b.*) include waiting for
+    SMs; the dominant kernel is chosen among the other traced kernels."""
+    import bench
+    tr = {"mh_b.p3_row_store": (2, 900.0), "mmh.p3_fwd_col": (2, 600.0), "mmh.p3_row_mac": (2, 550.0)}
+    assert bench.dominant_kernel(tr) == "mmh.p3_fwd_col"
