@@ -172,10 +172,10 @@ def p3_butterfly_alu(T: int):
     return (3, 4) if T <= (1 << 21) else (4, 6)
 
 
-# Eq. 4 transforms of 2^20 or more take b's spectrum from the side stream
+# Eq. 4 transforms of 2^20 and 2^21 take b's spectrum from the side stream
 # (mh_b.*): Eq. 4's column pass then transforms y alone and its row pass
 # multiplies by the stored spectrum.
-P3_SIDE_MIN_LEN = 1 << 20
+P3_SIDE_LENS = (1 << 20, 1 << 21)
 
 
 def kernel_model_p3(info, stage: str, kernel: str, geometry=None):
@@ -186,7 +186,7 @@ def kernel_model_p3(info, stage: str, kernel: str, geometry=None):
         nops = 2 * K  # operands transformed
     else:
         T, K = info.mh_len, 1
-        side = T >= P3_SIDE_MIN_LEN
+        side = T in P3_SIDE_LENS
         src_bits = gamma if (side or stage == "mh_b") else 2 * gamma
         nops = 1 if (side or stage == "mh_b") else 2
     logT = int(math.log2(T))

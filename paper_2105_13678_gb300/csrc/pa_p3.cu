@@ -2045,15 +2045,17 @@ int p3_enqueue_mmh(P3Plan *pl, const u64 *key, const u64 *seed, u64 *y, bool can
 }
 
 // A whole block (Algorithm 1).  b's column and row transforms (Eq. 4) do not
-// depend on y: from Eq. 4 transforms of 2^20 on (whose single-pair column
-// pass fills less than a wave) they run on the plan's side stream, forked
-// from `stream` at the start and joined before Eq. 4, filling SMs the Eq. 2
-// kernels leave idle; Eq. 4 then transforms y alone and multiplies by the
-// stored spectrum of b.  Shorter blocks keep the pair (y, b) in Eq. 4.
+// depend on y: for Eq. 4 transforms of 2^20 and 2^21 (whose single-pair
+// column pass fills less than a wave) they run on the plan's side stream,
+// forked from `stream` at the start and joined before Eq. 4, filling SMs the
+// Eq. 2 kernels leave idle; Eq. 4 then transforms y alone and multiplies by
+// the stored spectrum of b.  Shorter blocks (latency-bound) and longer ones
+// (an Eq. 4 column pass of several waves, rows of 2^12 or more) keep the pair
+// (y, b) in Eq. 4: measured faster there.
 int p3_enqueue_hash(P3Plan *pl, const u64 *key, const u64 *seed, u64 *out, int *status, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     int e;
-    if (pl->mh.T < (1ULL << 20)) {
+    if (pl->mh.T < (1ULL << 20) || pl->mh.T > (1ULL << 21)) {
         if ((e = mmh_impl(pl, key, seed, pl->ybuf, false, stream, false))) return e;
         return mh_impl(pl, seed, out, status, stream, nullptr);
     }
