@@ -1375,10 +1375,11 @@ static size_t col_smem3(const Geo3 &X, bool pair) {
 }
 static size_t row_smem3(const Geo3 &X) { return (size_t)2 * (X.C + (X.C >> 3) + 8) * sizeof(u32); }
 
-// Instantiated shapes.  Transforms up to 2^21 use the primes below 2^28
-// (headroom H = 4), longer ones the primes below 2^30 (H = 2); with R = 2^10
-// for T >= 2^20 the row length fixes H: rows of 2^10, 2^11 (and every shorter
-// transform) H = 4, rows of 2^12 .. 2^14 H = 2.
+// Instantiated shapes.  Transforms up to 2^22 use primes below 2^28
+// (headroom H = 4), longer ones primes below 2^30 (H = 2); with R = 2^10 for
+// T >= 2^20 the row length fixes H: rows of 2^10, 2^11 (and every shorter
+// transform) H = 4, rows of 2^12 H = 4 or (operands beyond the smaller
+// primes' bound) 2, rows of 2^13 and 2^14 H = 2.
 template <int MODE>
 static cudaError_t p3_row_attrs(int big) {
     cudaError_t e;
@@ -1387,6 +1388,7 @@ static cudaError_t p3_row_attrs(int big) {
     P3_ATTR((k3_row_mac<8, 0, MODE, 4>))
     P3_ATTR((k3_row_mac<8, 10, MODE, 4>))
     P3_ATTR((k3_row_mac<8, 11, MODE, 4>))
+    P3_ATTR((k3_row_mac<8, 12, MODE, 4>))
     P3_ATTR((k3_row_mac<8, 12, MODE, 2>))
     P3_ATTR((k3_row_mac<8, 13, MODE, 2>))
     P3_ATTR((k3_row_mac<16, 14, MODE, 2>))
@@ -1471,7 +1473,12 @@ static int p3_row_launch(const Geo3 &X, const u32 *Y, u32 *S3, u32 *spec, cudaSt
     switch (X.logC) {
     case 10: P3_ROW(8, 10, 4); break;
     case 11: P3_ROW(8, 11, 4); break;
-    case 12: P3_ROW(8, 12, 2); break;
+    case 12:
+        if (X.head == 4)
+            P3_ROW(8, 12, 4);
+        else
+            P3_ROW(8, 12, 2);
+        break;
     case 13: P3_ROW(8, 13, 2); break;
     case 14: P3_ROW(16, 14, 2); break;
     default:
@@ -1584,12 +1591,19 @@ struct PrimeSet {
     u32 head;    // 2^head p < 2^32: the lazy-reduction headroom of the butterflies
 };
 // Transforms up to 2^21: the three largest primes below 2^28 with 2^21 | p - 1
-// (product 2^83.6; values may grow to 16p between reductions).  Up to 2^23:
-// the three largest below 2^30 with 2^23 | p - 1; 2^24: the three below 2^30
-// with 2^24 | p - 1 (the only ones); both reduce to [0, 2p) every stage.
+// (product 2^83.6; values may grow to 16p between reductions); 2^22: the
+// three largest below 2^28 with 2^22 | p - 1 (product 2^82.4, headroom 16p as
+// well).  2^23: the three largest below 2^30 with 2^23 | p - 1 (below 2^28
+// there is only one); 2^24: the three below 2^30 with 2^24 | p - 1 (the only
+// ones); both with headroom 4p.
 const PrimeSet kSetA4 = {{257949697u, 249561089u, 230686721u}, 21, 4};
+const PrimeSet kSetA4b = {{230686721u, 167772161u, 163577857u}, 22, 4};
 const PrimeSet kSetA = {{998244353u, 754974721u, 469762049u}, 23, 2};
 const PrimeSet kSetB = {{754974721u, 469762049u, 167772161u}, 24, 2};
+
+const PrimeSet &prime_set(u32 logT) {
+    return logT <= kSetA4.maxlog ? kSetA4 : logT <= kSetA4b.maxlog ? kSetA4b : logT <= kSetA.maxlog ? kSetA : kSetB;
+}
 
 u32 powmod(u64 b, u64 e, u32 p) {
     u64 r = 1;
@@ -1637,21 +1651,27 @@ struct Choice {
 // top carry chunk must span >= 64 bits whenever the parallel carry runs.
 bool choose(uint64_t G, uint64_t K, bool ring, Choice *out) {
     for (u32 l = 8; l <= 24; l++) {
-        const PrimeSet &ps = l <= kSetA4.maxlog ? kSetA4 : (l <= kSetA.maxlog ? kSetA : kSetB);
-        const unsigned __int128 P = (unsigned __int128)ps.p[0] * ps.p[1] * ps.p[2];
-        const u64 M = 1ULL << (l - 1);
-        const u64 bmin = std::max<u64>(1, (G + M - 1) / M);
-        for (u64 b = bmin; b <= 30; b++) {
-            const unsigned __int128 m = ((unsigned __int128)1 << b) - 1;
-            if ((unsigned __int128)K * M * m * m >= P) break;
-            const u64 nd = (G + b - 1) / b;
-            const u64 nch = (nd + PA_CARRY_D - 1) / PA_CARRY_D;
-            const bool parallel = nch >= PA_CARRY_T && b * PA_CARRY_D >= 64;
-            if (ring && parallel && G - (nch - 1) * PA_CARRY_D * b < 64) continue;
-            out->logT = l;
-            out->b = (u32)b;
-            out->ps = &ps;
-            return true;
+        // at 2^22 the primes below 2^30 (a larger product) serve the operands
+        // whose bound the primes below 2^28 cannot meet, before a longer transform
+        const PrimeSet *cand[2] = {&prime_set(l), l == kSetA4b.maxlog ? &kSetA : nullptr};
+        for (const PrimeSet *pc : cand) {
+            if (!pc) continue;
+            const PrimeSet &ps = *pc;
+            const unsigned __int128 P = (unsigned __int128)ps.p[0] * ps.p[1] * ps.p[2];
+            const u64 M = 1ULL << (l - 1);
+            const u64 bmin = std::max<u64>(1, (G + M - 1) / M);
+            for (u64 b = bmin; b <= 30; b++) {
+                const unsigned __int128 m = ((unsigned __int128)1 << b) - 1;
+                if ((unsigned __int128)K * M * m * m >= P) break;
+                const u64 nd = (G + b - 1) / b;
+                const u64 nch = (nd + PA_CARRY_D - 1) / PA_CARRY_D;
+                const bool parallel = nch >= PA_CARRY_T && b * PA_CARRY_D >= 64;
+                if (ring && parallel && G - (nch - 1) * PA_CARRY_D * b < 64) continue;
+                out->logT = l;
+                out->b = (u32)b;
+                out->ps = &ps;
+                return true;
+            }
         }
     }
     return false;
@@ -2144,7 +2164,7 @@ int p3_toeplitz_create(uint64_t n, uint64_t r, uint32_t rb_log, P3Plan **out) {
     Choice ch;
     ch.logT = rb_log + 2;
     ch.b = 1;
-    ch.ps = ch.logT <= kSetA4.maxlog ? &kSetA4 : (ch.logT <= kSetA.maxlog ? &kSetA : &kSetB);
+    ch.ps = &prime_set(ch.logT);
     // coefficients are at most n (< every prime): exact
     P3Plan *pl = new (std::nothrow) P3Plan();
     if (!pl) return PA_ERR_NOMEM;
